@@ -1,0 +1,300 @@
+"""Flow-level pins of the oracle: exact invariants, closed forms and the
+paper's verification cases (Sec. III).
+
+* Uniform periodic state under uniform g: u(n) = u0 + n g exactly (the
+  half-force shift of Eq. half_F and the first-moment force g dt).
+* Total momentum grows by M g per step; mass is conserved with walls and
+  obstacles.
+* Body-force-driven Poiseuille flow (BGK + second-order force + halfway
+  bounce-back) equals the parabola plus a uniform slip
+  u(y_j) = g/(2 nu) [(H/2)^2 - (y_j - H/2)^2] + g (16 a^2 - 3)/(8 a),
+  a = tau - 1/2, y_j = j + 1/2 (steady link-wise analysis of the scheme).
+* Forced Taylor-Green flow converges at second order (Sec. III.A).
+* Womersley flow matches the analytic solution (Sec. III.B), with the
+  start-from-rest transient of the diffusion equation added.
+* A tiny domain with walls and solids against a population-space BGK written
+  out independently below.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import lbm_workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_cases.json")))
+LATTICES = [O.D2Q9, O.D3Q19, O.D3Q27]
+
+
+def _shape(lat, n2=(6, 5), n3=(4, 3, 5)):
+    return (n2[0], n2[1], 1) if lat == O.D2Q9 else n3
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+def test_uniform_state_velocity_grows_by_g(lat, coll):
+    D = 2 if lat == O.D2Q9 else 3
+    shape = _shape(lat)
+    nx, ny, nz = shape
+    u0 = np.array([0.01, -0.02, 0.015][:D])
+    g = np.array([1e-4, 3e-5, -2e-5][:D])
+    s = O.Sim(lat, coll, shape, tau=(1, 1.1, 0.7, 0.9, 1.0), g=g,
+              u0=np.broadcast_to(u0[:, None, None, None], (D, nz, ny, nx)).copy())
+    for n in (1, 7, 20):
+        s.step(n - s.t)
+        rho, u, tot = s.moments()
+        for a in range(D):
+            assert np.abs(u[a] - (u0[a] + n * g[a])).max() < 1e-15
+        assert np.abs(rho - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+def test_momentum_grows_by_Mg(lat, coll):
+    D = 2 if lat == O.D2Q9 else 3
+    shape = _shape(lat, (8, 7), (5, 4, 6))
+    rho0, u0 = W.random_near_equilibrium(W.D2Q9 if D == 2 else W.D3Q27, shape, seed=7)
+    g = np.array([2e-5, -1e-5, 3e-6][:D])
+    s = O.Sim(lat, coll, shape, tau=(1, 1, 0.62, 0.8, 1.0), g=g, rho0=rho0, u0=u0)
+    _, _, t0 = s.moments()
+    s.step(50)
+    _, _, t1 = s.moments()
+    M = t0[0]
+    assert abs(t1[0] - M) / M < 1e-14
+    for a in range(D):
+        assert abs(t1[1 + a] - t0[1 + a] - 50 * M * g[a]) < 1e-12 * M * 50 * abs(g).max()
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+def test_mass_conserved_with_walls_and_solids(lat, coll):
+    D = 2 if lat == O.D2Q9 else 3
+    shape = _shape(lat, (12, 9), (6, 5, 4))
+    # exact in the method; in FP64 with O(1) populations the rounding drifts
+    # by ~1e-16 relative per step, so the bound is checked over 500 steps
+    steps = 500 if D == 2 else 100
+    rho0, u0 = W.random_near_equilibrium(W.D2Q9 if D == 2 else W.D3Q27, shape, seed=8)
+    solid = W.random_solid(shape, seed=9, frac=0.15)
+    g = np.array([1e-5, 2e-6, 0.0][:D])
+    s = O.Sim(lat, coll, shape, periodic=(1, 0, 0), tau=(1, 1, 0.7, 1.0, 1.0), g=g,
+              solid=solid, rho0=rho0, u0=u0)
+    _, _, t0 = s.moments()
+    s.step(steps)
+    rho, u, t1 = s.moments()
+    assert abs(t1[0] - t0[0]) / t0[0] < 1e-13
+    assert np.all(np.isfinite(u))
+    assert np.all(u[:, solid.astype(bool)] == 0.0)
+
+
+def test_poiseuille_closed_form():
+    """The 64 x 32 channel, tau 0.8, g 1e-6, 20000 steps (FP64)."""
+    wl = W.poiseuille_channel()
+    nx, ny, _ = wl.shape
+    tau = wl.tau[2]
+    gx = wl.g[0]
+    s = O.Sim(O.D2Q9, O.BGK, wl.shape, periodic=wl.periodic, tau=wl.tau, g=wl.g)
+    s.step(wl.steps)
+    _, u, _ = s.moments()
+    nu, a = (tau - 0.5) / 3.0, tau - 0.5
+    y = np.arange(ny) + 0.5
+    ua = gx / (2 * nu) * ((ny / 2) ** 2 - (y - ny / 2) ** 2) + gx * (16 * a * a - 3) / (8 * a)
+    ux = u[0, 0]
+    # uniform in x, no cross flow
+    assert np.abs(ux - ux[:, :1]).max() < 1e-18
+    assert np.abs(u[1]).max() < 1e-14
+    # remaining transient of the slowest mode: exp(-nu pi^2 t / H^2) ~ 4e-9
+    err = np.linalg.norm(ux[:, 0] - ua) / np.linalg.norm(ua)
+    assert err < 1e-8, err
+
+
+def test_poiseuille_smrt_second_difference():
+    """SMRT in the same channel: the interior profile has the exact viscosity
+    nu = (tau_2 - 1/2)/3, i.e. second difference -g/nu (wall slip depends on
+    tau_3 and is left to the GPU-oracle parity)."""
+    ny = 32
+    s = O.Sim(O.D2Q9, O.SMRT, (4, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1.0, 1.0), g=[1e-6, 0])
+    s.step(20000)
+    _, u, _ = s.moments()
+    ux = u[0, 0, :, 0]
+    nu = 0.3 / 3
+    d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    assert np.abs(d2 + 1e-6 / nu).max() < 1e-8 * 1e-6 / nu * 1e3
+
+
+@pytest.mark.slow
+def test_taylor_green_second_order():
+    cfg = GOLD["taylor_green_2d"]
+    errs = []
+    for L in cfg["L"]:
+        tau, T, uinit, force = W.taylor_green_2d(L, cfg["u0"], cfg["Re"])
+        s = O.Sim(O.D2Q9, O.SMRT, (L, L, 1), tau=(1, 1, tau, 1, 1), g=force(0),
+                  force_kind="field", u0=uinit)
+        for t in range(T):
+            s.set_force(force(t), "field")
+            s.step(1)
+        s.set_force(force(T), "field")
+        _, u, _ = s.moments()
+        k, nu = 2 * np.pi / L, cfg["u0"] * L / cfg["Re"]
+        ua = uinit * math.exp(-2 * k * k * nu * T)  # velocity decays at (k1^2 + k2^2) nu
+        errs.append(math.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    lo, hi = cfg["slope_range"]
+    assert all(lo <= s <= hi for s in slopes), (errs, slopes)
+
+
+def _womersley_periodic(y, t, A, om, nu, Lh):
+    k = (1 + 1j) * math.sqrt(om / (2 * nu))
+    return np.real(1j * A / om * (1 - np.cosh(k * y) / np.cosh(k * Lh)) * np.exp(1j * om * t))
+
+
+def _womersley_transient(y, t, A, om, nu, Lh, nmax=200):
+    """Start-up from rest: u_t = nu u_yy, u(+-Lh) = 0, u(y, 0) = -U_periodic(y, 0),
+    expanded in the even no-slip modes cos((2n+1) pi y / (2 Lh))."""
+    yq = np.linspace(-Lh, Lh, 40001)
+    u0 = -_womersley_periodic(yq, 0.0, A, om, nu, Lh)
+    out = np.zeros_like(y)
+    for n in range(nmax):
+        kn = (2 * n + 1) * math.pi / (2 * Lh)
+        bn = np.trapezoid(u0 * np.cos(kn * yq), yq) / Lh
+        out += bn * np.cos(kn * y) * math.exp(-nu * kn * kn * t)
+    return out
+
+
+@pytest.mark.slow
+def test_womersley():
+    """Sec. III.B with halfway bounce-back in place of diffuse reflection.  The
+    flow is uniform in x, so a one-node-wide periodic strip is the same flow
+    as the 50-wide domain (checked for a few hundred steps below)."""
+    cfg = GOLD["womersley"]
+    ny, T, nu, A = cfg["ny"], cfg["T"], cfg["nu"], cfg["Ap"]
+    tau = 3 * nu + 0.5
+    om = 2 * math.pi / T
+    Lh = ny / 2
+    y = np.arange(ny) + 0.5 - Lh
+    s = O.Sim(O.D2Q9, O.SMRT, (1, ny, 1), periodic=(1, 0, 1), tau=(1, 1, tau, 1, 1), g=[-A, 0])
+    t = 0
+    worst = 0.0
+    for n in range(cfg["periods"] * 16 + 15):
+        tgt = n * T // 16
+        while t < tgt:
+            s.set_force([-A * math.cos(om * t), 0.0])
+            s.step(1)
+            t += 1
+        if n >= cfg["periods"] * 16 and (n - cfg["periods"] * 16) in cfg["sample_n"]:
+            s.set_force([-A * math.cos(om * t), 0.0])
+            _, u, _ = s.moments()
+            ua = _womersley_periodic(y, t, A, om, nu, Lh) + _womersley_transient(y, t, A, om, nu, Lh)
+            worst = max(worst, np.abs(u[0, 0, :, 0] - ua).max() / (A / om))
+    # halfway bounce-back is second order; the error is ~1e-3 of the amplitude
+    assert worst < 3e-3, worst
+
+
+def test_womersley_strip_equals_wide_domain():
+    A, T, ny = 1e-4, 1200, 40
+    om = 2 * math.pi / T
+    a = O.Sim(O.D2Q9, O.SMRT, (1, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1, 1), g=[-A, 0])
+    b = O.Sim(O.D2Q9, O.SMRT, (50, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1, 1), g=[-A, 0])
+    for t in range(300):
+        a.set_force([-A * math.cos(om * t), 0])
+        b.set_force([-A * math.cos(om * t), 0])
+        a.step(1)
+        b.step(1)
+    _, ua, _ = a.moments()
+    _, ub, _ = b.moments()
+    assert np.abs(ub - ua[:, :, :, :1]).max() < 1e-18
+
+
+# --------------------------------------------------------------------------
+# brute force: population-space BGK with its own tables and streaming
+# --------------------------------------------------------------------------
+def _lat_tables(D):
+    if D == 2:
+        c = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+        w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    else:
+        c = [(0, 0, 0)] + [v for v in
+                           [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                            (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
+                            (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]]
+        w = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+    return np.array(c, float), np.array(w)
+
+
+def _brute_bgk_step(c, w, tau, f, g, solid, periodic):
+    """f: (Q, nz, ny, nx) pre-collision.  Guo BGK, then push with bounce-back."""
+    Q = len(w)
+    D = c.shape[1]
+    out = np.tile(w[:, None, None, None], (1,) + f.shape[1:])
+    nz, ny, nx = f.shape[1:]
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if solid[z, y, x]:
+                    continue
+                fi = f[:, z, y, x]
+                rho = fi.sum()
+                u = (fi @ c + 0.5 * rho * g) / rho
+                cu = c @ u
+                feq = rho * w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * u @ u)
+                F = w * ((3 * (c - u) + 9 * cu[:, None] * c) @ (rho * g))
+                fp = fi - (fi - feq) / tau + (1 - 0.5 / tau) * F
+                for i in range(Q):
+                    pos = [x + int(c[i, 0]), y + int(c[i, 1]), z + (int(c[i, 2]) if D == 3 else 0)]
+                    n3 = [nx, ny, nz]
+                    hit = False
+                    for k in range(3):
+                        if not 0 <= pos[k] < n3[k]:
+                            if periodic[k]:
+                                pos[k] %= n3[k]
+                            else:
+                                hit = True
+                    if not hit and solid[pos[2], pos[1], pos[0]]:
+                        hit = True
+                    if hit:
+                        j = [k for k in range(Q) if np.all(c[k] == -c[i])][0]
+                        out[j, z, y, x] = fp[i]
+                    else:
+                        out[i, pos[2], pos[1], pos[0]] = fp[i]
+    return out
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_brute_force_bgk_with_walls_and_solids(D):
+    lat = O.D2Q9 if D == 2 else O.D3Q19
+    shape = (5, 4, 1) if D == 2 else (4, 3, 3)
+    periodic = (1, 0, 1) if D == 2 else (1, 0, 0)
+    c, w = _lat_tables(D)
+    solid = np.zeros(shape[::-1], np.uint8)
+    solid[0, 2, 1] = 1
+    tau = 0.73
+    g = np.array([2e-4, -1e-4, 5e-5][:D])
+    rho0, u0 = W.random_near_equilibrium(W.D2Q9 if D == 2 else W.D3Q19, shape, seed=3, du=0.05)
+    s = O.Sim(lat, O.BGK, shape, periodic=periodic, tau=(1, 1, tau, 1, 1), g=g, solid=solid,
+              rho0=rho0, u0=u0)
+    f = s.populations()
+    for _ in range(6):
+        f = _brute_bgk_step(c, w, tau, f, g, solid, periodic)
+        s.step(1)
+        fo = s.populations()
+        assert np.abs(fo - f)[:, ~solid.astype(bool)].max() < 1e-15
+
+
+def test_storage_rounding_matches_ieee():
+    """The oracle's storage emulation rounds to nearest-even: compare with
+    numpy's float32 / float16 casts and with a bit-level bfloat16 rounding of
+    float32-representable values."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=2000) * 10.0 ** rng.integers(-9, 2, size=2000),
+                        [0.0, 65504.0, 65520.0, 6e-8, 3e-8, 2.0 ** -25, 1.0 + 2.0 ** -11]])
+    assert np.array_equal(O.round_values(O.ROUND_F32, x), x.astype(np.float32).astype(np.float64))
+    with np.errstate(over="ignore"):
+        f16 = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(O.round_values(O.ROUND_F16, x), f16)
+    xf = x.astype(np.float32)
+    b = xf.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    bf = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    assert np.array_equal(O.round_values(O.ROUND_BF16, xf.astype(np.float64)), bf)
