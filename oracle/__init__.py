@@ -217,7 +217,9 @@ def force_field(params, g, force_kind="uniform"):
 
 
 class Sim:
-    """Stateful oracle run: f holds the pre-collision populations fbar(x, t)."""
+    """Stateful oracle run.  ``d`` holds the stored deviations
+    delta_i = fbar_i - w_i of the pre-collision populations fbar(x, t), [Q][N];
+    ``populations()`` / ``set_populations()`` speak fbar."""
 
     def __init__(self, lattice, collision, shape, periodic=(1, 1, 1), tau=(1, 1, 0.8, 1, 1),
                  g=None, force_kind="uniform", solid=None, rho0=None, u0=None, round_mode=0):
@@ -232,18 +234,19 @@ class Sim:
         self.round_mode = int(round_mode)
         rho0 = None if rho0 is None else np.ascontiguousarray(np.asarray(rho0, np.float64).reshape(self.N))
         u0 = None if u0 is None else np.ascontiguousarray(np.asarray(u0, np.float64).reshape(self.D * self.N))
-        self.f = np.zeros((self.Q, self.N))
-        assert lib().or_init(C.byref(p), _u8(self.solid), _d(rho0), _d(u0), _d(self.g), _d(self.f)) == 0
+        self.w = lattice_tables(lattice)[3]
+        self.d = np.zeros((self.Q, self.N))
+        assert lib().or_init(C.byref(p), _u8(self.solid), _d(rho0), _d(u0), _d(self.g), _d(self.d)) == 0
         if self.round_mode:
-            assert lib().or_round_storage(C.byref(p), self.round_mode, _d(self.f)) == 0
-        self._work = np.zeros_like(self.f)
+            assert lib().or_round_storage(C.byref(p), self.round_mode, _d(self.d)) == 0
+        self._work = np.zeros_like(self.d)
         self.t = 0
 
     def set_force(self, g, force_kind="uniform"):
         self.g = force_field(self.p, g, force_kind)
 
     def step(self, n=1):
-        rc = lib().or_run(C.byref(self.p), _u8(self.solid), _d(self.g), _d(self.f), _d(self._work),
+        rc = lib().or_run(C.byref(self.p), _u8(self.solid), _d(self.g), _d(self.d), _d(self._work),
                           int(n), self.round_mode)
         assert rc == 0
         self.t += n
@@ -252,12 +255,22 @@ class Sim:
         rho = np.zeros(self.N)
         u = np.zeros(self.D * self.N)
         tot = np.zeros(4)
-        assert lib().or_moments(C.byref(self.p), _u8(self.solid), _d(self.g), _d(self.f),
+        assert lib().or_moments(C.byref(self.p), _u8(self.solid), _d(self.g), _d(self.d),
                                 _d(rho), _d(u), _d(tot)) == 0
         return rho.reshape(self.shape), u.reshape((self.D,) + self.shape), tot
 
     def populations(self):
-        return self.f.reshape((self.Q,) + self.shape).copy()
+        """Pre-collision populations fbar = w + delta, (Q, nz, ny, nx)."""
+        return (self.w[:, None] + self.d).reshape((self.Q,) + self.shape)
+
+    def set_populations(self, f, round_mode=None):
+        """Replace the state by fbar (deviations taken exactly, then rounded to
+        the storage format when round_mode (default: the run's) is set)."""
+        d = np.asarray(f, np.float64).reshape(self.Q, self.N) - self.w[:, None]
+        self.d = np.ascontiguousarray(d)
+        mode = self.round_mode if round_mode is None else int(round_mode)
+        if mode:
+            assert lib().or_round_storage(C.byref(self.p), mode, _d(self.d)) == 0
 
 
 def round_values(mode, x):

@@ -31,6 +31,8 @@
  *  - BGK uses the second-order equilibrium and force of Eq. (collision_BGK)
  *    and the second-order F(xi) (Sec. II.A).
  *  - initial state: fbar = f_eq(rho0,u0) - F/2 (zero non-equilibrium part).
+ *  - the state is stored as deviations delta_i = fbar_i - w_i (see the
+ *    collision section).
  *  - boundaries: periodic, or halfway bounce-back at -1/2 and n-1/2 and at
  *    solid nodes.
  */
@@ -254,34 +256,45 @@ static void shift(const or_lattice *L, const double *s, const double *in, double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Collision at one node.  fbar: pre-collision populations (the variable of  */
-/* Eq. newf); gL: body-force acceleration in lattice units.  Writes the      */
-/* post-collision populations fp and, when dbg != NULL, the packed moment    */
-/* vectors [a_bar | a_0 | a_1 | d_1 | d_p | a_p] (6 x OR_PACK) for tests.    */
+/* Collision at one node.  The state is stored as deviations from the rest  */
+/* weights, delta_i = fbar_i - w_i (fbar: the variable of Eq. newf), in     */
+/* FP64: an O(1) population carries a rounding error of ~1e-17 per step,    */
+/* which at a slowly decaying steady state leaves a floor of ~5e-12 on a    */
+/* small velocity; the deviation carries it on its own, much smaller, size. */
+/* The algebra is unchanged: the weights' Hermite coefficients are          */
+/* (1, 0, 0, ...), so every moment of order >= 1 of fbar equals that of     */
+/* delta, a^(0) = 1 + sum delta, and reconstructing a coefficient vector    */
+/* with its order-0 entry lowered by one yields fbar_p - w directly.        */
+/* gL: body-force acceleration in lattice units.  When dbg != NULL the      */
+/* packed vectors [a_bar | a_0 | a_1 | d_1 | d_p | a_p] (6 x OR_PACK) are   */
+/* written for tests.                                                       */
 /* ------------------------------------------------------------------------ */
-static void macroscopic(const or_lattice *L, const double *fbar, const double *gL,
-                        double *rho_out, double *uH, double *gH)
+static void macroscopic(const or_lattice *L, const double *dev, const double *gL,
+                        double *drho_out, double *rho_out, double *uH, double *gH)
 {
-    double rho = 0.0, j[3] = {0, 0, 0};
+    double drho = 0.0, j[3] = {0, 0, 0};
     for (int i = 0; i < L->Q; ++i) {
-        rho += fbar[i];
-        for (int k = 0; k < L->D; ++k) j[k] += fbar[i] * L->xi[i][k];
+        drho += dev[i];
+        for (int k = 0; k < L->D; ++k) j[k] += dev[i] * L->xi[i][k];
     }
+    const double rho = 1.0 + drho;
     for (int k = 0; k < 3; ++k) { gH[k] = 0.0; uH[k] = 0.0; }
     for (int k = 0; k < L->D; ++k) {
         gH[k] = SQ3 * gL[k];
         /* Eq. (half_F): u = u_bar + F/(2 rho) with F = rho g */
         uH[k] = j[k] / rho + 0.5 * gH[k];
     }
+    *drho_out = drho;
     *rho_out = rho;
 }
 
-/* Second-order equilibrium and force of the BGK section */
-static double feq2(const or_lattice *L, int i, double rho, const double *u)
+/* Second-order equilibrium of the BGK section, minus w_i:
+ * f_eq - w = w_i [ (rho - 1) + rho (xi.u + ((xi.u)^2 - u^2)/2) ] */
+static double feq2_dev(const or_lattice *L, int i, double drho, double rho, const double *u)
 {
     double xu = 0.0, uu = 0.0;
     for (int k = 0; k < L->D; ++k) { xu += L->xi[i][k] * u[k]; uu += u[k] * u[k]; }
-    return rho * L->w[i] * (1.0 + xu + 0.5 * (xu * xu - uu));
+    return L->w[i] * (drho + rho * (xu + 0.5 * (xu * xu - uu)));
 }
 
 static double force2(const or_lattice *L, int i, double rho, const double *u, const double *g)
@@ -296,30 +309,31 @@ static double force2(const or_lattice *L, int i, double rho, const double *u, co
     return rho * L->w[i] * ((gx - gu) + gx * ux);
 }
 
-static void collide_bgk(const or_lattice *L, const double *tau, const double *fbar,
-                        const double *gL, double *fp)
+static void collide_bgk(const or_lattice *L, const double *tau, const double *dev,
+                        const double *gL, double *dp)
 {
-    double rho, u[3], g[3];
-    macroscopic(L, fbar, gL, &rho, u, g);
+    double drho, rho, u[3], g[3];
+    macroscopic(L, dev, gL, &drho, &rho, u, g);
     const double th = tau[2];
     for (int i = 0; i < L->Q; ++i) {
-        /* Eq. (explict_eq) */
-        fp[i] = fbar[i] - (fbar[i] - feq2(L, i, rho, u)) / th
+        /* Eq. (explict_eq), with w_i subtracted from fbar and f_eq alike */
+        dp[i] = dev[i] - (dev[i] - feq2_dev(L, i, drho, rho, u)) / th
               + (1.0 - 0.5 / th) * force2(L, i, rho, u, g);
     }
 }
 
-static void collide_smrt(const or_lattice *L, const double *tau, const double *fbar,
-                         const double *gL, double *fp, double *dbg)
+static void collide_smrt(const or_lattice *L, const double *tau, const double *dev,
+                         const double *gL, double *dpop, double *dbg)
 {
-    double rho, u[3], g[3], mu[3];
+    double drho, rho, u[3], g[3], mu[3];
     double abar[OR_PACK], a0[OR_PACK], a1[OR_PACK], d1[OR_PACK], dp[OR_PACK], ap[OR_PACK];
     double tot[OR_PACK];
     const int P = L->off[OR_MAXN + 1];
-    macroscopic(L, fbar, gL, &rho, u, g);
+    macroscopic(L, dev, gL, &drho, &rho, u, g);
     for (int k = 0; k < 3; ++k) mu[k] = -u[k];
 
-    project(L, fbar, abar);                 /* Eq. (dft) */
+    project(L, dev, abar);                  /* Eq. (dft); orders >= 1 of fbar */
+    abar[0] = rho;
     equilibrium_moments(L, rho, u, a0);     /* a_0^(n) = rho u^n */
     /* non-equilibrium raw moments a_bar_1 = a_bar - a_0; a_bar_1^(0) = 0 and
      * a_bar_1^(1) = -F/2 follow from the same subtraction (Eq. half_F). */
@@ -339,7 +353,8 @@ static void collide_smrt(const or_lattice *L, const double *tau, const double *f
     }
     shift(L, u, dp, ap);                    /* RCM -> RM (Eq. bbd1) */
     for (int k = 0; k < P; ++k) tot[k] = a0[k] + ap[k];
-    reconstruct(L, tot, fp);                /* post-collision reconstruction */
+    tot[0] = drho;                          /* rho - 1: reconstruct fbar_p - w */
+    reconstruct(L, tot, dpop);              /* post-collision reconstruction */
     if (dbg) {
         memcpy(dbg + 0 * OR_PACK, abar, sizeof(double) * P);
         memcpy(dbg + 1 * OR_PACK, a0, sizeof(double) * P);
@@ -350,15 +365,16 @@ static void collide_smrt(const or_lattice *L, const double *tau, const double *f
     }
 }
 
-/* fbar = f_eq - F/2 with the collision model's own equilibrium and force */
+/* delta = f_eq - F/2 - w with the collision model's own equilibrium and force */
 static void initial_node(const or_lattice *L, int collision, double rho, const double *uL,
-                         const double *gL, double *f)
+                         const double *gL, double *dev)
 {
     double u[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+    const double drho = rho - 1.0;
     for (int k = 0; k < L->D; ++k) { u[k] = SQ3 * uL[k]; g[k] = SQ3 * gL[k]; }
     if (collision == OR_BGK) {
         for (int i = 0; i < L->Q; ++i)
-            f[i] = feq2(L, i, rho, u) - 0.5 * force2(L, i, rho, u, g);
+            dev[i] = feq2_dev(L, i, drho, rho, u) - 0.5 * force2(L, i, rho, u, g);
         return;
     }
     double a0[OR_PACK], dF[OR_PACK], aF[OR_PACK], A[OR_PACK];
@@ -368,7 +384,8 @@ static void initial_node(const or_lattice *L, int collision, double rho, const d
     for (int k = 0; k < L->D; ++k) dF[L->off[1] + k] = rho * g[k];
     shift(L, u, dF, aF); /* raw-moment force coefficients a_F^(n) = n F u^(n-1) */
     for (int k = 0; k < P; ++k) A[k] = a0[k] - 0.5 * aF[k];
-    reconstruct(L, A, f);
+    A[0] = drho;
+    reconstruct(L, A, dev);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -463,29 +480,36 @@ int or_shift(int lattice, const double *s, const double *in, double *out)
     return 0;
 }
 
-/* One node's collision (lattice-unit g).  dbg: 6 x 121 doubles or NULL. */
+/* One node's collision (lattice-unit g) on populations fbar -> fbar_p.
+ * dbg: 6 x 121 doubles or NULL. */
 int or_collide_node(const or_params *p, const double *fbar, const double *gL, double *fp,
                     double *dbg)
 {
     or_lattice L;
+    double dev[OR_MAXQ], dp[OR_MAXQ];
     if (check_params(p, &L)) return -1;
-    if (p->collision == OR_BGK) collide_bgk(&L, p->tau, fbar, gL, fp);
-    else collide_smrt(&L, p->tau, fbar, gL, fp, dbg);
+    for (int i = 0; i < L.Q; ++i) dev[i] = fbar[i] - L.w[i];
+    if (p->collision == OR_BGK) collide_bgk(&L, p->tau, dev, gL, dp);
+    else collide_smrt(&L, p->tau, dev, gL, dp, dbg);
+    for (int i = 0; i < L.Q; ++i) fp[i] = L.w[i] + dp[i];
     return 0;
 }
 
-/* Initial populations at one node (lattice units). */
+/* Initial populations fbar at one node (lattice units). */
 int or_initial_node(const or_params *p, double rho, const double *uL, const double *gL, double *f)
 {
     or_lattice L;
+    double dev[OR_MAXQ];
     if (check_params(p, &L)) return -1;
-    initial_node(&L, p->collision, rho, uL, gL, f);
+    initial_node(&L, p->collision, rho, uL, gL, dev);
+    for (int i = 0; i < L.Q; ++i) f[i] = L.w[i] + dev[i];
     return 0;
 }
 
 static size_t n_nodes(const or_params *p) { return (size_t)p->nx * p->ny * p->nz; }
 
-/* f = f_eq(rho0, u0) - F/2 at fluid nodes, w_i at solid nodes.
+/* State arrays hold deviations delta = fbar - w, [Q][N].
+ * delta = f_eq(rho0, u0) - F/2 - w at fluid nodes, 0 at solid nodes.
  * rho0 / u0 nullable (=> 1 / 0). */
 int or_init(const or_params *p, const unsigned char *solid, const double *rho0,
             const double *u0, const double *g, double *f)
@@ -496,7 +520,7 @@ int or_init(const or_params *p, const unsigned char *solid, const double *rho0,
     for (size_t x = 0; x < N; ++x) {
         double fl[OR_MAXQ], uL[3] = {0, 0, 0}, gL[3] = {0, 0, 0};
         if (solid && solid[x]) {
-            for (int i = 0; i < L.Q; ++i) f[(size_t)i * N + x] = L.w[i];
+            for (int i = 0; i < L.Q; ++i) f[(size_t)i * N + x] = 0.0;
             continue;
         }
         for (int k = 0; k < L.D; ++k) {
@@ -520,7 +544,7 @@ int or_step(const or_params *p, const unsigned char *solid, const double *g,
     const size_t N = n_nodes(p);
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     for (int i = 0; i < L.Q; ++i)
-        for (size_t x = 0; x < N; ++x) f_out[(size_t)i * N + x] = L.w[i];
+        for (size_t x = 0; x < N; ++x) f_out[(size_t)i * N + x] = 0.0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -566,14 +590,15 @@ int or_moments(const or_params *p, const unsigned char *solid, const double *g,
     const size_t N = n_nodes(p);
     double T[4] = {0, 0, 0, 0};
     for (size_t x = 0; x < N; ++x) {
-        double r = 0.0, j[3] = {0, 0, 0}, uu[3] = {0, 0, 0};
+        double r = 0.0, dr = 0.0, j[3] = {0, 0, 0}, uu[3] = {0, 0, 0};
         int s = solid && solid[x];
         if (!s) {
             for (int i = 0; i < L.Q; ++i) {
-                double fi = f[(size_t)i * N + x];
-                r += fi;
-                for (int k = 0; k < L.D; ++k) j[k] += fi * L.c[i][k];
+                double di = f[(size_t)i * N + x];
+                dr += di;
+                for (int k = 0; k < L.D; ++k) j[k] += di * L.c[i][k];
             }
+            r = 1.0 + dr;
             for (int k = 0; k < L.D; ++k) {
                 double gk = g ? g[(size_t)k * N + x] : 0.0;
                 uu[k] = j[k] / r + 0.5 * gk; /* Eq. (half_F) in lattice units */
@@ -609,7 +634,7 @@ static double round_format(double x, int mant, int emin, double maxv)
 }
 
 /* Storage-precision emulation: mode 1 = FP32, 2 = FP16, 3 = BF16 applied to
- * the deviations delta_i = f_i - w_i of every population (solid included). */
+ * the stored deviations delta_i = fbar_i - w_i (solid nodes included). */
 int or_round_storage(const or_params *p, int mode, double *f)
 {
     or_lattice L;
@@ -617,14 +642,14 @@ int or_round_storage(const or_params *p, int mode, double *f)
     const size_t N = n_nodes(p);
     for (int i = 0; i < L.Q; ++i)
         for (size_t x = 0; x < N; ++x) {
-            double d = f[(size_t)i * N + x] - L.w[i];
+            double d = f[(size_t)i * N + x];
             switch (mode) {
             case 1: d = round_format(d, 23, -126, 3.4028234663852886e38); break;
             case 2: d = round_format(d, 10, -14, 65504.0); break;
             case 3: d = round_format(d, 7, -126, 3.3895313892515355e38); break;
             default: break;
             }
-            f[(size_t)i * N + x] = L.w[i] + d;
+            f[(size_t)i * N + x] = d;
         }
     return 0;
 }
