@@ -1,0 +1,157 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann library implementing the
+ * second-order force scheme of Li, Duan & Shan, "Second-order force scheme for
+ * lattice Boltzmann method" (arXiv:2212.07494).
+ *
+ * Problem statement (Sec. II of the paper): the discrete-velocity Boltzmann
+ * equation with a body-force term F_i (Eq. dv), discretised in space and time
+ * by the trapezoidal rule (Eq. implicityeq), which makes the stored variable
+ *   fbar_i = f_i - Omega_i / 2 - F_i / 2                          (Eq. newf)
+ * and the explicit update
+ *   fbar_i(x + c_i, t + 1) = fbar_i(x, t) + Omega_i(x, t) + F_i(x, t)   (Eq. evolution)
+ * with, for BGK, Eq. (explict_eq):
+ *   fbar_i <- fbar_i - (fbar_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i
+ * and, for SMRT, the order-by-order relaxation of the non-equilibrium central
+ * (co-moving) Hermite moments, Eq. (RHS) in explicit form:
+ *   d_p^(n) = (1 - 1/tau_n) d_1^(n) + (1 - 1/(2 tau_n)) d_F^(n),  d_F^(1) = rho g,
+ * followed by the shift back to raw moments (Eq. bbd1), reconstruction and
+ * streaming.  Macroscopic velocity: u = ubar + g/2 (Eq. half_F).
+ *
+ * Conventions shared by every entry point:
+ *  - Units: lattice units (dx = dt = 1, c_s^2 = 1/3).  "tau" is the relaxation
+ *    time appearing in the explicit update (the paper's tau-hat = tau + 1/2);
+ *    the kinematic viscosity is nu = (tau_2 - 1/2)/3.  Every tau must be > 1/2.
+ *  - Population order:
+ *      D2Q9 : 0 (0,0); 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1);
+ *             5 (1,1); 6 (-1,1); 7 (-1,-1); 8 (1,-1)
+ *      D3Q19: 0 rest; 1..6 (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1);
+ *             7..18 (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *             (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *      D3Q27: the D3Q19 order, then 19..26 (1,1,1) (-1,-1,-1) (1,1,-1)
+ *             (-1,-1,1) (1,-1,1) (-1,1,-1) (-1,1,1) (1,-1,-1)
+ *  - Host field layouts are structure-of-arrays with x fastest:
+ *      populations f[i][z][y][x], velocity u[a][z][y][x] (a < D),
+ *      per-node force g[a][z][y][x], per-row force g[y][a], solid[z][y][x].
+ *  - Boundaries: an axis with periodic[k] = 0 has halfway bounce-back walls at
+ *    -1/2 and n_k - 1/2; solid nodes (solid[x] != 0) bounce links back halfway
+ *    too.  Solid nodes report rho = 1, u = 0 and are left out of totals.
+ *  - Status codes: every call returns LBM_OK or a negative lbm_status; nothing
+ *    throws across the ABI; lbm_last_error() returns a description of the
+ *    last failure (per handle; thread-local for NULL).
+ *  - Memory: the handle owns every device buffer it allocates (through the
+ *    optional alloc/free callbacks, e.g. a PyTorch caching allocator, else
+ *    cudaMalloc).  Input arrays are copied during the call; output arrays are
+ *    caller-owned.  Calls are asynchronous on the handle's stream unless they
+ *    return host data, in which case they synchronise that stream.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument (sizes, tau <= 1/2, null pointer) */
+    LBM_ERR_CUDA = -2,     /* a CUDA call failed; see lbm_last_error */
+    LBM_ERR_OOM = -3,      /* device allocation failed */
+    LBM_ERR_UNSTABLE = -4, /* a non-finite density or velocity was detected */
+    LBM_ERR_TIMEOUT = -5,  /* a bounded device-side wait expired */
+    LBM_ERR_STATE = -6     /* wrong state size / storage tag / handle kind */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
+typedef enum { LBM_BGK = 0, LBM_SMRT = 1 } lbm_collision;
+
+/* Storage of the populations.  All modes store the deviation
+ * delta_i = fbar_i - w_i; arithmetic is FP64 for LBM_F64 and FP32 otherwise.
+ * FP16/BF16 conversions round to nearest even. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFT = 2, LBM_BF16_SHIFT = 3 } lbm_storage;
+
+typedef enum {
+    LBM_G_NONE = 0,    /* g = 0 */
+    LBM_G_UNIFORM = 1, /* g: D doubles */
+    LBM_G_ROWS = 2,    /* g: ny * D doubles, g[y][a] */
+    LBM_G_FIELD = 3    /* g: D * nz * ny * nx doubles, g[a][z][y][x] */
+} lbm_force_kind;
+
+typedef struct lbm_handle lbm_handle;
+
+typedef struct {
+    int lattice;          /* lbm_lattice */
+    int collision;        /* lbm_collision */
+    int storage;          /* lbm_storage */
+    int nx, ny, nz;       /* nz = 1 for D2Q9; nx * ny * nz < 2^31 / Q */
+    int periodic[3];      /* per axis; 0 => halfway bounce-back walls */
+    double tau[5];        /* tau per Hermite order n (index n); SMRT uses tau[2..4]
+                             (tau[0], tau[1] unused: orders 0 and 1 are conserved /
+                             fixed by the force); BGK uses tau[2] */
+    int force_kind;       /* lbm_force_kind */
+    const double *g;      /* host, layout per force_kind; copied */
+    const uint8_t *solid; /* host, nullable, nx*ny*nz bytes; copied */
+    const double *rho0;   /* host, nullable (=> 1), nx*ny*nz; copied */
+    const double *u0;     /* host, nullable (=> 0), D*nx*ny*nz; copied */
+    void *stream;         /* cudaStream_t to run on; NULL => the library makes one */
+    void *(*alloc)(size_t bytes, void *ctx); /* optional device allocator */
+    void (*free_)(void *ptr, void *ctx);     /* its release function */
+    void *alloc_ctx;
+} lbm_desc;
+
+/* Create a lattice: validates the description, allocates two population
+ * buffers, uploads g / solid / rho0 / u0 and initialises
+ *   fbar = f_eq(rho0, u0) - F(rho0, u0)/2   (zero non-equilibrium part)
+ * with the collision model's own equilibrium and force (Eq. newf with
+ * Omega_i = 0).  On failure *out is NULL. */
+lbm_status lbm_create(const lbm_desc *desc, lbm_handle **out);
+
+/* Advance nsteps time steps (fused pull-stream, collide, store; Sec. II.B-C).
+ * Asynchronous; long runs replay a captured CUDA graph. */
+lbm_status lbm_step(lbm_handle *h, int64_t nsteps);
+
+/* Macroscopic fields at the current step (Eq. half_F): rho (nx*ny*nz), u
+ * (D planes) and totals {M, Px, Py, Pz} = sums over fluid nodes of rho and
+ * rho*u (FP64, deterministic order).  Any output may be NULL.  Synchronises. */
+lbm_status lbm_moments(lbm_handle *h, double *rho, double *u, double *totals);
+
+/* Same on device pointers (FP64, same layouts); asynchronous. */
+lbm_status lbm_moments_device(lbm_handle *h, double *rho_dev, double *u_dev,
+                              double *totals_dev);
+
+/* Advance K steps and return the K-step residual
+ *   r = ||u(n) - u(n-K)||_2 / (K ||u(n)||_2)
+ * over fluid nodes, accumulated in FP64.  Returns LBM_ERR_UNSTABLE if a
+ * non-finite velocity appears.  Synchronises. */
+lbm_status lbm_residual(lbm_handle *h, int K, double *r);
+
+/* Replace the body force (same kind and layout as at creation); takes effect
+ * for the next step.  Asynchronous (the host array is copied first). */
+lbm_status lbm_set_force(lbm_handle *h, const double *g);
+
+/* Pre-collision populations fbar_i(x, t) in FP64, host layout f[i][z][y][x]
+ * (solid nodes: w_i).  Synchronises. */
+lbm_status lbm_get_populations(lbm_handle *h, double *f);
+/* Overwrite the state with the given pre-collision populations (rounded to the
+ * storage format). */
+lbm_status lbm_set_populations(lbm_handle *h, const double *f);
+
+/* Raw checkpoint of the state in the storage format (opaque layout, size
+ * lbm_state_bytes) plus the step counter; restore is bit-exact. */
+size_t lbm_state_bytes(const lbm_handle *h);
+lbm_status lbm_get_state(lbm_handle *h, void *host, size_t bytes, int64_t *step);
+lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t step);
+
+/* Information: D, Q, the step counter, and the device population buffer
+ * currently holding the state (for profiling tools; do not free). */
+lbm_status lbm_info(const lbm_handle *h, int *D, int *Q, int64_t *step, size_t *bytes_per_node);
+
+void lbm_destroy(lbm_handle *h);
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,19 @@
+"""GB300 lattice Boltzmann library: the second-order force scheme of Li, Duan &
+Shan (arXiv:2212.07494) as fused sm_103a CUDA kernels behind a C ABI.
+
+This package is a thin ctypes binding of ``include/lbm.h``: the functions
+``lbm_create`` ... ``lbm_destroy`` marshal arguments to the C entry points of
+the same names, and ``Lattice`` wraps a handle.  Every step of the update runs
+in the CUDA library; there is no CPU fallback.  If the library has not been
+built, importing the binding raises ``ImportError``; build it with
+``python -m paper_2212_07494_gb300.build``.
+
+PyTorch is optional and only supplies device memory (its caching allocator)
+and streams when a caller passes ``torch_stream=...``.
+"""
+from ._binding import (  # noqa: F401
+    LBM_BGK, LBM_SMRT, LBM_D2Q9, LBM_D3Q19, LBM_D3Q27, LBM_F64, LBM_F32, LBM_F16_SHIFT,
+    LBM_BF16_SHIFT, LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD, LbmError, Lattice,
+    lbm_create, lbm_destroy, lbm_step, lbm_moments, lbm_moments_device, lbm_residual,
+    lbm_set_force, lbm_get_populations, lbm_set_populations, lbm_state_bytes, lbm_get_state,
+    lbm_set_state, lbm_info, lbm_last_error, library, library_path, make_desc)

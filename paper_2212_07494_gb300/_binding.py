@@ -1,0 +1,319 @@
+"""ctypes marshalling for include/lbm.h.  Argument conversion only: every
+computation happens in the CUDA library ``lib/liblbm_gb300.so``."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "lib", "liblbm_gb300.so")
+
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
+LBM_BGK, LBM_SMRT = 0, 1
+LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT = 0, 1, 2, 3
+LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD = 0, 1, 2, 3
+
+_NAMES = {
+    "lattice": {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2},
+    "collision": {"BGK": 0, "SMRT": 1},
+    "storage": {"F64": 0, "F32": 1, "F16": 2, "F16_SHIFT": 2, "BF16": 3, "BF16_SHIFT": 3},
+    "force": {"none": 0, "uniform": 1, "rows": 2, "field": 3},
+}
+_DQ = {0: (2, 9), 1: (3, 19), 2: (3, 27)}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class lbm_desc(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("collision", C.c_int), ("storage", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("periodic", C.c_int * 3), ("tau", C.c_double * 5), ("force_kind", C.c_int),
+                ("g", C.POINTER(C.c_double)), ("solid", C.POINTER(C.c_uint8)),
+                ("rho0", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free_", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    """Load the CUDA library; raise ImportError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built: run `python -m paper_2212_07494_gb300.build`")
+    L = C.CDLL(_LIB_PATH)
+    H = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    L.lbm_create.argtypes = [C.POINTER(lbm_desc), C.POINTER(H)]
+    L.lbm_step.argtypes = [H, C.c_int64]
+    L.lbm_moments.argtypes = [H, dp, dp, dp]
+    L.lbm_moments_device.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.lbm_residual.argtypes = [H, C.c_int, dp]
+    L.lbm_set_force.argtypes = [H, dp]
+    L.lbm_get_populations.argtypes = [H, dp]
+    L.lbm_set_populations.argtypes = [H, dp]
+    L.lbm_state_bytes.argtypes = [H]
+    L.lbm_state_bytes.restype = C.c_size_t
+    L.lbm_get_state.argtypes = [H, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64)]
+    L.lbm_set_state.argtypes = [H, C.c_void_p, C.c_size_t, C.c_int64]
+    L.lbm_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                           C.POINTER(C.c_size_t)]
+    L.lbm_destroy.argtypes = [H]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [H]
+    L.lbm_last_error.restype = C.c_char_p
+    for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
+              "lbm_set_force", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
+              "lbm_set_state", "lbm_info"):
+        getattr(L, n).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = library().lbm_last_error(handle)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).ravel()
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _enum(kind, v):
+    return _NAMES[kind][v] if isinstance(v, str) else int(v)
+
+
+def make_desc(lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1), g=None,
+              force_kind=None, solid=None, rho0=None, u0=None, stream=None, alloc=None, free=None):
+    """Build an lbm_desc plus the arrays it points to (kept in the returned
+    ``keep`` list for as long as the descriptor is used)."""
+    lat = _enum("lattice", lattice)
+    D, Q = _DQ[lat]
+    nx, ny, nz = (list(shape) + [1, 1])[:3]
+    N = nx * ny * nz
+    if force_kind is None:
+        force_kind = "none" if g is None else "uniform"
+    fk = _enum("force", force_kind)
+    d = lbm_desc()
+    d.lattice, d.collision, d.storage = lat, _enum("collision", collision), _enum("storage", storage)
+    d.nx, d.ny, d.nz = nx, ny, nz
+    for k in range(3):
+        d.periodic[k] = int(periodic[k])
+    t = list(tau) + [1.0] * (5 - len(tau))
+    for k in range(5):
+        d.tau[k] = float(t[k])
+    d.force_kind = fk
+    keep = []
+    if fk != LBM_G_NONE:
+        n = {LBM_G_UNIFORM: D, LBM_G_ROWS: ny * D, LBM_G_FIELD: D * N}[fk]
+        ga = _f64(g, n)
+        keep.append(ga)
+        d.g = _dptr(ga)
+    if solid is not None:
+        sa = np.ascontiguousarray(np.asarray(solid, np.uint8)).ravel()
+        if sa.size != N:
+            raise ValueError("solid has the wrong size")
+        keep.append(sa)
+        d.solid = sa.ctypes.data_as(C.POINTER(C.c_uint8))
+    if rho0 is not None:
+        r = _f64(rho0, N)
+        keep.append(r)
+        d.rho0 = _dptr(r)
+    if u0 is not None:
+        u = _f64(u0, D * N)
+        keep.append(u)
+        d.u0 = _dptr(u)
+    d.stream = stream
+    if alloc is not None:
+        d.alloc, d.free_ = alloc, free
+        keep += [alloc, free]
+    return d, keep
+
+
+# ---------------------------------------------------------------- C ABI names
+def lbm_create(desc):
+    h = C.c_void_p()
+    _check(library().lbm_create(C.byref(desc), C.byref(h)))
+    return h
+
+
+def lbm_destroy(h):
+    library().lbm_destroy(h)
+
+
+def lbm_step(h, n):
+    _check(library().lbm_step(h, int(n)), h)
+
+
+def lbm_moments(h, rho, u, totals):
+    _check(library().lbm_moments(h, _dptr(rho), _dptr(u), _dptr(totals)), h)
+
+
+def lbm_moments_device(h, rho_ptr, u_ptr, totals_ptr):
+    _check(library().lbm_moments_device(h, rho_ptr, u_ptr, totals_ptr), h)
+
+
+def lbm_residual(h, K):
+    r = C.c_double()
+    _check(library().lbm_residual(h, int(K), C.byref(r)), h)
+    return r.value
+
+
+def lbm_set_force(h, g):
+    _check(library().lbm_set_force(h, _dptr(g)), h)
+
+
+def lbm_get_populations(h, out):
+    _check(library().lbm_get_populations(h, _dptr(out)), h)
+
+
+def lbm_set_populations(h, f):
+    _check(library().lbm_set_populations(h, _dptr(f)), h)
+
+
+def lbm_state_bytes(h):
+    return int(library().lbm_state_bytes(h))
+
+
+def lbm_get_state(h, buf):
+    step = C.c_int64()
+    _check(library().lbm_get_state(h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, C.byref(step)), h)
+    return step.value
+
+
+def lbm_set_state(h, buf, step):
+    _check(library().lbm_set_state(h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, int(step)), h)
+
+
+def lbm_info(h):
+    D, Q, s, b = C.c_int(), C.c_int(), C.c_int64(), C.c_size_t()
+    _check(library().lbm_info(h, C.byref(D), C.byref(Q), C.byref(s), C.byref(b)), h)
+    return D.value, Q.value, s.value, b.value
+
+
+def lbm_last_error(h=None):
+    m = library().lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+class Lattice:
+    """One lattice handle.  Arrays are numpy, SoA, x fastest (see lbm.h).
+
+    torch_stream: a ``torch.cuda.Stream`` to run on; with it the handle also
+    allocates through PyTorch's caching allocator.  Otherwise the library
+    creates its own stream and uses cudaMalloc."""
+
+    def __init__(self, lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1), g=None,
+                 force_kind=None, solid=None, rho0=None, u0=None, torch_stream=None):
+        self.lattice = _enum("lattice", lattice)
+        self.D, self.Q = _DQ[self.lattice]
+        nx, ny, nz = (list(shape) + [1, 1])[:3]
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self._cb = []
+        stream = None
+        alloc = free = None
+        if torch_stream is not None:
+            import torch
+            self._torch_stream = torch_stream
+            stream = torch_stream.cuda_stream
+            dev = torch_stream.device
+
+            def _alloc(nbytes, ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, torch_stream)
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            alloc, free = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._cb = [alloc, free]
+        desc, keep = make_desc(lattice, collision, shape, tau, storage, periodic, g, force_kind,
+                               solid, rho0, u0, stream, alloc, free)
+        self.force_kind = desc.force_kind
+        self.h = lbm_create(desc)
+        del keep
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self):
+        rho = np.empty(self.N)
+        u = np.empty(self.D * self.N)
+        tot = np.empty(4)
+        lbm_moments(self.h, rho, u, tot)
+        return rho.reshape(self.shape), u.reshape((self.D,) + self.shape), tot
+
+    def totals(self):
+        tot = np.empty(4)
+        lbm_moments(self.h, None, None, tot)
+        return tot
+
+    def residual(self, K):
+        return lbm_residual(self.h, K)
+
+    def set_force(self, g):
+        lbm_set_force(self.h, _f64(g))
+
+    def populations(self):
+        f = np.empty(self.Q * self.N)
+        lbm_get_populations(self.h, f)
+        return f.reshape((self.Q,) + self.shape)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.h, _f64(f, self.Q * self.N))
+
+    def state(self):
+        buf = np.empty(lbm_state_bytes(self.h), np.uint8)
+        step = lbm_get_state(self.h, buf)
+        return buf, step
+
+    def set_state(self, buf, step):
+        lbm_set_state(self.h, np.ascontiguousarray(buf), step)
+
+    def info(self):
+        return lbm_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,426 @@
+// lbm_device.cuh -- device building blocks of the fused lattice Boltzmann
+// update with the second-order force scheme (arXiv:2212.07494).
+//
+// Populations are kept as deviations delta_i = fbar_i - w_i, structure of
+// arrays f[i][z][y][xp] with rows padded to nxp elements.  The SMRT collision
+// works on the 3 x 3 (x 3) velocity grid of the tensor-product lattices
+// (D2Q9 = D1Q3^2, D3Q27 = D1Q3^3; D3Q19 = D3Q27 without its 8 corners) and
+// runs every moment transform as three-point passes along one axis at a time:
+//   project  (Hermite moments h0 = 1, h1 = c, h2 = c^2 - 1/3; Eq. dft)
+//   shift by -u   (raw -> central moments, the Hermite addition theorem)
+//   relax    (order by order, d_p^(n) = (1 - 1/tau_n) d_1^(n); d_p^(1) = F/2)
+//   shift by +u   (central -> raw, Eq. bbd1 in closed binomial form)
+//   truncate to the retained components and reconstruct (Sec. II.C).
+// In lattice units the reconstruction coefficients per axis are
+// r0 = 1, r1 = 3c, r2 = 4.5 c^2 - 1.5.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
+enum { BGK = 0, SMRT = 1 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+enum { G_NONE = 0, G_UNIFORM = 1, G_ROWS = 2, G_FIELD = 3 };
+
+// ---------------------------------------------------------------- lattices
+template <int L> struct Lat;
+
+template <> struct Lat<D2Q9> {
+    static constexpr int D = 2, Q = 9, NG = 9;
+    __host__ __device__ static constexpr int cx(int i) {
+        return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+};
+
+// D3Q27 order: rest; 6 faces; 12 edges; 8 corners, opposite pairs adjacent.
+struct C3 {
+    __host__ __device__ static constexpr int c(int i, int a) {
+        // rows of the table (cx, cy, cz)
+        return i == 0 ? 0
+             : i == 1 ? (a == 0 ? 1 : 0)
+             : i == 2 ? (a == 0 ? -1 : 0)
+             : i == 3 ? (a == 1 ? 1 : 0)
+             : i == 4 ? (a == 1 ? -1 : 0)
+             : i == 5 ? (a == 2 ? 1 : 0)
+             : i == 6 ? (a == 2 ? -1 : 0)
+             : i == 7 ? (a == 2 ? 0 : 1)
+             : i == 8 ? (a == 2 ? 0 : -1)
+             : i == 9 ? (a == 0 ? 1 : (a == 1 ? -1 : 0))
+             : i == 10 ? (a == 0 ? -1 : (a == 1 ? 1 : 0))
+             : i == 11 ? (a == 1 ? 0 : 1)
+             : i == 12 ? (a == 1 ? 0 : -1)
+             : i == 13 ? (a == 0 ? 1 : (a == 2 ? -1 : 0))
+             : i == 14 ? (a == 0 ? -1 : (a == 2 ? 1 : 0))
+             : i == 15 ? (a == 0 ? 0 : 1)
+             : i == 16 ? (a == 0 ? 0 : -1)
+             : i == 17 ? (a == 1 ? 1 : (a == 2 ? -1 : 0))
+             : i == 18 ? (a == 1 ? -1 : (a == 2 ? 1 : 0))
+             : i == 19 ? 1
+             : i == 20 ? -1
+             : i == 21 ? (a == 2 ? -1 : 1)
+             : i == 22 ? (a == 2 ? 1 : -1)
+             : i == 23 ? (a == 1 ? -1 : 1)
+             : i == 24 ? (a == 1 ? 1 : -1)
+             : i == 25 ? (a == 0 ? -1 : 1)
+             : (a == 0 ? 1 : -1);
+    }
+};
+
+template <> struct Lat<D3Q19> {
+    static constexpr int D = 3, Q = 19, NG = 27;
+    __host__ __device__ static constexpr int cx(int i) { return C3::c(i, 0); }
+    __host__ __device__ static constexpr int cy(int i) { return C3::c(i, 1); }
+    __host__ __device__ static constexpr int cz(int i) { return C3::c(i, 2); }
+};
+template <> struct Lat<D3Q27> {
+    static constexpr int D = 3, Q = 27, NG = 27;
+    __host__ __device__ static constexpr int cx(int i) { return C3::c(i, 0); }
+    __host__ __device__ static constexpr int cy(int i) { return C3::c(i, 1); }
+    __host__ __device__ static constexpr int cz(int i) { return C3::c(i, 2); }
+};
+
+template <int L> __host__ __device__ constexpr int opp(int i) {
+    // opposite pairs: D2Q9 (1,3) (2,4) (5,7) (6,8); 3-D: (2k-1, 2k)
+    return L == D2Q9 ? (i == 0 ? 0 : (i <= 4 ? (i <= 2 ? i + 2 : i - 2) : (i <= 6 ? i + 2 : i - 2)))
+                     : (i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1));
+}
+
+__host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+template <int L> __host__ __device__ constexpr double weight(int i) {
+    return L == D3Q19
+        ? ((Lat<L>::cx(i) != 0) + (Lat<L>::cy(i) != 0) + (Lat<L>::cz(i) != 0) == 0 ? 1.0 / 3.0
+           : (Lat<L>::cx(i) != 0) + (Lat<L>::cy(i) != 0) + (Lat<L>::cz(i) != 0) == 1 ? 1.0 / 18.0
+                                                                                    : 1.0 / 36.0)
+        : w1d(Lat<L>::cx(i)) * w1d(Lat<L>::cy(i)) * (Lat<L>::D == 3 ? w1d(Lat<L>::cz(i)) : 1.0);
+}
+
+// grid position of population i on the 3^D velocity grid: (c + 1) per axis
+template <int L> __host__ __device__ constexpr int gpos(int i) {
+    return (Lat<L>::cx(i) + 1) + 3 * (Lat<L>::cy(i) + 1) + (Lat<L>::D == 3 ? 9 * (Lat<L>::cz(i) + 1) : 0);
+}
+
+// moment index digits on the grid (order m_a per axis)
+template <int D> __host__ __device__ constexpr int mdig(int g, int a) { return (a == 0 ? g : (a == 1 ? g / 3 : g / 9)) % 3; }
+template <int D> __host__ __device__ constexpr int morder(int g) {
+    return mdig<D>(g, 0) + mdig<D>(g, 1) + (D == 3 ? mdig<D>(g, 2) : 0);
+}
+template <int D> __host__ __device__ constexpr int maxdig(int g) {
+    return mdig<D>(g, 0) > mdig<D>(g, 1)
+               ? (D == 3 && mdig<D>(g, 2) > mdig<D>(g, 0) ? mdig<D>(g, 2) : mdig<D>(g, 0))
+               : (D == 3 && mdig<D>(g, 2) > mdig<D>(g, 1) ? mdig<D>(g, 2) : mdig<D>(g, 1));
+}
+// retained Hermite components: D2Q9 all nine; D3Q27 total order <= 4;
+// D3Q19 orders <= 2 and the (2,1,0)-type third-order components
+template <int L> __host__ __device__ constexpr bool retained(int g) {
+    return L == D2Q9 ? true
+         : L == D3Q27 ? morder<3>(g) <= 4
+                      : (morder<3>(g) <= 2 || (morder<3>(g) == 3 && maxdig<3>(g) == 2));
+}
+template <int L> __host__ __device__ constexpr bool on_lattice(int g) {
+    // D3Q19 has no (+-1, +-1, +-1) velocities
+    return L != D3Q19 || !((g % 3) != 1 && ((g / 3) % 3) != 1 && (g / 9) != 1);
+}
+
+// ------------------------------------------------------------- storage codec
+template <int ST> struct Store;
+template <> struct Store<ST_F64> {
+    typedef double T;
+    typedef double R;
+    __device__ static R ld(const T *p) { return __ldg(p); }
+    __device__ static void st(T *p, R v) { *p = v; }
+};
+template <> struct Store<ST_F32> {
+    typedef float T;
+    typedef float R;
+    __device__ static R ld(const T *p) { return __ldg(p); }
+    __device__ static void st(T *p, R v) { *p = v; }
+};
+template <> struct Store<ST_F16> {
+    typedef __half T;
+    typedef float R;
+    __device__ static R ld(const T *p) { return __half2float(__ldg(p)); }
+    __device__ static void st(T *p, R v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<ST_BF16> {
+    typedef __nv_bfloat16 T;
+    typedef float R;
+    __device__ static R ld(const T *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st(T *p, R v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------------ kernel params
+struct KParams {
+    int nx, ny, nz, nxp;
+    long long plane;               // elements per population plane (nxp*ny*nz)
+    int per[3];                    // periodic flags
+    int force_kind;                // G_*
+    const double *g;               // uniform [3] | rows [ny][D] | field [D][plane]
+    const unsigned char *solid;    // [plane] or null
+    double om[5];                  // 1 / tau_n
+};
+
+// --------------------------------------------------------- moment-space passes
+// All passes act in place on a 3^D array indexed by grid position / moment
+// order, along axis AX (stride 3^AX).
+template <int D> struct Grid { static constexpr int N = D == 2 ? 9 : 27; };
+
+template <int D, int AX, typename R, typename F>
+__device__ __forceinline__ void for_lines(R *a, F f) {
+    constexpr int S = AX == 0 ? 1 : (AX == 1 ? 3 : 9);
+#pragma unroll
+    for (int g = 0; g < Grid<D>::N; ++g) {
+        if ((g / S) % 3 == 0) f(a[g], a[g + S], a[g + 2 * S]);
+    }
+}
+
+// populations (c = -1, 0, +1) -> moments (h0, h1, h2) on one line
+template <typename R> __device__ __forceinline__ void proj_line(R &m, R &z, R &p) {
+    const R s = p + m, d = p - m;
+    const R m0 = s + z;
+    const R m2 = (R(2) * s - z) * R(1.0 / 3.0);
+    m = m0;
+    z = d;
+    p = m2;
+}
+// shift a line of moments (h0, h1, h2) by velocity v: Hermite addition theorem
+template <typename R> __device__ __forceinline__ void shift_line(R &a0, R &a1, R &a2, R v) {
+    a2 = a2 + v * (R(2) * a1 + v * a0);
+    a1 = a1 + v * a0;
+}
+// moments (t0, t1, t2) -> populations with the D1Q3 weight folded in
+template <typename R> __device__ __forceinline__ void recon_line_w(R &t0, R &t1, R &t2) {
+    const R a = t0 + R(3) * t2, b = R(3) * t1;
+    const R fz = R(2.0 / 3.0) * (t0 - R(1.5) * t2);
+    t0 = R(1.0 / 6.0) * (a - b);
+    t2 = R(1.0 / 6.0) * (a + b);
+    t1 = fz;
+}
+template <typename R> __device__ __forceinline__ void recon_line(R &t0, R &t1, R &t2) {
+    const R a = t0 + R(3) * t2, b = R(3) * t1;
+    const R fz = t0 - R(1.5) * t2;
+    t0 = a - b;
+    t2 = a + b;
+    t1 = fz;
+}
+
+template <int D, typename R> __device__ __forceinline__ void project(R *a) {
+    for_lines<D, 0>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
+    for_lines<D, 1>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
+    if (D == 3) for_lines<D, 2>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
+}
+template <int D, typename R> __device__ __forceinline__ void shift(R *a, R ux, R uy, R uz) {
+    for_lines<D, 0>(a, [ux](R &x, R &y, R &z) { shift_line(x, y, z, ux); });
+    for_lines<D, 1>(a, [uy](R &x, R &y, R &z) { shift_line(x, y, z, uy); });
+    if (D == 3) for_lines<D, 2>(a, [uz](R &x, R &y, R &z) { shift_line(x, y, z, uz); });
+}
+template <int L, typename R> __device__ __forceinline__ void reconstruct(R *a) {
+    constexpr int D = Lat<L>::D;
+    if (L == D3Q19) {
+        for_lines<D, 0>(a, [](R &x, R &y, R &z) { recon_line(x, y, z); });
+        for_lines<D, 1>(a, [](R &x, R &y, R &z) { recon_line(x, y, z); });
+        for_lines<D, 2>(a, [](R &x, R &y, R &z) { recon_line(x, y, z); });
+    } else {
+        for_lines<D, 0>(a, [](R &x, R &y, R &z) { recon_line_w(x, y, z); });
+        for_lines<D, 1>(a, [](R &x, R &y, R &z) { recon_line_w(x, y, z); });
+        if (D == 3) for_lines<D, 2>(a, [](R &x, R &y, R &z) { recon_line_w(x, y, z); });
+    }
+}
+
+// ------------------------------------------------------------------ collisions
+// G holds the deviations delta on the velocity grid (zeros off-lattice) and is
+// overwritten with the post-collision deviations.  g: acceleration (lattice
+// units).  Returns nothing; rho/u are recomputed by the moments kernel.
+template <int L, typename R>
+__device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+    constexpr int D = Lat<L>::D;
+    constexpr int N = Grid<D>::N;
+    constexpr int EX = 1, EY = 3, EZ = 9;
+    project<D>(G);
+    const R drho = G[0];                 // rho - 1 (moments of w vanish beyond order 0)
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = G[EX] * inv + R(0.5) * gx;   // Eq. (half_F)
+    const R uy = G[EY] * inv + R(0.5) * gy;
+    const R uz = D == 3 ? G[EZ] * inv + R(0.5) * gz : R(0);
+    G[0] = rho;
+    shift<D>(G, -ux, -uy, -uz);           // central moments of fbar
+    // relaxation of the non-equilibrium central moments (equilibrium ones are
+    // rho delta_{n0}); the force enters at first order only: d_p^(1) = rho g/2
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+        const int n = morder<D>(g);
+        if (n == 2) G[g] *= (R(1) - om2);
+        else if (n == 3) G[g] *= (R(1) - om3);
+        else if (n == 4) G[g] *= (R(1) - om4);
+        else if (n >= 5) G[g] = R(0);
+    }
+    G[0] = rho;
+    G[EX] = R(0.5) * rho * gx;
+    G[EY] = R(0.5) * rho * gy;
+    if (D == 3) G[EZ] = R(0.5) * rho * gz;
+    shift<D>(G, ux, uy, uz);              // back to raw moments: a_0 + a_p
+#pragma unroll
+    for (int g = 0; g < N; ++g)
+        if (!retained<L>(g)) G[g] = R(0);
+    G[0] = drho;                          // deviation from the weights
+    reconstruct<L>(G);
+    if (L == D3Q19) {
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) G[gpos<L>(i)] *= R(weight<L>(i));
+    }
+}
+
+// BGK with the second-order equilibrium and Guo-form force, Eq. (explict_eq)
+template <int L, typename R>
+__device__ __forceinline__ void collide_bgk(R *G, R gx, R gy, R gz, R om) {
+    constexpr int Q = Lat<L>::Q;
+    constexpr int D = Lat<L>::D;
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R v = G[gpos<L>(i)];
+        drho += v;
+        if (Lat<L>::cx(i)) jx += Lat<L>::cx(i) > 0 ? v : -v;
+        if (Lat<L>::cy(i)) jy += Lat<L>::cy(i) > 0 ? v : -v;
+        if (D == 3 && Lat<L>::cz(i)) jz += Lat<L>::cz(i) > 0 ? v : -v;
+    }
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = jx * inv + R(0.5) * gx, uy = jy * inv + R(0.5) * gy;
+    const R uz = D == 3 ? jz * inv + R(0.5) * gz : R(0);
+    const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R gu = gx * ux + gy * uy + gz * uz;
+    const R fk = (R(1) - R(0.5) * om) * rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = Lat<L>::cx(i), cy = Lat<L>::cy(i), cz = Lat<L>::cz(i);
+        const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+        const R cg = R(cx) * gx + R(cy) * gy + R(cz) * gz;
+        const R w = R(weight<L>(i));
+        const R deq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - uu15));
+        const R Fi = w * fk * (R(3) * (cg - gu) + R(9) * cu * cg);
+        R &v = G[gpos<L>(i)];
+        v = v + om * (deq - v) + Fi;
+    }
+}
+
+// initial deviations fbar - w = f_eq(rho, u) - F/2 - w for the model's own
+// equilibrium and force; G receives the grid values
+template <int L, int COLL, typename R>
+__device__ __forceinline__ void initial_state(R *G, R drho, R ux, R uy, R uz, R gx, R gy, R gz) {
+    constexpr int D = Lat<L>::D;
+    constexpr int N = Grid<D>::N;
+    const R rho = R(1) + drho;
+    if (COLL == BGK) {
+        const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+        const R gu = gx * ux + gy * uy + gz * uz;
+#pragma unroll
+        for (int g = 0; g < N; ++g) G[g] = R(0);
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) {
+            const int cx = Lat<L>::cx(i), cy = Lat<L>::cy(i), cz = Lat<L>::cz(i);
+            const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+            const R cg = R(cx) * gx + R(cy) * gy + R(cz) * gz;
+            const R w = R(weight<L>(i));
+            G[gpos<L>(i)] = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - uu15)) -
+                            R(0.5) * w * rho * (R(3) * (cg - gu) + R(9) * cu * cg);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < N; ++g) G[g] = R(0);
+        G[0] = rho;
+        G[1] = -R(0.5) * rho * gx;
+        G[3] = -R(0.5) * rho * gy;
+        if (D == 3) G[9] = -R(0.5) * rho * gz;
+        shift<D>(G, ux, uy, uz);
+#pragma unroll
+        for (int g = 0; g < N; ++g)
+            if (!retained<L>(g)) G[g] = R(0);
+        G[0] = drho;
+        reconstruct<L>(G);
+        if (L == D3Q19) {
+#pragma unroll
+            for (int i = 0; i < Lat<L>::Q; ++i) G[gpos<L>(i)] *= R(weight<L>(i));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ indexing
+struct NodeNbr {
+    int xs[3], ys[3], zs[3];   // source coordinate for c = -1, 0, +1 (x - c)
+    bool xw[3], yw[3], zw[3];  // true when x - c lies beyond a wall
+};
+
+__device__ __forceinline__ void axis_src(int x, int n, int per, int *s, bool *w) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int c = k - 1;
+        int v = x - c;
+        bool wall = false;
+        if (v < 0) { if (per) v += n; else { wall = true; v = 0; } }
+        else if (v >= n) { if (per) v -= n; else { wall = true; v = n - 1; } }
+        s[k] = v;
+        w[k] = wall;
+    }
+}
+
+__device__ __forceinline__ void node_nbr(const KParams &p, int x, int y, int z, NodeNbr &nb) {
+    axis_src(x, p.nx, p.per[0], nb.xs, nb.xw);
+    axis_src(y, p.ny, p.per[1], nb.ys, nb.yw);
+    axis_src(z, p.nz, p.per[2], nb.zs, nb.zw);
+}
+
+__device__ __forceinline__ long long node_index(const KParams &p, int x, int y, int z) {
+    return ((long long)z * p.ny + y) * p.nxp + x;
+}
+
+// pull the pre-collision deviations of node (x,y,z) onto the velocity grid:
+// delta_i(x) = P_i(x - c_i), or P_opp(i)(x) across a wall or a solid node
+template <int L, int ST, bool MASK>
+__device__ __forceinline__ void gather(const KParams &p, const typename Store<ST>::T *__restrict__ f,
+                                       int x, int y, int z, typename Store<ST>::R *G) {
+    typedef typename Store<ST>::R R;
+    NodeNbr nb;
+    node_nbr(p, x, y, z, nb);
+    const long long own = node_index(p, x, y, z);
+#pragma unroll
+    for (int g = 0; g < Grid<Lat<L>::D>::N; ++g) G[g] = R(0);
+#pragma unroll
+    for (int i = 0; i < Lat<L>::Q; ++i) {
+        const int kx = Lat<L>::cx(i) + 1, ky = Lat<L>::cy(i) + 1, kz = Lat<L>::cz(i) + 1;
+        bool wall = nb.xw[kx] || nb.yw[ky] || (Lat<L>::D == 3 && nb.zw[kz]);
+        const long long src = node_index(p, nb.xs[kx], nb.ys[ky], Lat<L>::D == 3 ? nb.zs[kz] : z);
+        if (MASK && i != 0 && !wall) wall = p.solid[src] != 0;
+        const long long idx = wall ? (long long)opp<L>(i) * p.plane + own : (long long)i * p.plane + src;
+        G[gpos<L>(i)] = Store<ST>::ld(f + idx);
+    }
+}
+
+template <int L, typename R>
+__device__ __forceinline__ void load_force(const KParams &p, int y, long long node, R &gx, R &gy, R &gz) {
+    constexpr int D = Lat<L>::D;
+    gx = gy = gz = R(0);
+    if (p.force_kind == G_UNIFORM) {
+        gx = R(__ldg(p.g + 0));
+        gy = R(__ldg(p.g + 1));
+        if (D == 3) gz = R(__ldg(p.g + 2));
+    } else if (p.force_kind == G_ROWS) {
+        gx = R(__ldg(p.g + (long long)y * D + 0));
+        gy = R(__ldg(p.g + (long long)y * D + 1));
+        if (D == 3) gz = R(__ldg(p.g + (long long)y * D + 2));
+    } else if (p.force_kind == G_FIELD) {
+        gx = R(__ldg(p.g + node));
+        gy = R(__ldg(p.g + p.plane + node));
+        if (D == 3) gz = R(__ldg(p.g + 2 * p.plane + node));
+    }
+}
+
+}  // namespace lbm

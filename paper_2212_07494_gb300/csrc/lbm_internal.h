@@ -1,0 +1,48 @@
+// lbm_internal.h -- host-side interface between the C ABI runtime and the
+// per-lattice kernel launchers.  Plain CUDA runtime types only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// number of doubles each moments block writes to the partial-sum scratch:
+// {M, Px, Py, Pz, residual numerator, residual denominator, non-finite count}
+constexpr int kPartials = 7;
+constexpr int kMomBlock = 256;
+
+struct StepCfg {
+    int bdx;  // threads per block along x
+    int npt;  // nodes per thread (strided by bdx)
+};
+
+struct Launchers {
+    cudaError_t (*step)(int coll, int st, bool mask, StepCfg cfg, const KParams &p, const void *fin,
+                        void *fout, cudaStream_t s);
+    // rho/u (unpadded FP64, nullable), partials [nblocks * kPartials];
+    // uprev (unpadded FP64 D planes, nullable): residual against it and update
+    cudaError_t (*moments)(int st, bool mask, const KParams &p, const void *f, double *rho, double *u,
+                           double *partials, double *uprev, cudaStream_t s, int *nblocks);
+    cudaError_t (*init)(int coll, int st, bool mask, const KParams &p, const double *rho0,
+                        const double *u0, void *target, cudaStream_t s);
+    cudaError_t (*unstream)(int st, bool mask, const KParams &p, const void *target, void *state,
+                            cudaStream_t s);
+    cudaError_t (*get_pops)(int st, bool mask, const KParams &p, const void *state, double *out,
+                            cudaStream_t s);
+    cudaError_t (*put_pops)(int st, const KParams &p, const double *in, void *target, cudaStream_t s);
+};
+
+const Launchers &launchers_d2q9();
+const Launchers &launchers_d3q19();
+const Launchers &launchers_d3q27();
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s);
+
+inline dim3 node_grid(const KParams &p, int bdx, int npt) {
+    return dim3((unsigned)((p.nx + bdx * npt - 1) / (bdx * npt)), (unsigned)p.ny, (unsigned)p.nz);
+}
+
+}  // namespace lbm

@@ -1,0 +1,346 @@
+// lbm_kernels.cuh -- the fused stream-collide kernel and its companions
+// (initialisation, moments with FP64 reductions, population import/export),
+// templated on lattice, collision, storage and obstacle mask.  Each lattice
+// instantiates them in its own translation unit.
+#pragma once
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Fused pull-stream + collide + store for NPT nodes per thread along x
+// (strided by blockDim.x so every load instruction of a warp is a contiguous
+// row segment).  Loads for all NPT nodes are issued before any arithmetic.
+template <int L, int COLL, int ST, bool MASK, int NPT>
+__global__ void __launch_bounds__(256) k_step(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+                                              typename Store<ST>::T *__restrict__ fout) {
+    typedef typename Store<ST>::R R;
+    constexpr int NG = Grid<Lat<L>::D>::N;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x0 = blockIdx.x * blockDim.x * NPT + threadIdx.x;
+    R G[NPT][NG];
+    bool act[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + k * blockDim.x;
+        act[k] = x < p.nx;
+        if (MASK && act[k]) act[k] = p.solid[node_index(p, x, y, z)] == 0;
+        if (act[k]) gather<L, ST, MASK>(p, fin, x, y, z, G[k]);
+    }
+    const R om2 = R(p.om[2]), om3 = R(p.om[3]), om4 = R(p.om[4]);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        if (!act[k]) continue;
+        const int x = x0 + k * blockDim.x;
+        const long long own = node_index(p, x, y, z);
+        R gx, gy, gz;
+        load_force<L>(p, y, own, gx, gy, gz);
+        if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4);
+        else collide_bgk<L>(G[k], gx, gy, gz, om2);
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i)
+            Store<ST>::st(fout + (long long)i * p.plane + own, G[k][gpos<L>(i)]);
+    }
+}
+
+// warp + block reduction of NV doubles; thread 0 of the block gets the sums
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sh[kMomBlock / 32][NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][k];
+            v[k] = s;
+        }
+    }
+}
+
+// Macroscopic fields of the current state (Eq. half_F): rho and u written in
+// the unpadded FP64 layout; per-block FP64 partial sums of rho, rho u and,
+// when uprev is given, of |u - uprev|^2 and |u|^2 (uprev is then updated).
+template <int L, int ST, bool MASK>
+__global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const typename Store<ST>::T *__restrict__ f,
+                                                       double *rho_out, double *u_out, double *partials,
+                                                       double *uprev) {
+    constexpr int D = Lat<L>::D;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[kPartials] = {0, 0, 0, 0, 0, 0, 0};
+    if (x < p.nx) {
+        const long long own = node_index(p, x, y, z);
+        const long long n = ((long long)z * p.ny + y) * p.nx + x;
+        const long long N = (long long)p.nx * p.ny * p.nz;
+        double rho = 1.0, u[3] = {0.0, 0.0, 0.0};
+        const bool fluid = !MASK || p.solid[own] == 0;
+        if (fluid) {
+            double Gd[Grid<D>::N];
+            {
+                typename Store<ST>::R G[Grid<D>::N];
+                gather<L, ST, MASK>(p, f, x, y, z, G);
+#pragma unroll
+                for (int g = 0; g < Grid<D>::N; ++g) Gd[g] = (double)G[g];
+            }
+            double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int i = 0; i < Lat<L>::Q; ++i) {
+                const double w = Gd[gpos<L>(i)];
+                drho += w;
+                j[0] += Lat<L>::cx(i) * w;
+                j[1] += Lat<L>::cy(i) * w;
+                if (D == 3) j[2] += Lat<L>::cz(i) * w;
+            }
+            rho = 1.0 + drho;
+            double gx, gy, gz;
+            load_force<L>(p, y, own, gx, gy, gz);
+            const double g3[3] = {gx, gy, gz};
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = j[a] / rho + 0.5 * g3[a];
+            v[0] = rho;
+#pragma unroll
+            for (int a = 0; a < D; ++a) v[1 + a] = rho * u[a];
+            bool finite = isfinite(rho);
+#pragma unroll
+            for (int a = 0; a < D; ++a) finite = finite && isfinite(u[a]);
+            v[6] = finite ? 0.0 : 1.0;
+            if (uprev) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const double d = u[a] - uprev[a * N + n];
+                    v[4] += d * d;
+                    v[5] += u[a] * u[a];
+                    uprev[a * N + n] = u[a];
+                }
+            }
+        }
+        if (rho_out) rho_out[n] = rho;
+        if (u_out)
+#pragma unroll
+            for (int a = 0; a < D; ++a) u_out[a * N + n] = u[a];
+    }
+    block_sum(v);
+    if (threadIdx.x == 0) {
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < kPartials; ++k) partials[b * kPartials + k] = v[k];
+    }
+}
+
+// Target pre-collision state at every node (fbar = f_eq - F/2, deviations),
+// written at the node's own position; solid nodes get zero deviation.
+template <int L, int COLL, int ST, bool MASK>
+__global__ void k_init(const KParams p, const double *__restrict__ rho0, const double *__restrict__ u0,
+                       typename Store<ST>::T *__restrict__ target) {
+    typedef typename Store<ST>::R R;
+    constexpr int D = Lat<L>::D;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const long long own = node_index(p, x, y, z);
+    const long long n = ((long long)z * p.ny + y) * p.nx + x;
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    R G[Grid<D>::N];
+    if (MASK && p.solid[own]) {
+#pragma unroll
+        for (int g = 0; g < Grid<D>::N; ++g) G[g] = R(0);
+    } else {
+        const R drho = rho0 ? R(rho0[n] - 1.0) : R(0);
+        const R ux = u0 ? R(u0[n]) : R(0);
+        const R uy = u0 ? R(u0[N + n]) : R(0);
+        const R uz = (u0 && D == 3) ? R(u0[2 * N + n]) : R(0);
+        R gx, gy, gz;
+        load_force<L>(p, y, own, gx, gy, gz);
+        initial_state<L, COLL>(G, drho, ux, uy, uz, gx, gy, gz);
+    }
+#pragma unroll
+    for (int i = 0; i < Lat<L>::Q; ++i) Store<ST>::st(target + (long long)i * p.plane + own, G[gpos<L>(i)]);
+}
+
+// Inverse of the pull: state P such that pulling it reproduces the target T,
+//   P_j(y) = T_j(y + c_j)   or   T_opp(j)(y) when y + c_j is a wall or solid.
+template <int L, int ST, bool MASK>
+__global__ void k_unstream(const KParams p, const typename Store<ST>::T *__restrict__ T,
+                           typename Store<ST>::T *__restrict__ P) {
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const long long own = node_index(p, x, y, z);
+    if (MASK && p.solid[own]) return;
+    NodeNbr nb;
+    node_nbr(p, x, y, z, nb);
+#pragma unroll
+    for (int j = 0; j < Lat<L>::Q; ++j) {
+        // destination x + c_j is the source entry for c = -c_j: index 1 - c_j
+        const int kx = 1 - Lat<L>::cx(j), ky = 1 - Lat<L>::cy(j), kz = 1 - Lat<L>::cz(j);
+        bool wall = nb.xw[kx] || nb.yw[ky] || (Lat<L>::D == 3 && nb.zw[kz]);
+        const long long dst = node_index(p, nb.xs[kx], nb.ys[ky], Lat<L>::D == 3 ? nb.zs[kz] : z);
+        if (MASK && j != 0 && !wall) wall = p.solid[dst] != 0;
+        const long long idx = wall ? (long long)opp<L>(j) * p.plane + own : (long long)j * p.plane + dst;
+        P[(long long)j * p.plane + own] = T[idx];
+    }
+}
+
+// Pre-collision populations fbar = w + delta in FP64, unpadded [Q][N]
+template <int L, int ST, bool MASK>
+__global__ void k_get_pops(const KParams p, const typename Store<ST>::T *__restrict__ f, double *__restrict__ out) {
+    typedef typename Store<ST>::R R;
+    constexpr int D = Lat<L>::D;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const long long own = node_index(p, x, y, z);
+    const long long n = ((long long)z * p.ny + y) * p.nx + x;
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    R G[Grid<D>::N];
+    const bool fluid = !MASK || p.solid[own] == 0;
+    if (fluid) gather<L, ST, MASK>(p, f, x, y, z, G);
+#pragma unroll
+    for (int i = 0; i < Lat<L>::Q; ++i)
+        out[(long long)i * N + n] = weight<L>(i) + (fluid ? (double)G[gpos<L>(i)] : 0.0);
+}
+
+// Encode FP64 populations (unpadded [Q][N]) as storage deviations at their
+// own position (a target for k_unstream)
+template <int L, int ST>
+__global__ void k_put_pops(const KParams p, const double *__restrict__ in, typename Store<ST>::T *__restrict__ T) {
+    typedef typename Store<ST>::R R;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const long long own = node_index(p, x, y, z);
+    const long long n = ((long long)z * p.ny + y) * p.nx + x;
+    const long long N = (long long)p.nx * p.ny * p.nz;
+#pragma unroll
+    for (int i = 0; i < Lat<L>::Q; ++i)
+        Store<ST>::st(T + (long long)i * p.plane + own, R(in[(long long)i * N + n] - weight<L>(i)));
+}
+
+// ------------------------------------------------------------ host dispatch
+template <int L> struct Dispatch {
+    template <int COLL, int ST, bool MASK, int NPT>
+    static cudaError_t step_t(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        typedef typename Store<ST>::T T;
+        k_step<L, COLL, ST, MASK, NPT><<<node_grid(p, cfg.bdx, NPT), cfg.bdx, 0, s>>>(
+            p, (const T *)fin, (T *)fout);
+        return cudaGetLastError();
+    }
+    template <int COLL, int ST, bool MASK>
+    static cudaError_t step_n(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        if (cfg.npt == 2) return step_t<COLL, ST, MASK, 2>(cfg, p, fin, fout, s);
+        return step_t<COLL, ST, MASK, 1>(cfg, p, fin, fout, s);
+    }
+    template <int COLL, int ST>
+    static cudaError_t step_m(bool mask, StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        return mask ? step_n<COLL, ST, true>(cfg, p, fin, fout, s) : step_n<COLL, ST, false>(cfg, p, fin, fout, s);
+    }
+    template <int COLL>
+    static cudaError_t step_s(int st, bool mask, StepCfg cfg, const KParams &p, const void *fin, void *fout,
+                              cudaStream_t s) {
+        switch (st) {
+        case ST_F64: return step_m<COLL, ST_F64>(mask, cfg, p, fin, fout, s);
+        case ST_F32: return step_m<COLL, ST_F32>(mask, cfg, p, fin, fout, s);
+        case ST_F16: return step_m<COLL, ST_F16>(mask, cfg, p, fin, fout, s);
+        case ST_BF16: return step_m<COLL, ST_BF16>(mask, cfg, p, fin, fout, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t step(int coll, int st, bool mask, StepCfg cfg, const KParams &p, const void *fin,
+                            void *fout, cudaStream_t s) {
+        return coll == SMRT ? step_s<SMRT>(st, mask, cfg, p, fin, fout, s)
+                            : step_s<BGK>(st, mask, cfg, p, fin, fout, s);
+    }
+
+    template <int ST, bool MASK>
+    static cudaError_t moments_t(const KParams &p, const void *f, double *rho, double *u, double *partials,
+                                 double *uprev, cudaStream_t s, int *nb) {
+        typedef typename Store<ST>::T T;
+        const dim3 grid = node_grid(p, kMomBlock, 1);
+        *nb = (int)(grid.x * grid.y * grid.z);
+        k_moments<L, ST, MASK><<<grid, kMomBlock, 0, s>>>(p, (const T *)f, rho, u, partials, uprev);
+        return cudaGetLastError();
+    }
+    static cudaError_t moments(int st, bool mask, const KParams &p, const void *f, double *rho, double *u,
+                               double *partials, double *uprev, cudaStream_t s, int *nb) {
+#define LBM_MOM(S)                                                                               \
+    case S:                                                                                      \
+        return mask ? moments_t<S, true>(p, f, rho, u, partials, uprev, s, nb)                   \
+                    : moments_t<S, false>(p, f, rho, u, partials, uprev, s, nb);
+        switch (st) { LBM_MOM(ST_F64) LBM_MOM(ST_F32) LBM_MOM(ST_F16) LBM_MOM(ST_BF16) }
+#undef LBM_MOM
+        return cudaErrorInvalidValue;
+    }
+
+    template <int COLL, int ST, bool MASK>
+    static cudaError_t init_t(const KParams &p, const double *rho0, const double *u0, void *target, cudaStream_t s) {
+        typedef typename Store<ST>::T T;
+        k_init<L, COLL, ST, MASK><<<node_grid(p, 128, 1), 128, 0, s>>>(p, rho0, u0, (T *)target);
+        return cudaGetLastError();
+    }
+    template <int COLL>
+    static cudaError_t init_c(int st, bool mask, const KParams &p, const double *rho0, const double *u0,
+                              void *target, cudaStream_t s) {
+#define LBM_INIT(S)                                                                                   \
+    case S:                                                                                           \
+        return mask ? init_t<COLL, S, true>(p, rho0, u0, target, s) : init_t<COLL, S, false>(p, rho0, u0, target, s);
+        switch (st) { LBM_INIT(ST_F64) LBM_INIT(ST_F32) LBM_INIT(ST_F16) LBM_INIT(ST_BF16) }
+#undef LBM_INIT
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t init(int coll, int st, bool mask, const KParams &p, const double *rho0, const double *u0,
+                            void *target, cudaStream_t s) {
+        return coll == SMRT ? init_c<SMRT>(st, mask, p, rho0, u0, target, s)
+                            : init_c<BGK>(st, mask, p, rho0, u0, target, s);
+    }
+
+    static cudaError_t unstream(int st, bool mask, const KParams &p, const void *T, void *P, cudaStream_t s) {
+#define LBM_UNS(S)                                                                                         \
+    case S: {                                                                                              \
+        typedef typename Store<S>::T TT;                                                                   \
+        if (mask) k_unstream<L, S, true><<<node_grid(p, 128, 1), 128, 0, s>>>(p, (const TT *)T, (TT *)P);   \
+        else k_unstream<L, S, false><<<node_grid(p, 128, 1), 128, 0, s>>>(p, (const TT *)T, (TT *)P);      \
+        return cudaGetLastError();                                                                         \
+    }
+        switch (st) { LBM_UNS(ST_F64) LBM_UNS(ST_F32) LBM_UNS(ST_F16) LBM_UNS(ST_BF16) }
+#undef LBM_UNS
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t get_pops(int st, bool mask, const KParams &p, const void *f, double *out, cudaStream_t s) {
+#define LBM_GET(S)                                                                                   \
+    case S: {                                                                                        \
+        typedef typename Store<S>::T TT;                                                             \
+        if (mask) k_get_pops<L, S, true><<<node_grid(p, 128, 1), 128, 0, s>>>(p, (const TT *)f, out); \
+        else k_get_pops<L, S, false><<<node_grid(p, 128, 1), 128, 0, s>>>(p, (const TT *)f, out);    \
+        return cudaGetLastError();                                                                   \
+    }
+        switch (st) { LBM_GET(ST_F64) LBM_GET(ST_F32) LBM_GET(ST_F16) LBM_GET(ST_BF16) }
+#undef LBM_GET
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t put_pops(int st, const KParams &p, const double *in, void *T, cudaStream_t s) {
+#define LBM_PUT(S)                                                                  \
+    case S: {                                                                       \
+        typedef typename Store<S>::T TT;                                            \
+        k_put_pops<L, S><<<node_grid(p, 128, 1), 128, 0, s>>>(p, in, (TT *)T);       \
+        return cudaGetLastError();                                                  \
+    }
+        switch (st) { LBM_PUT(ST_F64) LBM_PUT(ST_F32) LBM_PUT(ST_F16) LBM_PUT(ST_BF16) }
+#undef LBM_PUT
+        return cudaErrorInvalidValue;
+    }
+
+    static const Launchers &table() {
+        static const Launchers t = {&step, &moments, &init, &unstream, &get_pops, &put_pops};
+        return t;
+    }
+};
+
+}  // namespace lbm

@@ -1,0 +1,551 @@
+// lbm_runtime.cu -- the C ABI (include/lbm.h): handle, buffers, stream and
+// CUDA-graph management, FP64 reductions and error reporting around the
+// fused stream-collide kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+int lattice_D(int lat) { return lat == LBM_D2Q9 ? 2 : 3; }
+int lattice_Q(int lat) { return lat == LBM_D2Q9 ? 9 : (lat == LBM_D3Q19 ? 19 : 27); }
+size_t storage_bytes(int st) { return st == LBM_F64 ? 8 : (st == LBM_F32 ? 4 : 2); }
+
+const Launchers &launchers_for(int lat) {
+    return lat == LBM_D2Q9 ? launchers_d2q9() : (lat == LBM_D3Q19 ? launchers_d3q19() : launchers_d3q27());
+}
+
+}  // namespace
+
+// finalize: one block sums the per-block partials in a fixed order
+namespace lbm {
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, double *__restrict__ out) {
+    __shared__ double sh[256][kPartials];
+    double v[kPartials];
+#pragma unroll
+    for (int k = 0; k < kPartials; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < kPartials; ++k) v[k] += partials[(long long)b * kPartials + k];
+#pragma unroll
+    for (int k = 0; k < kPartials; ++k) sh[threadIdx.x][k] = v[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < kPartials; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kPartials; ++k) out[k] = sh[0][k];
+}
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+}  // namespace lbm
+
+struct lbm_handle {
+    int lattice = 0, collision = 0, storage = 0;
+    int D = 2, Q = 9;
+    int nx = 0, ny = 0, nz = 0;
+    int force_kind = 0;
+    bool mask = false;
+    KParams kp{};
+    StepCfg cfg{128, 1};
+    size_t state_bytes = 0;   // one population buffer
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;              // buffer holding the state
+    double *g_dev = nullptr;
+    size_t g_count = 0;       // doubles in the host layout of g
+    unsigned char *solid_dev = nullptr;
+    double *partials = nullptr;
+    int max_blocks = 0;
+    double *red_dev = nullptr;   // kPartials doubles
+    double *uprev = nullptr;     // D * N doubles, velocity at the last residual check
+    int64_t uprev_step = -1;
+    double *fields = nullptr;    // (1 + D) * N doubles for lbm_moments
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    int64_t step = 0;
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free_)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    std::string err;
+
+    size_t N() const { return (size_t)nx * ny * nz; }
+};
+
+namespace {
+
+lbm_status fail(lbm_handle *h, lbm_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_thread_err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_handle *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define LBM_CUDA(h, call)                                          \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return cuda_fail((h), e__, #call); \
+    } while (0)
+
+void *dev_alloc(lbm_handle *h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (h->alloc) return h->alloc(bytes, h->alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_handle *h, void *p) {
+    if (!p) return;
+    if (h->free_) h->free_(p, h->alloc_ctx);
+    else cudaFree(p);
+}
+
+template <typename T>
+lbm_status alloc_into(lbm_handle *h, T **out, size_t bytes, const char *what) {
+    *out = (T *)dev_alloc(h, bytes);
+    if (!*out) return fail(h, LBM_ERR_OOM, std::string("device allocation failed: ") + what);
+    return LBM_OK;
+}
+
+size_t g_count_for(const lbm_handle *h) {
+    switch (h->force_kind) {
+    case LBM_G_UNIFORM: return (size_t)h->D;
+    case LBM_G_ROWS: return (size_t)h->ny * h->D;
+    case LBM_G_FIELD: return (size_t)h->D * h->N();
+    default: return 0;
+    }
+}
+
+// device layout of g: uniform [3], rows [ny][D], field [D][plane] (padded rows)
+lbm_status upload_force(lbm_handle *h, const double *g) {
+    if (h->force_kind == LBM_G_NONE) return LBM_OK;
+    if (!g) return fail(h, LBM_ERR_ARG, "force array is NULL");
+    std::vector<double> tmp;
+    if (h->force_kind == LBM_G_UNIFORM) {
+        tmp.assign(3, 0.0);
+        for (int a = 0; a < h->D; ++a) tmp[a] = g[a];
+    } else if (h->force_kind == LBM_G_ROWS) {
+        tmp.assign(g, g + (size_t)h->ny * h->D);
+    } else {
+        const size_t plane = (size_t)h->kp.plane;
+        tmp.assign((size_t)h->D * plane, 0.0);
+        for (int a = 0; a < h->D; ++a)
+            for (size_t zy = 0; zy < (size_t)h->ny * h->nz; ++zy)
+                std::memcpy(&tmp[a * plane + zy * h->kp.nxp], &g[a * h->N() + zy * h->nx],
+                            sizeof(double) * h->nx);
+    }
+    for (double v : tmp)
+        if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "force contains a non-finite value");
+    LBM_CUDA(h, cudaMemcpyAsync(h->g_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    // the staging vector dies on return: wait for the copy
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status launch_steps(lbm_handle *h, int64_t n) {
+    const Launchers &L = launchers_for(h->lattice);
+    for (int64_t s = 0; s < n; ++s) {
+        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, h->kp, h->buf[h->cur],
+                               h->buf[1 - h->cur], h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
+        h->cur = 1 - h->cur;
+    }
+    return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_handle *h) {
+    if (h->graph) return LBM_OK;
+    const int steps = h->graph_steps;
+    const int saved = h->cur;
+    cudaGraph_t g = nullptr;
+    LBM_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = launch_steps(h, steps);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->cur = saved;  // capture does not execute; steps is even anyway
+    if (st != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
+// rho/u into device pointers (nullable), partial sums, finalize into red_dev
+lbm_status run_moments(lbm_handle *h, double *rho, double *u, double *uprev) {
+    const Launchers &L = launchers_for(h->lattice);
+    int nb = 0;
+    cudaError_t e = L.moments(h->storage, h->mask, h->kp, h->buf[h->cur], rho, u, h->partials, uprev,
+                              h->stream, &nb);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments launch");
+    if (nb > h->max_blocks) return fail(h, LBM_ERR_STATE, "partial-sum scratch too small");
+    e = launch_finalize(h->partials, nb, h->red_dev, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "finalize launch");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(const lbm_handle *h) { return h ? h->err.c_str() : g_thread_err.c_str(); }
+
+void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    dev_free(h, h->buf[0]);
+    dev_free(h, h->buf[1]);
+    dev_free(h, h->g_dev);
+    dev_free(h, h->solid_dev);
+    dev_free(h, h->partials);
+    dev_free(h, h->red_dev);
+    dev_free(h, h->uprev);
+    dev_free(h, h->fields);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, LBM_ERR_ARG, "desc is NULL");
+    if (d->lattice < LBM_D2Q9 || d->lattice > LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "bad lattice");
+    if (d->collision != LBM_BGK && d->collision != LBM_SMRT) return fail(nullptr, LBM_ERR_ARG, "bad collision");
+    if (d->storage < LBM_F64 || d->storage > LBM_BF16_SHIFT) return fail(nullptr, LBM_ERR_ARG, "bad storage");
+    if (d->force_kind < LBM_G_NONE || d->force_kind > LBM_G_FIELD) return fail(nullptr, LBM_ERR_ARG, "bad force kind");
+    const int D = lattice_D(d->lattice), Q = lattice_Q(d->lattice);
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(nullptr, LBM_ERR_ARG, "sizes must be >= 1");
+    if (D == 2 && d->nz != 1) return fail(nullptr, LBM_ERR_ARG, "nz must be 1 for D2Q9");
+    if (d->ny > 65535 || d->nz > 65535) return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
+    if (d->collision == LBM_BGK && !(d->tau[2] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau[2] must be > 1/2");
+    if (d->collision == LBM_SMRT)
+        for (int n = 2; n <= 4; ++n)
+            if (!(d->tau[n] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");
+    if ((d->alloc == nullptr) != (d->free_ == nullptr))
+        return fail(nullptr, LBM_ERR_ARG, "alloc and free_ must be given together");
+
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    h->lattice = d->lattice;
+    h->collision = d->collision;
+    h->storage = d->storage;
+    h->D = D;
+    h->Q = Q;
+    h->nx = d->nx;
+    h->ny = d->ny;
+    h->nz = d->nz;
+    h->force_kind = d->force_kind;
+    h->mask = d->solid != nullptr;
+    h->alloc = d->alloc;
+    h->free_ = d->free_;
+    h->alloc_ctx = d->alloc_ctx;
+
+    const int nxp = (d->nx + 31) / 32 * 32;
+    const long long plane = (long long)nxp * d->ny * d->nz;
+    if (plane * Q >= (1LL << 40) || plane >= (1LL << 31)) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "domain too large");
+    }
+    KParams &kp = h->kp;
+    kp.nx = d->nx;
+    kp.ny = d->ny;
+    kp.nz = d->nz;
+    kp.nxp = nxp;
+    kp.plane = plane;
+    for (int k = 0; k < 3; ++k) kp.per[k] = d->periodic[k] ? 1 : 0;
+    kp.force_kind = d->force_kind;
+    for (int n = 0; n < 5; ++n) kp.om[n] = d->tau[n] > 0.0 ? 1.0 / d->tau[n] : 0.0;
+
+    // launch shape: 3-D and wide rows use two nodes per thread
+    h->cfg.bdx = 128;
+    h->cfg.npt = (d->nx >= 512) ? 2 : 1;
+    if (d->nx <= 64) h->cfg.bdx = 64;
+    h->graph_steps = 64;
+
+    lbm_status st;
+    if (d->stream) {
+        h->stream = (cudaStream_t)d->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            lbm_status s2 = cuda_fail(nullptr, e, "cudaStreamCreate");
+            delete h;
+            return s2;
+        }
+        h->own_stream = true;
+    }
+    h->state_bytes = (size_t)plane * Q * storage_bytes(d->storage);
+    const dim3 mg = node_grid(kp, kMomBlock, 1);
+    h->max_blocks = (int)(mg.x * mg.y * mg.z);
+    const size_t N = h->N();
+    h->g_count = g_count_for(h);
+    if ((st = alloc_into(h, &h->buf[0], h->state_bytes, "population buffer A")) ||
+        (st = alloc_into(h, &h->buf[1], h->state_bytes, "population buffer B")) ||
+        (st = alloc_into(h, &h->partials, (size_t)h->max_blocks * kPartials * sizeof(double), "partials")) ||
+        (st = alloc_into(h, &h->red_dev, 8 * sizeof(double), "reduction")) ||
+        (st = alloc_into(h, &h->g_dev,
+                         std::max<size_t>(3, h->force_kind == LBM_G_FIELD ? (size_t)D * plane : h->g_count) *
+                             sizeof(double),
+                         "force"))) {
+        *out = nullptr;
+        std::string m = h->err;
+        lbm_destroy(h);
+        return fail(nullptr, st, m);
+    }
+    kp.g = h->g_dev;
+    // zero both buffers (padding included) so every byte is defined
+    cudaError_t e = cudaMemsetAsync(h->buf[0], 0, h->state_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->state_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->g_dev, 0, 3 * sizeof(double), h->stream);
+    if (e != cudaSuccess) {
+        lbm_status s2 = cuda_fail(nullptr, e, "cudaMemsetAsync");
+        lbm_destroy(h);
+        return s2;
+    }
+    if ((st = upload_force(h, d->g)) != LBM_OK) {
+        std::string m = h->err;
+        lbm_destroy(h);
+        return fail(nullptr, st, m);
+    }
+    if (h->mask) {
+        if ((st = alloc_into(h, &h->solid_dev, (size_t)plane, "solid mask")) != LBM_OK) {
+            std::string m = h->err;
+            lbm_destroy(h);
+            return fail(nullptr, st, m);
+        }
+        std::vector<unsigned char> tmp((size_t)plane, 0);
+        for (size_t zy = 0; zy < (size_t)d->ny * d->nz; ++zy)
+            for (int x = 0; x < d->nx; ++x) tmp[zy * nxp + x] = d->solid[zy * d->nx + x] ? 1 : 0;
+        e = cudaMemcpyAsync(h->solid_dev, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            lbm_status s2 = cuda_fail(nullptr, e, "solid upload");
+            lbm_destroy(h);
+            return s2;
+        }
+        kp.solid = h->solid_dev;
+    }
+    // initial state: target fbar in buffer B, unstreamed into buffer A
+    double *rho0_dev = nullptr, *u0_dev = nullptr;
+    if (d->rho0 || d->u0) {
+        if ((st = alloc_into(h, &h->fields, (size_t)(1 + D) * N * sizeof(double), "fields")) != LBM_OK) {
+            std::string m = h->err;
+            lbm_destroy(h);
+            return fail(nullptr, st, m);
+        }
+        if (d->rho0) {
+            rho0_dev = h->fields;
+            e = cudaMemcpyAsync(rho0_dev, d->rho0, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess && d->u0) {
+            u0_dev = h->fields + N;
+            e = cudaMemcpyAsync(u0_dev, d->u0, (size_t)D * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e != cudaSuccess) {
+            lbm_status s2 = cuda_fail(nullptr, e, "initial field upload");
+            lbm_destroy(h);
+            return s2;
+        }
+    }
+    const Launchers &L = launchers_for(h->lattice);
+    e = L.init(h->collision, h->storage, h->mask, kp, rho0_dev, u0_dev, h->buf[1], h->stream);
+    if (e == cudaSuccess) e = L.unstream(h->storage, h->mask, kp, h->buf[1], h->buf[0], h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        lbm_status s2 = cuda_fail(nullptr, e, "initialisation");
+        lbm_destroy(h);
+        return s2;
+    }
+    h->cur = 0;
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle *h, int64_t nsteps) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    int64_t left = nsteps;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LBM_CUDA(h, cudaStreamIsCapturing(h->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone && left >= h->graph_steps) {
+        lbm_status st = ensure_graph(h);
+        if (st != LBM_OK) return st;
+        while (left >= h->graph_steps) {
+            LBM_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+            left -= h->graph_steps;
+        }
+    }
+    lbm_status st = launch_steps(h, left);
+    if (st != LBM_OK) return st;
+    h->step += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_moments_device(lbm_handle *h, double *rho_dev, double *u_dev, double *totals_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    lbm_status st = run_moments(h, rho_dev, u_dev, nullptr);
+    if (st != LBM_OK) return st;
+    if (totals_dev)
+        LBM_CUDA(h, cudaMemcpyAsync(totals_dev, h->red_dev, 4 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_handle *h, double *rho, double *u, double *totals) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    const size_t N = h->N();
+    if ((rho || u) && !h->fields) {
+        lbm_status st = alloc_into(h, &h->fields, (size_t)(1 + h->D) * N * sizeof(double), "fields");
+        if (st != LBM_OK) return st;
+    }
+    double *rd = rho ? h->fields : nullptr;
+    double *ud = u ? h->fields + N : nullptr;
+    lbm_status st = run_moments(h, rd, ud, nullptr);
+    if (st != LBM_OK) return st;
+    double red[kPartials];
+    LBM_CUDA(h, cudaMemcpyAsync(red, h->red_dev, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
+    if (rho) LBM_CUDA(h, cudaMemcpyAsync(rho, rd, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (u) LBM_CUDA(h, cudaMemcpyAsync(u, ud, (size_t)h->D * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (totals) {
+        totals[0] = red[0];
+        totals[1] = red[1];
+        totals[2] = red[2];
+        totals[3] = h->D == 3 ? red[3] : 0.0;
+    }
+    if (red[6] > 0.0) return fail(h, LBM_ERR_UNSTABLE, "non-finite density or velocity");
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_handle *h, int K, double *r) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (K < 1 || !r) return fail(h, LBM_ERR_ARG, "K must be >= 1 and r non-NULL");
+    const size_t N = h->N();
+    if (!h->uprev) {
+        lbm_status st = alloc_into(h, &h->uprev, (size_t)h->D * N * sizeof(double), "residual velocity");
+        if (st != LBM_OK) return st;
+    }
+    lbm_status st;
+    if (h->uprev_step != h->step) {
+        // velocity at the current step into uprev
+        if ((st = run_moments(h, nullptr, h->uprev, nullptr)) != LBM_OK) return st;
+    }
+    if ((st = lbm_step(h, K)) != LBM_OK) return st;
+    if ((st = run_moments(h, nullptr, nullptr, h->uprev)) != LBM_OK) return st;
+    double red[kPartials];
+    LBM_CUDA(h, cudaMemcpyAsync(red, h->red_dev, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->uprev_step = h->step;
+    if (red[6] > 0.0 || !std::isfinite(red[4]) || !std::isfinite(red[5])) {
+        *r = NAN;
+        return fail(h, LBM_ERR_UNSTABLE, "non-finite velocity");
+    }
+    *r = red[5] > 0.0 ? std::sqrt(red[4]) / ((double)K * std::sqrt(red[5])) : (red[4] > 0.0 ? INFINITY : 0.0);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_handle *h, const double *g) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (h->force_kind == LBM_G_NONE) return fail(h, LBM_ERR_STATE, "created without a force");
+    return upload_force(h, g);
+}
+
+lbm_status lbm_get_populations(lbm_handle *h, double *f) {
+    if (!h || !f) return fail(h, LBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->Q * h->N();
+    double *tmp = nullptr;
+    lbm_status st = alloc_into(h, &tmp, n * sizeof(double), "population export");
+    if (st != LBM_OK) return st;
+    cudaError_t e = launchers_for(h->lattice).get_pops(h->storage, h->mask, h->kp, h->buf[h->cur], tmp, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "population export");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle *h, const double *f) {
+    if (!h || !f) return fail(h, LBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->Q * h->N();
+    double *tmp = nullptr;
+    lbm_status st = alloc_into(h, &tmp, n * sizeof(double), "population import");
+    if (st != LBM_OK) return st;
+    const Launchers &L = launchers_for(h->lattice);
+    void *spare = h->buf[1 - h->cur];
+    cudaError_t e = cudaMemcpyAsync(tmp, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = L.put_pops(h->storage, h->kp, tmp, spare, h->stream);
+    if (e == cudaSuccess) e = L.unstream(h->storage, h->mask, h->kp, spare, h->buf[h->cur], h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "population import");
+    h->uprev_step = -1;
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_handle *h) { return h ? h->state_bytes : 0; }
+
+lbm_status lbm_get_state(lbm_handle *h, void *host, size_t bytes, int64_t *step) {
+    if (!h || !host) return fail(h, LBM_ERR_ARG, "NULL argument");
+    if (bytes != h->state_bytes) return fail(h, LBM_ERR_STATE, "state size mismatch");
+    LBM_CUDA(h, cudaMemcpyAsync(host, h->buf[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (step) *step = h->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t step) {
+    if (!h || !host) return fail(h, LBM_ERR_ARG, "NULL argument");
+    if (bytes != h->state_bytes) return fail(h, LBM_ERR_STATE, "state size mismatch");
+    LBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], host, bytes, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->step = step;
+    h->uprev_step = -1;
+    return LBM_OK;
+}
+
+lbm_status lbm_info(const lbm_handle *h, int *D, int *Q, int64_t *step, size_t *bytes_per_node) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (D) *D = h->D;
+    if (Q) *Q = h->Q;
+    if (step) *step = h->step;
+    if (bytes_per_node) *bytes_per_node = 2 * (size_t)h->Q * storage_bytes(h->storage);
+    return LBM_OK;
+}
+
+}  // extern "C"
