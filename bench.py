@@ -1,0 +1,384 @@
+"""Benchmark of the fused stream-collide path on the 4096 x 4096 Kolmogorov flow
+(D2Q9, SMRT tau_2 = 0.6, tau_3 = tau_4 = 1, FP32 storage of deviations,
+g_x = 1e-5 sin(2 pi y / 4096), initial u = that profile plus seeded 1e-4
+Gaussian noise).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+One step = one lattice time step over the whole domain (pull-stream, collide,
+store) with the FP64 check (mass, momentum, K-step residual) every
+--check-every steps inside the timed region.  Prints one JSON line (rank 0).
+
+N > 1 (torchrun) runs one independent replica per GPU (weak scaling); ranks
+share nothing but a barrier and a max-reduction of their times.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded strip of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_workloads as W  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline per lattice"
+UNIT = "MLUPS"
+WORKLOAD = "kolmogorov_d2q9_smrt_f32_4096x4096"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_d2q9_smrt_f32_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--n", type=int, default=4096, help="domain edge (4096 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2212_07494_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._th = threading.Thread(target=self._read, daemon=True)
+            self._th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append((t, parts))
+        mine = [r for r in rows if r[1][1] == str(self.index)]
+        if mine:
+            rows = mine
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.15 <= r[0] <= self.t1 + 0.15]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(p[2]) for _, p in use if p[2].replace(".", "").isdigit()]
+        smax = [float(p[3]) for _, p in use if p[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in use:
+            for k, n in enumerate(names):
+                if p[6 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(use), "in_window": bool(inside)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_launch(n_nodes):
+    """DRAM bytes per launch of the stream-collide kernel from the committed ncu
+    summary, scaled to this launch by node count; None when the summary is
+    missing or the kernel sources changed since it was taken."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    d = json.load(open(PROFILE_TRAFFIC))
+    if d.get("kernel_sources_sha") != kernel_sources_sha():
+        return None
+    return float(d["dram_bytes_per_node"]) * n_nodes
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_strip(n, rows, seed=2212074940):
+    """Rows [0, rows) of the n x n Kolmogorov workload as an n x rows periodic
+    strip (same per-node work; the oracle cannot hold the full run)."""
+    import oracle as O
+    wl = W.kolmogorov(n=n, seed=seed) if n <= 1024 else None
+    if wl is None:
+        # draw only what the strip needs: same profile and noise recipe
+        rng = W.SplitMix64(seed)
+        y = np.arange(rows, dtype=np.float64)
+        prof = 1e-5 * np.sin(2 * np.pi * y / n)
+        u0 = rng.normal(2 * rows * n).reshape(2, 1, rows, n) * 1e-4
+        u0[0, 0] += prof[:, None]
+        g = np.zeros((rows, 2))
+        g[:, 0] = prof
+        tau = (1.0, 1.0, 0.6, 1.0, 1.0)
+    else:
+        u0 = wl.u0[:, :, :rows]
+        g = wl.g[:rows]
+        tau = wl.tau
+    return O.Sim(O.D2Q9, O.SMRT, (n, rows, 1), (1, 1, 1), tau, g=g, force_kind="rows",
+                 u0=np.ascontiguousarray(u0))
+
+
+def cpu_baseline(n, seconds):
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    rows = max(8, min(n, 256))
+    sim = oracle_strip(n, rows)
+    sim.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds and steps < 50:
+        sim.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    mlups = n * rows * steps / dt / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of the FP64 oracle on a {n} x {rows} periodic strip of the "
+                      f"{n} x {n} Kolmogorov workload ({n * rows * steps} node updates, {dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    n = args.n
+    # size the strip so that warmup + steps take about two minutes
+    probe = oracle_strip(n, 8)
+    t0 = time.perf_counter()
+    probe.step(2)
+    per_row = (time.perf_counter() - t0) / 2 / 8
+    total = max(1, args.steps + args.warmup)
+    rows = int(max(1, min(n, 120.0 / (total * per_row))))
+    sim = oracle_strip(n, rows)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = n * rows * args.steps / dt / 1e6
+    sample = f"each step: one FP64 oracle time step on a {n} x {rows} periodic strip of the {n} x {n} workload"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "D2Q9", "collision": "SMRT", "storage": "F64 (oracle)",
+                       "nx": n, "ny": n, "tau": [1.0, 1.0, 0.6, 1.0, 1.0]},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    import paper_2212_07494_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    t_gen = time.perf_counter()
+    wl = W.kolmogorov(n=n)
+    stream = torch.cuda.Stream(device=local)
+    N = n * n
+    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, "F32", (1, 1, 1), g=wl.g, force_kind="rows",
+                    u0=wl.u0, torch_stream=stream)
+    D, Q, _, bytes_per_node = lat.info()
+    C = max(1, args.check_every)
+    chunks = max(1, args.steps // C)
+    steps = chunks * C
+    checks = torch.zeros((chunks, 7), dtype=torch.float64, device=f"cuda:{local}")
+    warm = torch.zeros(7, dtype=torch.float64, device=f"cuda:{local}")
+    # warm-up: graphs captured, clocks up
+    with torch.cuda.stream(stream):
+        lat.step(max(args.warmup, 3))
+        lat.check_device(warm.data_ptr())
+    torch.cuda.synchronize()
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(chunks)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(chunks)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark(0)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for c in range(chunks):
+            ev_s[c].record(stream)
+            lat.step(C)
+            ev_e[c].record(stream)
+            lat.check_device(checks[c].data_ptr())
+        e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(1)
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    total_ms = e0.elapsed_time(e1)
+    kern_ms = sum(ev_s[c].elapsed_time(ev_e[c]) for c in range(chunks)) / steps
+    t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ck = checks.cpu().numpy()
+    finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
+    res = float(math.sqrt(ck[-1, 4]) / (C * math.sqrt(ck[-1, 5]))) if chunks > 1 and ck[-1, 5] > 0 else None
+    mass_drift = float(abs(ck[-1, 0] - ck[0, 0]) / ck[0, 0])
+    lat.close()
+
+    value = ws * N * steps / (total_ms * 1e-3) / 1e6
+    peak, peak_kind = measured_peaks()
+    algo_bytes = bytes_per_node * N
+    achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
+    traffic = traffic_per_launch(N)
+    clocks = sampler.summary()
+    launches = chunks * (C + 2)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(P, torch, wl, n, steps, C, local, ws, dist)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "D2Q9", "collision": "SMRT", "storage": "F32",
+                       "nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)",
+                       "check_every": C, "l2": "inputs larger than L2 (two 604 MB population buffers)",
+                       "replicas": ws},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_step<D2Q9,SMRT,F32>", "bytes_per_launch": algo_bytes,
+                         "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+            "gpu_launches": launches, "clocks": clocks,
+            "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res}}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(P, torch, wl, n, steps, C, local, ws, dist):
+    """Whole job through the public API from pinned host memory: create (H2D of
+    the initial velocity and force), run with a host-read residual every C
+    steps, read rho and u back (D2H)."""
+    u0 = torch.from_numpy(np.ascontiguousarray(wl.u0)).pin_memory()
+    g = torch.from_numpy(np.ascontiguousarray(wl.g)).pin_memory()
+    N = n * n
+    rho = torch.empty(N, dtype=torch.float64).pin_memory()
+    u = torch.empty(2 * N, dtype=torch.float64).pin_memory()
+    tot = np.empty(4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, "F32", (1, 1, 1), g=g.numpy(), force_kind="rows",
+                    u0=u0.numpy())
+    r = None
+    for _ in range(steps // C):
+        r = lat.residual(C)
+    P.lbm_moments(lat.h, rho.numpy(), u.numpy(), tot)
+    dt = time.perf_counter() - t0
+    lat.close()
+    tt = torch.tensor([dt], dtype=torch.float64, device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dt = float(tt.item())
+    h2d = u0.numel() * 8 + g.numel() * 8
+    d2h = (rho.numel() + u.numel()) * 8 + (steps // C) * 7 * 8
+    return {"value": ws * N * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "residual_last": r,
+            "what": "lbm_create from host u0/g, lbm_residual every check interval, lbm_moments to host"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.gpus != ws and ws != 1:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {ws}", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -127,6 +127,14 @@ lbm_status lbm_moments_device(lbm_handle *h, double *rho_dev, double *u_dev,
  * non-finite velocity appears.  Synchronises. */
 lbm_status lbm_residual(lbm_handle *h, int K, double *r);
 
+/* The periodic FP64 check of the state, asynchronously on the handle's
+ * stream: writes 7 doubles to out_dev,
+ *   {M, Px, Py, Pz, sum |u - u_snap|^2, sum |u|^2, number of non-finite nodes}
+ * over fluid nodes, then stores u as the new snapshot u_snap.  The residual
+ * of lbm_residual follows as sqrt(out[4]) / (K sqrt(out[5])) when the
+ * previous check was K steps earlier; the snapshot starts at u = 0. */
+lbm_status lbm_check_device(lbm_handle *h, double *out_dev);
+
 /* Replace the body force (same kind and layout as at creation); takes effect
  * for the next step.  Asynchronous (the host array is copied first). */
 lbm_status lbm_set_force(lbm_handle *h, const double *g);
@@ -143,6 +151,18 @@ lbm_status lbm_set_populations(lbm_handle *h, const double *f);
 size_t lbm_state_bytes(const lbm_handle *h);
 lbm_status lbm_get_state(lbm_handle *h, void *host, size_t bytes, int64_t *step);
 lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t step);
+
+/* Launch shape of the fused stream-collide kernel: threads per block along x
+ * (block_x: 32, 64, 128 or 256) and nodes per thread along x (1 or 2).
+ * Drops the captured step graph.  Results do not depend on the shape. */
+lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread);
+
+/* Time every supported launch shape over `trials` launches each (CUDA events
+ * on the handle's stream; the kernel reads the current state and writes the
+ * spare buffer, so the state does not advance), keep the fastest and return
+ * it (outputs nullable) with its mean launch time in milliseconds.
+ * Synchronises. */
+lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms);
 
 /* Information: D, Q, the step counter, and the device population buffer
  * currently holding the state (for profiling tools; do not free). */

@@ -65,6 +65,7 @@ def library():
     L.lbm_moments.argtypes = [H, dp, dp, dp]
     L.lbm_moments_device.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     L.lbm_residual.argtypes = [H, C.c_int, dp]
+    L.lbm_check_device.argtypes = [H, C.c_void_p]
     L.lbm_set_force.argtypes = [H, dp]
     L.lbm_get_populations.argtypes = [H, dp]
     L.lbm_set_populations.argtypes = [H, dp]
@@ -74,13 +75,16 @@ def library():
     L.lbm_set_state.argtypes = [H, C.c_void_p, C.c_size_t, C.c_int64]
     L.lbm_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                            C.POINTER(C.c_size_t)]
+    L.lbm_set_launch.argtypes = [H, C.c_int, C.c_int]
+    L.lbm_autotune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [H]
     L.lbm_last_error.restype = C.c_char_p
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
+              "lbm_check_device",
               "lbm_set_force", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
-              "lbm_set_state", "lbm_info"):
+              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune"):
         getattr(L, n).restype = C.c_int
     _lib = L
     return L
@@ -187,6 +191,10 @@ def lbm_residual(h, K):
     return r.value
 
 
+def lbm_check_device(h, out_ptr):
+    _check(library().lbm_check_device(h, out_ptr), h)
+
+
 def lbm_set_force(h, g):
     _check(library().lbm_set_force(h, _dptr(g)), h)
 
@@ -217,6 +225,16 @@ def lbm_info(h):
     D, Q, s, b = C.c_int(), C.c_int(), C.c_int64(), C.c_size_t()
     _check(library().lbm_info(h, C.byref(D), C.byref(Q), C.byref(s), C.byref(b)), h)
     return D.value, Q.value, s.value, b.value
+
+
+def lbm_set_launch(h, block_x, nodes_per_thread):
+    _check(library().lbm_set_launch(h, int(block_x), int(nodes_per_thread)), h)
+
+
+def lbm_autotune(h, trials=20):
+    bx, npt, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(library().lbm_autotune(h, int(trials), C.byref(bx), C.byref(npt), C.byref(ms)), h)
+    return bx.value, npt.value, ms.value
 
 
 def lbm_last_error(h=None):
@@ -257,6 +275,7 @@ class Lattice:
             self._cb = [alloc, free]
         desc, keep = make_desc(lattice, collision, shape, tau, storage, periodic, g, force_kind,
                                solid, rho0, u0, stream, alloc, free)
+        self.signature_fields = (desc.lattice, desc.collision, desc.storage, nx, ny, nz, solid is not None)
         self.force_kind = desc.force_kind
         self.h = lbm_create(desc)
         del keep
@@ -279,6 +298,10 @@ class Lattice:
     def residual(self, K):
         return lbm_residual(self.h, K)
 
+    def check_device(self, out_ptr):
+        """Asynchronous FP64 check into 7 doubles at device address out_ptr."""
+        lbm_check_device(self.h, out_ptr)
+
     def set_force(self, g):
         lbm_set_force(self.h, _f64(g))
 
@@ -300,6 +323,27 @@ class Lattice:
 
     def info(self):
         return lbm_info(self.h)
+
+    def set_launch(self, block_x, nodes_per_thread):
+        lbm_set_launch(self.h, block_x, nodes_per_thread)
+
+    def autotune(self, trials=20, cache=None):
+        """Pick the fastest launch shape (see lbm_autotune).  With a cache path,
+        reuse a stored choice for the same problem signature or store the new
+        one (JSON keyed by lattice, collision, storage, sizes, mask, device)."""
+        key = None
+        if cache:
+            from . import autotune as A
+            key = A.signature(self)
+            hit = A.lookup(cache, key)
+            if hit:
+                self.set_launch(*hit["launch"])
+                return tuple(hit["launch"]) + (hit["ms"],)
+        bx, npt, ms = lbm_autotune(self.h, trials)
+        if cache:
+            from . import autotune as A
+            A.store(cache, key, (bx, npt), ms)
+        return bx, npt, ms
 
     def close(self):
         if getattr(self, "h", None) is not None:

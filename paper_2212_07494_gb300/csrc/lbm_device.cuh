@@ -163,9 +163,27 @@ struct KParams {
     int per[3];                    // periodic flags
     int force_kind;                // G_*
     const double *g;               // uniform [3] | rows [ny][D] | field [D][plane]
+    const float *g32;              // the same force in FP32 (for FP32 arithmetic)
     const unsigned char *solid;    // [plane] or null
     double om[5];                  // 1 / tau_n
+    float om32[5];
+    // per population i, relative to a node's element index:
+    long long doff[27];            // i*plane - (cx + cy*nxp + cz*nxp*ny): pull source
+    long long poff[27];            // i*plane: the node's own entry
+    int noff[27];                  // -(cx + cy*nxp + cz*nxp*ny): neighbour x - c_i
 };
+
+// fill the per-population offsets of KParams for lattice L (host side)
+template <int L> inline void fill_offsets(KParams &p) {
+    for (int i = 0; i < 27; ++i) p.doff[i] = p.poff[i] = p.noff[i] = 0;
+    for (int i = 0; i < Lat<L>::Q; ++i) {
+        const long long nb = (long long)Lat<L>::cx(i) + (long long)Lat<L>::cy(i) * p.nxp +
+                             (long long)Lat<L>::cz(i) * p.nxp * p.ny;
+        p.poff[i] = (long long)i * p.plane;
+        p.doff[i] = p.poff[i] - nb;
+        p.noff[i] = (int)(-nb);
+    }
+}
 
 // --------------------------------------------------------- moment-space passes
 // All passes act in place on a 3^D array indexed by grid position / moment
@@ -383,44 +401,69 @@ __device__ __forceinline__ long long node_index(const KParams &p, int x, int y, 
 }
 
 // pull the pre-collision deviations of node (x,y,z) onto the velocity grid:
-// delta_i(x) = P_i(x - c_i), or P_opp(i)(x) across a wall or a solid node
+// delta_i(x) = P_i(x - c_i), or P_opp(i)(x) across a wall or a solid node.
+// Interior nodes use the precomputed per-population offsets; nodes on the
+// domain faces resolve periodic wrap and walls per axis.
 template <int L, int ST, bool MASK>
 __device__ __forceinline__ void gather(const KParams &p, const typename Store<ST>::T *__restrict__ f,
                                        int x, int y, int z, typename Store<ST>::R *G) {
     typedef typename Store<ST>::R R;
-    NodeNbr nb;
-    node_nbr(p, x, y, z, nb);
+    constexpr int D = Lat<L>::D;
     const long long own = node_index(p, x, y, z);
 #pragma unroll
-    for (int g = 0; g < Grid<Lat<L>::D>::N; ++g) G[g] = R(0);
+    for (int g = 0; g < Grid<D>::N; ++g) G[g] = R(0);
+    const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && (D == 2 || (z > 0 && z < p.nz - 1));
+    if (interior) {
+        const typename Store<ST>::T *base = f + own;
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) {
+            if (MASK && i != 0 && p.solid[own + p.noff[i]] != 0)
+                G[gpos<L>(i)] = Store<ST>::ld(base + p.poff[opp<L>(i)]);
+            else
+                G[gpos<L>(i)] = Store<ST>::ld(base + p.doff[i]);
+        }
+        return;
+    }
+    NodeNbr nb;
+    node_nbr(p, x, y, z, nb);
 #pragma unroll
     for (int i = 0; i < Lat<L>::Q; ++i) {
         const int kx = Lat<L>::cx(i) + 1, ky = Lat<L>::cy(i) + 1, kz = Lat<L>::cz(i) + 1;
-        bool wall = nb.xw[kx] || nb.yw[ky] || (Lat<L>::D == 3 && nb.zw[kz]);
-        const long long src = node_index(p, nb.xs[kx], nb.ys[ky], Lat<L>::D == 3 ? nb.zs[kz] : z);
+        bool wall = nb.xw[kx] || nb.yw[ky] || (D == 3 && nb.zw[kz]);
+        const long long src = node_index(p, nb.xs[kx], nb.ys[ky], D == 3 ? nb.zs[kz] : z);
         if (MASK && i != 0 && !wall) wall = p.solid[src] != 0;
-        const long long idx = wall ? (long long)opp<L>(i) * p.plane + own : (long long)i * p.plane + src;
+        const long long idx = wall ? p.poff[opp<L>(i)] + own : p.poff[i] + src;
         G[gpos<L>(i)] = Store<ST>::ld(f + idx);
     }
 }
 
+template <typename R> __device__ __forceinline__ const R *force_ptr(const KParams &p);
+template <> __device__ __forceinline__ const double *force_ptr<double>(const KParams &p) { return p.g; }
+template <> __device__ __forceinline__ const float *force_ptr<float>(const KParams &p) { return p.g32; }
+
+// body-force acceleration at a node; `node` is the element index within a plane
 template <int L, typename R>
 __device__ __forceinline__ void load_force(const KParams &p, int y, long long node, R &gx, R &gy, R &gz) {
     constexpr int D = Lat<L>::D;
+    const R *g = force_ptr<R>(p);
     gx = gy = gz = R(0);
     if (p.force_kind == G_UNIFORM) {
-        gx = R(__ldg(p.g + 0));
-        gy = R(__ldg(p.g + 1));
-        if (D == 3) gz = R(__ldg(p.g + 2));
+        gx = __ldg(g + 0);
+        gy = __ldg(g + 1);
+        if (D == 3) gz = __ldg(g + 2);
     } else if (p.force_kind == G_ROWS) {
-        gx = R(__ldg(p.g + (long long)y * D + 0));
-        gy = R(__ldg(p.g + (long long)y * D + 1));
-        if (D == 3) gz = R(__ldg(p.g + (long long)y * D + 2));
+        gx = __ldg(g + (long long)y * D + 0);
+        gy = __ldg(g + (long long)y * D + 1);
+        if (D == 3) gz = __ldg(g + (long long)y * D + 2);
     } else if (p.force_kind == G_FIELD) {
-        gx = R(__ldg(p.g + node));
-        gy = R(__ldg(p.g + p.plane + node));
-        if (D == 3) gz = R(__ldg(p.g + 2 * p.plane + node));
+        gx = __ldg(g + node);
+        gy = __ldg(g + p.plane + node);
+        if (D == 3) gz = __ldg(g + 2 * p.plane + node);
     }
 }
+
+template <typename R> __device__ __forceinline__ R omega(const KParams &p, int n);
+template <> __device__ __forceinline__ double omega<double>(const KParams &p, int n) { return p.om[n]; }
+template <> __device__ __forceinline__ float omega<float>(const KParams &p, int n) { return p.om32[n]; }
 
 }  // namespace lbm

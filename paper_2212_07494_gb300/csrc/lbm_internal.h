@@ -10,9 +10,11 @@
 namespace lbm {
 
 // number of doubles each moments block writes to the partial-sum scratch:
-// {M, Px, Py, Pz, residual numerator, residual denominator, non-finite count}
-constexpr int kPartials = 7;
+// {sum (rho - 1), Px, Py, Pz, residual numerator, residual denominator,
+//  non-finite count, fluid-node count}
+constexpr int kPartials = 8;
 constexpr int kMomBlock = 256;
+constexpr int kMomGridMax = 1216;   // 8 blocks per SM on 152 SMs
 
 struct StepCfg {
     int bdx;  // threads per block along x
@@ -23,9 +25,10 @@ struct Launchers {
     cudaError_t (*step)(int coll, int st, bool mask, StepCfg cfg, const KParams &p, const void *fin,
                         void *fout, cudaStream_t s);
     // rho/u (unpadded FP64, nullable), partials [nblocks * kPartials];
-    // uprev (unpadded FP64 D planes, nullable): residual against it and update
+    // uprev (unpadded D planes of the arithmetic type, nullable): residual
+    // against it, then updated
     cudaError_t (*moments)(int st, bool mask, const KParams &p, const void *f, double *rho, double *u,
-                           double *partials, double *uprev, cudaStream_t s, int *nblocks);
+                           double *partials, void *uprev, cudaStream_t s, int *nblocks);
     cudaError_t (*init)(int coll, int st, bool mask, const KParams &p, const double *rho0,
                         const double *u0, void *target, cudaStream_t s);
     cudaError_t (*unstream)(int st, bool mask, const KParams &p, const void *target, void *state,
@@ -41,6 +44,13 @@ const Launchers &launchers_d3q27();
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s);
 
+inline int moments_grid(const KParams &p) {
+    const long long items = (long long)((p.nx + kMomBlock - 1) / kMomBlock) * p.ny * p.nz;
+    return (int)(items < kMomGridMax ? items : kMomGridMax);
+}
+
+// totals out[0..6] = {M, Px, Py, Pz, residual num, residual den, non-finite}
+// from per-block partials in a fixed order
 inline dim3 node_grid(const KParams &p, int bdx, int npt) {
     return dim3((unsigned)((p.nx + bdx * npt - 1) / (bdx * npt)), (unsigned)p.ny, (unsigned)p.nz);
 }

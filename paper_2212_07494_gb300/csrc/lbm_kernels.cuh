@@ -26,19 +26,21 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         if (MASK && act[k]) act[k] = p.solid[node_index(p, x, y, z)] == 0;
         if (act[k]) gather<L, ST, MASK>(p, fin, x, y, z, G[k]);
     }
-    const R om2 = R(p.om[2]), om3 = R(p.om[3]), om4 = R(p.om[4]);
+    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4);
+    R gx, gy, gz;
+    const bool per_node_force = p.force_kind == G_FIELD;
+    if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         if (!act[k]) continue;
         const int x = x0 + k * blockDim.x;
         const long long own = node_index(p, x, y, z);
-        R gx, gy, gz;
-        load_force<L>(p, y, own, gx, gy, gz);
+        if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
         if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4);
         else collide_bgk<L>(G[k], gx, gy, gz, om2);
+        typename Store<ST>::T *dst = fout + own;
 #pragma unroll
-        for (int i = 0; i < Lat<L>::Q; ++i)
-            Store<ST>::st(fout + (long long)i * p.plane + own, G[k][gpos<L>(i)]);
+        for (int i = 0; i < Lat<L>::Q; ++i) Store<ST>::st(dst + p.poff[i], G[k][gpos<L>(i)]);
     }
 }
 
@@ -65,74 +67,92 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
-// Macroscopic fields of the current state (Eq. half_F): rho and u written in
-// the unpadded FP64 layout; per-block FP64 partial sums of rho, rho u and,
-// when uprev is given, of |u - uprev|^2 and |u|^2 (uprev is then updated).
+// Macroscopic fields of the current state (Eq. half_F) and the FP64 check.
+// A fixed grid walks the rows (grid-stride, so the partial sums and their
+// order do not depend on the domain); per-node arithmetic runs in the
+// storage's arithmetic type and only the accumulation is FP64.  Partials per
+// block: {sum (rho - 1), sum rho u_x, sum rho u_y, sum rho u_z,
+//         sum |u - uprev|^2, sum |u|^2, non-finite count, fluid count}.
+// rho/u outputs (unpadded FP64) and uprev (unpadded, arithmetic type; read
+// for the residual, then overwritten with u) are optional.
 template <int L, int ST, bool MASK>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const typename Store<ST>::T *__restrict__ f,
                                                        double *rho_out, double *u_out, double *partials,
-                                                       double *uprev) {
+                                                       typename Store<ST>::R *uprev) {
+    typedef typename Store<ST>::R R;
     constexpr int D = Lat<L>::D;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[kPartials] = {0, 0, 0, 0, 0, 0, 0};
-    if (x < p.nx) {
+    // work items (row segment, row) walked with 32-bit counters: a row is
+    // (y, z), at most 65535^2 of them, and segments per row are few
+    const int segs = (p.nx + kMomBlock - 1) / kMomBlock;
+    const unsigned rows = (unsigned)p.ny * (unsigned)p.nz;
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    double v[kPartials];
+#pragma unroll
+    for (int k = 0; k < kPartials; ++k) v[k] = 0.0;
+    unsigned row = blockIdx.x / segs;
+    int seg = blockIdx.x % segs;
+    const unsigned drow = gridDim.x / segs;
+    const int dseg = gridDim.x % segs;
+    for (; row < rows; row += drow, seg += dseg) {
+        if (seg >= segs) {
+            seg -= segs;
+            ++row;
+            if (row >= rows) break;
+        }
+        const int y = (int)(row % (unsigned)p.ny), z = (int)(row / (unsigned)p.ny);
+        const int x = seg * kMomBlock + threadIdx.x;
+        if (x >= p.nx) continue;
         const long long own = node_index(p, x, y, z);
         const long long n = ((long long)z * p.ny + y) * p.nx + x;
-        const long long N = (long long)p.nx * p.ny * p.nz;
-        double rho = 1.0, u[3] = {0.0, 0.0, 0.0};
         const bool fluid = !MASK || p.solid[own] == 0;
+        R drho = R(0), u[3] = {R(0), R(0), R(0)};
         if (fluid) {
-            double Gd[Grid<D>::N];
-            {
-                typename Store<ST>::R G[Grid<D>::N];
-                gather<L, ST, MASK>(p, f, x, y, z, G);
-#pragma unroll
-                for (int g = 0; g < Grid<D>::N; ++g) Gd[g] = (double)G[g];
-            }
-            double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+            R G[Grid<D>::N];
+            gather<L, ST, MASK>(p, f, x, y, z, G);
+            R j[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int i = 0; i < Lat<L>::Q; ++i) {
-                const double w = Gd[gpos<L>(i)];
+                const R w = G[gpos<L>(i)];
                 drho += w;
-                j[0] += Lat<L>::cx(i) * w;
-                j[1] += Lat<L>::cy(i) * w;
-                if (D == 3) j[2] += Lat<L>::cz(i) * w;
+                if (Lat<L>::cx(i)) j[0] += Lat<L>::cx(i) > 0 ? w : -w;
+                if (Lat<L>::cy(i)) j[1] += Lat<L>::cy(i) > 0 ? w : -w;
+                if (D == 3 && Lat<L>::cz(i)) j[2] += Lat<L>::cz(i) > 0 ? w : -w;
             }
-            rho = 1.0 + drho;
-            double gx, gy, gz;
-            load_force<L>(p, y, own, gx, gy, gz);
-            const double g3[3] = {gx, gy, gz};
-#pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = j[a] / rho + 0.5 * g3[a];
-            v[0] = rho;
-#pragma unroll
-            for (int a = 0; a < D; ++a) v[1 + a] = rho * u[a];
+            const R rho = R(1) + drho;
+            R g3[3];
+            load_force<L>(p, y, own, g3[0], g3[1], g3[2]);
             bool finite = isfinite(rho);
 #pragma unroll
-            for (int a = 0; a < D; ++a) finite = finite && isfinite(u[a]);
-            v[6] = finite ? 0.0 : 1.0;
+            for (int a = 0; a < D; ++a) {
+                u[a] = j[a] / rho + R(0.5) * g3[a];
+                finite = finite && isfinite(u[a]);
+                v[1 + a] += (double)(j[a] + R(0.5) * rho * g3[a]);   // rho u
+            }
+            v[0] += (double)drho;
+            v[6] += finite ? 0.0 : 1.0;
+            v[7] += 1.0;
             if (uprev) {
+                R dd = R(0), uu = R(0);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const double d = u[a] - uprev[a * N + n];
-                    v[4] += d * d;
-                    v[5] += u[a] * u[a];
+                    const R d = u[a] - uprev[a * N + n];
+                    dd += d * d;
+                    uu += u[a] * u[a];
                     uprev[a * N + n] = u[a];
                 }
+                v[4] += (double)dd;
+                v[5] += (double)uu;
             }
         }
-        if (rho_out) rho_out[n] = rho;
+        if (rho_out) rho_out[n] = fluid ? 1.0 + (double)drho : 1.0;
         if (u_out)
 #pragma unroll
-            for (int a = 0; a < D; ++a) u_out[a * N + n] = u[a];
+            for (int a = 0; a < D; ++a) u_out[a * N + n] = (double)u[a];
     }
     block_sum(v);
-    if (threadIdx.x == 0) {
-        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < kPartials; ++k) partials[b * kPartials + k] = v[k];
-    }
+        for (int k = 0; k < kPartials; ++k) partials[(long long)blockIdx.x * kPartials + k] = v[k];
 }
 
 // Target pre-collision state at every node (fbar = f_eq - F/2, deviations),
@@ -261,15 +281,15 @@ template <int L> struct Dispatch {
 
     template <int ST, bool MASK>
     static cudaError_t moments_t(const KParams &p, const void *f, double *rho, double *u, double *partials,
-                                 double *uprev, cudaStream_t s, int *nb) {
+                                 void *uprev, cudaStream_t s, int *nb) {
         typedef typename Store<ST>::T T;
-        const dim3 grid = node_grid(p, kMomBlock, 1);
-        *nb = (int)(grid.x * grid.y * grid.z);
-        k_moments<L, ST, MASK><<<grid, kMomBlock, 0, s>>>(p, (const T *)f, rho, u, partials, uprev);
+        typedef typename Store<ST>::R R;
+        *nb = moments_grid(p);
+        k_moments<L, ST, MASK><<<*nb, kMomBlock, 0, s>>>(p, (const T *)f, rho, u, partials, (R *)uprev);
         return cudaGetLastError();
     }
     static cudaError_t moments(int st, bool mask, const KParams &p, const void *f, double *rho, double *u,
-                               double *partials, double *uprev, cudaStream_t s, int *nb) {
+                               double *partials, void *uprev, cudaStream_t s, int *nb) {
 #define LBM_MOM(S)                                                                               \
     case S:                                                                                      \
         return mask ? moments_t<S, true>(p, f, rho, u, partials, uprev, s, nb)                   \

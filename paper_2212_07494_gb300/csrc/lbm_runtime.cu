@@ -23,6 +23,7 @@ thread_local std::string g_thread_err;
 int lattice_D(int lat) { return lat == LBM_D2Q9 ? 2 : 3; }
 int lattice_Q(int lat) { return lat == LBM_D2Q9 ? 9 : (lat == LBM_D3Q19 ? 19 : 27); }
 size_t storage_bytes(int st) { return st == LBM_F64 ? 8 : (st == LBM_F32 ? 4 : 2); }
+size_t arith_bytes(int st) { return st == LBM_F64 ? 8 : 4; }
 
 const Launchers &launchers_for(int lat) {
     return lat == LBM_D2Q9 ? launchers_d2q9() : (lat == LBM_D3Q19 ? launchers_d3q19() : launchers_d3q27());
@@ -49,9 +50,11 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, dou
             for (int k = 0; k < kPartials; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
         __syncthreads();
     }
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][7] + sh[0][0];  // M = fluid nodes + sum (rho - 1)
 #pragma unroll
-        for (int k = 0; k < kPartials; ++k) out[k] = sh[0][k];
+        for (int k = 1; k < 7; ++k) out[k] = sh[0][k];
+    }
 }
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
@@ -76,8 +79,9 @@ struct lbm_handle {
     unsigned char *solid_dev = nullptr;
     double *partials = nullptr;
     int max_blocks = 0;
-    double *red_dev = nullptr;   // kPartials doubles
-    double *uprev = nullptr;     // D * N doubles, velocity at the last residual check
+    double *red_dev = nullptr;   // 8 doubles: M, Px, Py, Pz, res num, res den, non-finite
+    void *uprev = nullptr;       // D * N values of the arithmetic type: u at the last check
+    float *g32_dev = nullptr;    // FP32 copy of the force
     int64_t uprev_step = -1;
     double *fields = nullptr;    // (1 + D) * N doubles for lbm_moments
     cudaStream_t stream = nullptr;
@@ -165,7 +169,10 @@ lbm_status upload_force(lbm_handle *h, const double *g) {
     }
     for (double v : tmp)
         if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "force contains a non-finite value");
+    std::vector<float> tmp32(tmp.begin(), tmp.end());
     LBM_CUDA(h, cudaMemcpyAsync(h->g_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->g32_dev, tmp32.data(), tmp32.size() * sizeof(float), cudaMemcpyHostToDevice,
                                 h->stream));
     // the staging vector dies on return: wait for the copy
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -206,15 +213,16 @@ lbm_status ensure_graph(lbm_handle *h) {
     return LBM_OK;
 }
 
-// rho/u into device pointers (nullable), partial sums, finalize into red_dev
-lbm_status run_moments(lbm_handle *h, double *rho, double *u, double *uprev) {
+// rho/u into device pointers (nullable), partial sums, finalize into `out`
+// (default: red_dev)
+lbm_status run_moments(lbm_handle *h, double *rho, double *u, void *uprev, double *out = nullptr) {
     const Launchers &L = launchers_for(h->lattice);
     int nb = 0;
     cudaError_t e = L.moments(h->storage, h->mask, h->kp, h->buf[h->cur], rho, u, h->partials, uprev,
                               h->stream, &nb);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments launch");
     if (nb > h->max_blocks) return fail(h, LBM_ERR_STATE, "partial-sum scratch too small");
-    e = launch_finalize(h->partials, nb, h->red_dev, h->stream);
+    e = launch_finalize(h->partials, nb, out ? out : h->red_dev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "finalize launch");
     return LBM_OK;
 }
@@ -232,6 +240,7 @@ void lbm_destroy(lbm_handle *h) {
     dev_free(h, h->buf[0]);
     dev_free(h, h->buf[1]);
     dev_free(h, h->g_dev);
+    dev_free(h, h->g32_dev);
     dev_free(h, h->solid_dev);
     dev_free(h, h->partials);
     dev_free(h, h->red_dev);
@@ -290,7 +299,13 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     kp.plane = plane;
     for (int k = 0; k < 3; ++k) kp.per[k] = d->periodic[k] ? 1 : 0;
     kp.force_kind = d->force_kind;
-    for (int n = 0; n < 5; ++n) kp.om[n] = d->tau[n] > 0.0 ? 1.0 / d->tau[n] : 0.0;
+    for (int n = 0; n < 5; ++n) {
+        kp.om[n] = d->tau[n] > 0.0 ? 1.0 / d->tau[n] : 0.0;
+        kp.om32[n] = (float)kp.om[n];
+    }
+    if (d->lattice == LBM_D2Q9) fill_offsets<D2Q9>(kp);
+    else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
+    else fill_offsets<D3Q27>(kp);
 
     // launch shape: 3-D and wide rows use two nodes per thread
     h->cfg.bdx = 128;
@@ -311,8 +326,7 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
         h->own_stream = true;
     }
     h->state_bytes = (size_t)plane * Q * storage_bytes(d->storage);
-    const dim3 mg = node_grid(kp, kMomBlock, 1);
-    h->max_blocks = (int)(mg.x * mg.y * mg.z);
+    h->max_blocks = kMomGridMax;
     const size_t N = h->N();
     h->g_count = g_count_for(h);
     if ((st = alloc_into(h, &h->buf[0], h->state_bytes, "population buffer A")) ||
@@ -322,17 +336,23 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
         (st = alloc_into(h, &h->g_dev,
                          std::max<size_t>(3, h->force_kind == LBM_G_FIELD ? (size_t)D * plane : h->g_count) *
                              sizeof(double),
-                         "force"))) {
+                         "force")) ||
+        (st = alloc_into(h, &h->g32_dev,
+                         std::max<size_t>(3, h->force_kind == LBM_G_FIELD ? (size_t)D * plane : h->g_count) *
+                             sizeof(float),
+                         "force (FP32)"))) {
         *out = nullptr;
         std::string m = h->err;
         lbm_destroy(h);
         return fail(nullptr, st, m);
     }
     kp.g = h->g_dev;
+    kp.g32 = h->g32_dev;
     // zero both buffers (padding included) so every byte is defined
     cudaError_t e = cudaMemsetAsync(h->buf[0], 0, h->state_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->state_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->g_dev, 0, 3 * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->g32_dev, 0, 3 * sizeof(float), h->stream);
     if (e != cudaSuccess) {
         lbm_status s2 = cuda_fail(nullptr, e, "cudaMemsetAsync");
         lbm_destroy(h);
@@ -438,7 +458,7 @@ lbm_status lbm_moments(lbm_handle *h, double *rho, double *u, double *totals) {
     double *ud = u ? h->fields + N : nullptr;
     lbm_status st = run_moments(h, rd, ud, nullptr);
     if (st != LBM_OK) return st;
-    double red[kPartials];
+    double red[7];
     LBM_CUDA(h, cudaMemcpyAsync(red, h->red_dev, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
     if (rho) LBM_CUDA(h, cudaMemcpyAsync(rho, rd, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (u) LBM_CUDA(h, cudaMemcpyAsync(u, ud, (size_t)h->D * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -458,17 +478,19 @@ lbm_status lbm_residual(lbm_handle *h, int K, double *r) {
     if (K < 1 || !r) return fail(h, LBM_ERR_ARG, "K must be >= 1 and r non-NULL");
     const size_t N = h->N();
     if (!h->uprev) {
-        lbm_status st = alloc_into(h, &h->uprev, (size_t)h->D * N * sizeof(double), "residual velocity");
+        const size_t bytes = (size_t)h->D * N * arith_bytes(h->storage);
+        lbm_status st = alloc_into(h, &h->uprev, bytes, "residual velocity");
         if (st != LBM_OK) return st;
+        LBM_CUDA(h, cudaMemsetAsync(h->uprev, 0, bytes, h->stream));
     }
     lbm_status st;
     if (h->uprev_step != h->step) {
         // velocity at the current step into uprev
-        if ((st = run_moments(h, nullptr, h->uprev, nullptr)) != LBM_OK) return st;
+        if ((st = run_moments(h, nullptr, nullptr, h->uprev)) != LBM_OK) return st;
     }
     if ((st = lbm_step(h, K)) != LBM_OK) return st;
     if ((st = run_moments(h, nullptr, nullptr, h->uprev)) != LBM_OK) return st;
-    double red[kPartials];
+    double red[7];
     LBM_CUDA(h, cudaMemcpyAsync(red, h->red_dev, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->uprev_step = h->step;
@@ -477,6 +499,21 @@ lbm_status lbm_residual(lbm_handle *h, int K, double *r) {
         return fail(h, LBM_ERR_UNSTABLE, "non-finite velocity");
     }
     *r = red[5] > 0.0 ? std::sqrt(red[4]) / ((double)K * std::sqrt(red[5])) : (red[4] > 0.0 ? INFINITY : 0.0);
+    return LBM_OK;
+}
+
+lbm_status lbm_check_device(lbm_handle *h, double *out_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!out_dev) return fail(h, LBM_ERR_ARG, "out_dev is NULL");
+    if (!h->uprev) {
+        const size_t bytes = (size_t)h->D * h->N() * arith_bytes(h->storage);
+        lbm_status st = alloc_into(h, &h->uprev, bytes, "residual velocity");
+        if (st != LBM_OK) return st;
+        LBM_CUDA(h, cudaMemsetAsync(h->uprev, 0, bytes, h->stream));
+    }
+    lbm_status st = run_moments(h, nullptr, nullptr, h->uprev, out_dev);
+    if (st != LBM_OK) return st;
+    h->uprev_step = h->step;
     return LBM_OK;
 }
 
@@ -536,6 +573,65 @@ lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t 
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->step = step;
     h->uprev_step = -1;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!(block_x == 32 || block_x == 64 || block_x == 128 || block_x == 256))
+        return fail(h, LBM_ERR_ARG, "block_x must be 32, 64, 128 or 256");
+    if (nodes_per_thread != 1 && nodes_per_thread != 2) return fail(h, LBM_ERR_ARG, "nodes_per_thread must be 1 or 2");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->cfg.bdx = block_x;
+    h->cfg.npt = nodes_per_thread;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (trials < 1) return fail(h, LBM_ERR_ARG, "trials must be >= 1");
+    const Launchers &L = launchers_for(h->lattice);
+    static const int shapes[][2] = {{32, 1}, {64, 1}, {64, 2}, {128, 1}, {128, 2}, {256, 1}, {256, 2}};
+    cudaEvent_t e0, e1;
+    LBM_CUDA(h, cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(h, e, "cudaEventCreate");
+    }
+    double best = 1e300;
+    StepCfg best_cfg = h->cfg;
+    for (const auto &sh : shapes) {
+        StepCfg c{sh[0], sh[1]};
+        // one untimed launch, then the timed ones; all read the state and
+        // write the spare buffer
+        e = L.step(h->collision, h->storage, h->mask, c, h->kp, h->buf[h->cur], h->buf[1 - h->cur], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t)
+            e = L.step(h->collision, h->storage, h->mask, c, h->kp, h->buf[h->cur], h->buf[1 - h->cur], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t_ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const double per = (double)t_ms / trials;
+        if (per < best) {
+            best = per;
+            best_cfg = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    lbm_status st = lbm_set_launch(h, best_cfg.bdx, best_cfg.npt);
+    if (st != LBM_OK) return st;
+    if (block_x) *block_x = best_cfg.bdx;
+    if (nodes_per_thread) *nodes_per_thread = best_cfg.npt;
+    if (ms) *ms = best;
     return LBM_OK;
 }
 
