@@ -146,8 +146,12 @@ lbm_status lbm_get_populations(lbm_handle *h, double *f);
  * storage format). */
 lbm_status lbm_set_populations(lbm_handle *h, const double *f);
 
-/* Raw checkpoint of the state in the storage format (opaque layout, size
- * lbm_state_bytes) plus the step counter; restore is bit-exact. */
+/* Raw checkpoint of the state in the storage format plus the step counter;
+ * restore is bit-exact.  Layout of the lbm_state_bytes bytes: the deviations
+ * fbar_{i,p} - w_i of the post-collision populations of the last step (the
+ * values the next step pulls), in the storage type (double, float, IEEE
+ * half or bfloat16), as [Q][nz][ny][nxp] with rows padded to
+ * nxp = 32 * ceil(nx / 32) (padding entries are zero). */
 size_t lbm_state_bytes(const lbm_handle *h);
 lbm_status lbm_get_state(lbm_handle *h, void *host, size_t bytes, int64_t *step);
 lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t step);
@@ -170,6 +174,40 @@ lbm_status lbm_info(const lbm_handle *h, int *D, int *Q, int64_t *step, size_t *
 
 void lbm_destroy(lbm_handle *h);
 const char *lbm_last_error(const lbm_handle *h);
+
+/* lbm_check_noalloc -- the FP64 check of lbm_check_device for callers that
+ * cannot allocate device memory.  The paper has no counterpart: it is a
+ * service of this library.
+ *
+ * Who needs it: code that receives device pointers but may not own device
+ * memory (plug-ins driven by a host framework), processes whose device
+ * memory is already reserved by a pooling allocator, and fixed-budget or
+ * latency-critical loops where cudaMalloc (which can fail and synchronises
+ * the device) is not allowed.  lbm_create allocates, so such callers hold the
+ * state in their own buffer and call this function with it.
+ *
+ * Inputs: desc (lattice, storage, nx, ny, nz, periodic, force_kind and, for
+ * LBM_G_UNIFORM, the D host values in desc->g; collision and tau are not
+ * used; desc->stream is ignored), state_dev: a device buffer in the
+ * lbm_get_state layout above.  Output: out_dev, 7 device doubles
+ *   {M, Px, Py, Pz, sum |u - u_snap|^2, sum |u|^2, non-finite nodes}
+ * as lbm_check_device writes them.  stream: cudaStream_t or NULL.
+ *
+ * Limits: no solid mask (LBM_ERR_ARG), force NONE or UNIFORM only, and the
+ * velocity snapshot D * nx * ny * nz * (8 for LBM_F64, else 4) bytes must fit
+ * in 16 MiB - 128 KiB (about 2.08 million nodes for D2Q9 in FP32);
+ * larger problems are rejected with LBM_ERR_ARG before any device work.
+ *
+ * Memory: nothing is allocated.  Scratch (partial sums, the force, the
+ * snapshot) lives in one static 16 MiB device array that every GPU which
+ * loads this library holds until the process exits.  The first call on a
+ * device sets up that device (looks up the array's address and clears it,
+ * synchronously), so make it before any stream capture on that device.
+ * All calls on a device share the array, which keeps the last call's
+ * snapshot: the residual entries compare with the velocity of the previous
+ * call on the same device (zero before the first one).  Calls that overlap
+ * on the GPU (different streams without ordering) race on the array. */
+lbm_status lbm_check_noalloc(const lbm_desc *desc, const void *state_dev, double *out_dev, void *stream);
 
 #ifdef __cplusplus
 }

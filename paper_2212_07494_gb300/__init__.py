@@ -17,5 +17,5 @@ from ._binding import (  # noqa: F401
     lbm_create, lbm_destroy, lbm_step, lbm_moments, lbm_moments_device, lbm_residual,
     lbm_check_device,
     lbm_set_force, lbm_get_populations, lbm_set_populations, lbm_state_bytes, lbm_get_state,
-    lbm_set_state, lbm_info, lbm_last_error, lbm_set_launch, lbm_autotune, library, library_path,
+    lbm_set_state, lbm_info, lbm_last_error, lbm_set_launch, lbm_autotune, lbm_check_noalloc, library, library_path,
     make_desc)

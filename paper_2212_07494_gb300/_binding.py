@@ -77,6 +77,7 @@ def library():
                            C.POINTER(C.c_size_t)]
     L.lbm_set_launch.argtypes = [H, C.c_int, C.c_int]
     L.lbm_autotune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.lbm_check_noalloc.argtypes = [C.POINTER(lbm_desc), C.c_void_p, C.c_void_p, C.c_void_p]
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [H]
@@ -84,7 +85,7 @@ def library():
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
               "lbm_check_device",
               "lbm_set_force", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
-              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune"):
+              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc"):
         getattr(L, n).restype = C.c_int
     _lib = L
     return L
@@ -235,6 +236,11 @@ def lbm_autotune(h, trials=20):
     bx, npt, ms = C.c_int(), C.c_int(), C.c_double()
     _check(library().lbm_autotune(h, int(trials), C.byref(bx), C.byref(npt), C.byref(ms)), h)
     return bx.value, npt.value, ms.value
+
+
+def lbm_check_noalloc(desc, state_ptr, out_ptr, stream=None):
+    """Allocation-free FP64 check of a caller-held state buffer (see lbm.h)."""
+    _check(library().lbm_check_noalloc(C.byref(desc), state_ptr, out_ptr, stream))
 
 
 def lbm_last_error(h=None):

@@ -44,6 +44,9 @@ const Launchers &launchers_d3q27();
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s);
 
+// record a message for lbm_last_error(NULL) (thread-local)
+void set_thread_error(const char *msg);
+
 inline int moments_grid(const KParams &p) {
     const long long items = (long long)((p.nx + kMomBlock - 1) / kMomBlock) * p.ny * p.nz;
     return (int)(items < kMomGridMax ? items : kMomGridMax);

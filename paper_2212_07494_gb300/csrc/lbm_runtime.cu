@@ -61,6 +61,8 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
     k_finalize<<<1, 256, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
+
+void set_thread_error(const char *msg) { g_thread_err = msg; }
 }  // namespace lbm
 
 struct lbm_handle {

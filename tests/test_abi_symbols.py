@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -59,3 +60,21 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert b"tau" in lib.lbm_last_error(None)
     d, keep = P.make_desc("D2Q9", "BGK", (8, 8, 2), (1, 1, 0.8, 1, 1))  # nz must be 1 in 2-D
     assert lib.lbm_create(ctypes.byref(d), ctypes.byref(h)) == -1
+
+
+def test_check_noalloc_rejects_oversized_problems_before_device_work(lib):
+    """The allocation-free check refuses problems whose velocity snapshot
+    does not fit its static scratch, on the host, before touching a device."""
+    import paper_2212_07494_gb300 as P
+    desc, keep = P.make_desc("D2Q9", "SMRT", (4096, 4096, 1), (1, 1, 0.6, 1, 1), "F32", (1, 1, 1))
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_check_noalloc(desc, None, None, None)
+    assert e.value.status == -1
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_check_noalloc(desc, 1, 1, None)
+    assert e.value.status == -1 and "static scratch" in str(e.value)
+    desc, keep = P.make_desc("D2Q9", "SMRT", (64, 64, 1), (1, 1, 0.6, 1, 1), "F32", (1, 1, 1),
+                             solid=np.zeros(64 * 64, np.uint8))
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_check_noalloc(desc, 1, 1, None)
+    assert "solid" in str(e.value)
