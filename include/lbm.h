@@ -55,6 +55,7 @@ extern "C" {
 #endif
 
 typedef enum {
+    LBM_NOT_CONVERGED = 1, /* per-channel status: max_steps reached above tol */
     LBM_OK = 0,
     LBM_ERR_ARG = -1,      /* invalid argument (sizes, tau <= 1/2, null pointer) */
     LBM_ERR_CUDA = -2,     /* a CUDA call failed; see lbm_last_error */
@@ -174,6 +175,57 @@ lbm_status lbm_info(const lbm_handle *h, int *D, int *Q, int64_t *step, size_t *
 
 void lbm_destroy(lbm_handle *h);
 const char *lbm_last_error(const lbm_handle *h);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent D2Q9 lattices ("channels") of different sizes, relaxation
+ * times and forces, advanced together by ONE persistent kernel launch
+ * (captured in a CUDA graph): each time step of a channel is split into
+ * tiles of rows that any CTA may claim; a channel's next step starts when
+ * all tiles of its current step are done.  Every K steps a channel computes
+ * its residual r_K (as lbm_residual) and retires once r_K <= tol.
+ * Channels share lattice (D2Q9), collision and storage (LBM_F32 or LBM_F64);
+ * each takes its own nx, ny, periodic flags, tau and uniform (or no) force;
+ * no solid masks.  The descriptions' rho0/u0 are copied.  The stream of
+ * descs[0] is used (NULL => the library makes one). */
+typedef struct lbm_batch lbm_batch;
+
+lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out);
+
+/* Run every channel until r_K <= tol (status LBM_OK), a non-finite residual
+ * (LBM_ERR_UNSTABLE) or max_steps more steps (LBM_NOT_CONVERGED).  Outputs
+ * (n entries each, nullable): steps completed (the channel stops one step
+ * after the check that met tol), status, last residual.  Returns
+ * LBM_ERR_TIMEOUT if the kernel's bounded scan for work saw no progress
+ * anywhere for the scan limit (see lbm_batch_set_spin_limit); the channels
+ * then hold the state they had reached.  Synchronises. */
+lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_steps, int64_t *steps_out,
+                                   int *st_out, double *r_out);
+
+/* Advance every channel nsteps more steps (same launch, no convergence). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Re-initialise every channel from its description (step counters to 0). */
+lbm_status lbm_batch_reset(lbm_batch *b);
+
+/* Macroscopic fields / FP64 pre-collision populations of channel i (host
+ * layouts as for a single lattice).  Synchronise. */
+lbm_status lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u);
+lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f);
+
+/* Tiling: threads per CTA (64, 128, 256) and target nodes per tile (rows of a
+ * channel per tile = ceil(tile_nodes / nx)).  lbm_batch_autotune times every
+ * (block, tile) pair over `steps` steps, keeps the fastest, then resets the
+ * channels (tuning advances them). */
+lbm_status lbm_batch_set_tiles(lbm_batch *b, int block, int tile_nodes);
+lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nodes, double *ms_per_step);
+
+/* Scans for work without progress anywhere before the kernel stops with
+ * LBM_ERR_TIMEOUT (default 2^26). */
+lbm_status lbm_batch_set_spin_limit(lbm_batch *b, int64_t scans);
+
+lbm_status lbm_batch_info(const lbm_batch *b, int i, int64_t *steps, int *tiles, int *rows);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
 
 /* lbm_check_noalloc -- the FP64 check of lbm_check_device for callers that
  * cannot allocate device memory.  The paper has no counterpart: it is a

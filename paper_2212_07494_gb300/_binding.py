@@ -11,6 +11,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "liblbm_gb300.so")
 
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
+LBM_NOT_CONVERGED = 1
 LBM_BGK, LBM_SMRT = 0, 1
 LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT = 0, 1, 2, 3
 LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD = 0, 1, 2, 3
@@ -78,6 +79,22 @@ def library():
     L.lbm_set_launch.argtypes = [H, C.c_int, C.c_int]
     L.lbm_autotune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.lbm_check_noalloc.argtypes = [C.POINTER(lbm_desc), C.c_void_p, C.c_void_p, C.c_void_p]
+    B = C.c_void_p
+    L.lbm_batch_create.argtypes = [C.POINTER(lbm_desc), C.c_int, C.POINTER(B)]
+    L.lbm_batch_run_to_steady.argtypes = [B, C.c_double, C.c_int, C.c_int64, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.lbm_batch_step.argtypes = [B, C.c_int64]
+    L.lbm_batch_reset.argtypes = [B]
+    L.lbm_batch_moments.argtypes = [B, C.c_int, dp, dp]
+    L.lbm_batch_get_populations.argtypes = [B, C.c_int, dp]
+    L.lbm_batch_set_tiles.argtypes = [B, C.c_int, C.c_int]
+    L.lbm_batch_autotune.argtypes = [B, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.lbm_batch_set_spin_limit.argtypes = [B, C.c_int64]
+    L.lbm_batch_info.argtypes = [B, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_batch_last_error.argtypes = [B]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_destroy.argtypes = [B]
+    L.lbm_batch_destroy.restype = None
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [H]
@@ -85,7 +102,10 @@ def library():
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
               "lbm_check_device",
               "lbm_set_force", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
-              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc"):
+              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc",
+              "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
+              "lbm_batch_moments", "lbm_batch_get_populations", "lbm_batch_set_tiles", "lbm_batch_autotune",
+              "lbm_batch_set_spin_limit", "lbm_batch_info"):
         getattr(L, n).restype = C.c_int
     _lib = L
     return L
@@ -367,3 +387,132 @@ class Lattice:
 
     def __exit__(self, *a):
         self.close()
+
+
+# -------------------------------------------------------------------- batches
+def _bcheck(status, b=None):
+    if status != 0:
+        msg = library().lbm_batch_last_error(b) if b is not None else library().lbm_last_error(None)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def lbm_batch_create(descs):
+    arr = (lbm_desc * len(descs))(*descs)
+    b = C.c_void_p()
+    _bcheck(library().lbm_batch_create(arr, len(descs), C.byref(b)))
+    return b
+
+
+def lbm_batch_run_to_steady(b, n, tol, K, max_steps):
+    steps = (C.c_int64 * n)()
+    st = (C.c_int * n)()
+    r = (C.c_double * n)()
+    status = library().lbm_batch_run_to_steady(b, float(tol), int(K), int(max_steps), steps, st, r)
+    return status, np.array(steps[:], np.int64), np.array(st[:], np.int32), np.array(r[:])
+
+
+def lbm_batch_step(b, n):
+    _bcheck(library().lbm_batch_step(b, int(n)), b)
+
+
+def lbm_batch_reset(b):
+    _bcheck(library().lbm_batch_reset(b), b)
+
+
+def lbm_batch_moments(b, i, rho, u):
+    _bcheck(library().lbm_batch_moments(b, int(i), _dptr(rho), _dptr(u)), b)
+
+
+def lbm_batch_get_populations(b, i, f):
+    _bcheck(library().lbm_batch_get_populations(b, int(i), _dptr(f)), b)
+
+
+def lbm_batch_set_tiles(b, block, tile_nodes):
+    _bcheck(library().lbm_batch_set_tiles(b, int(block), int(tile_nodes)), b)
+
+
+def lbm_batch_autotune(b, steps):
+    bl, tn, ms = C.c_int(), C.c_int(), C.c_double()
+    _bcheck(library().lbm_batch_autotune(b, int(steps), C.byref(bl), C.byref(tn), C.byref(ms)), b)
+    return bl.value, tn.value, ms.value
+
+
+def lbm_batch_set_spin_limit(b, scans):
+    _bcheck(library().lbm_batch_set_spin_limit(b, int(scans)), b)
+
+
+def lbm_batch_info(b, i):
+    s, t, r = C.c_int64(), C.c_int(), C.c_int()
+    _bcheck(library().lbm_batch_info(b, int(i), C.byref(s), C.byref(t), C.byref(r)), b)
+    return s.value, t.value, r.value
+
+
+def lbm_batch_last_error(b):
+    m = library().lbm_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def lbm_batch_destroy(b):
+    library().lbm_batch_destroy(b)
+
+
+class Batch:
+    """Independent D2Q9 channels in one persistent launch.  ``channels`` is a
+    list of dicts with keys shape, tau, periodic, g (uniform), rho0, u0."""
+
+    def __init__(self, channels, collision="SMRT", storage="F32", stream=None):
+        self._keep = []
+        descs = []
+        for ch in channels:
+            d, keep = make_desc("D2Q9", collision, ch["shape"], ch["tau"], storage, ch.get("periodic", (1, 0, 1)),
+                                g=ch.get("g"), rho0=ch.get("rho0"), u0=ch.get("u0"), stream=stream)
+            descs.append(d)
+            self._keep.append(keep)
+        self.shapes = [tuple((list(ch["shape"]) + [1, 1])[:3]) for ch in channels]
+        self.n = len(descs)
+        self.b = lbm_batch_create(descs)
+
+    def run_to_steady(self, tol, K=1000, max_steps=10 ** 7):
+        return lbm_batch_run_to_steady(self.b, self.n, tol, K, max_steps)
+
+    def step(self, n):
+        lbm_batch_step(self.b, n)
+
+    def reset(self):
+        lbm_batch_reset(self.b)
+
+    def moments(self, i):
+        nx, ny, _ = self.shapes[i]
+        rho = np.empty(nx * ny)
+        u = np.empty(2 * nx * ny)
+        lbm_batch_moments(self.b, i, rho, u)
+        return rho.reshape(1, ny, nx), u.reshape(2, 1, ny, nx)
+
+    def populations(self, i):
+        nx, ny, _ = self.shapes[i]
+        f = np.empty(9 * nx * ny)
+        lbm_batch_get_populations(self.b, i, f)
+        return f.reshape(9, 1, ny, nx)
+
+    def set_tiles(self, block, tile_nodes):
+        lbm_batch_set_tiles(self.b, block, tile_nodes)
+
+    def autotune(self, steps=200):
+        return lbm_batch_autotune(self.b, steps)
+
+    def set_spin_limit(self, scans):
+        lbm_batch_set_spin_limit(self.b, scans)
+
+    def info(self, i):
+        return lbm_batch_info(self.b, i)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

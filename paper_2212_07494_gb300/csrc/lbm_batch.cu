@@ -1,0 +1,742 @@
+// lbm_batch.cu -- many independent D2Q9 lattices (channels of uneven size and
+// parameters) advanced by ONE persistent kernel until each reaches its
+// steady-state residual.
+//
+// Work unit: a tile = a band of rows of one channel for one time step.  A CTA
+// claims a tile through the channel's packed word (step << 32 | next tile),
+// pulls, collides and stores it, then counts it done; the CTA finishing the
+// last tile of a step closes the step: at check steps it sums the tiles' FP64
+// residual partials in tile order, decides convergence, and publishes the next
+// step (or retires the channel).  Steps of one channel are thus ordered by the
+// done counter; different channels run independently.  No CTA waits for a
+// particular other CTA: a CTA that finds nothing to claim scans again, and the
+// scan is bounded by a no-progress counter that sets an error flag and exits.
+// Population data written during the kernel by other CTAs is read through L2
+// (ld.global.cg), never through the non-coherent read-only path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace lbm {
+
+struct BatchChan {
+    long long off;       // element offset of the channel's Q planes in each population arena
+    long long plane;     // nxp * ny
+    long long snap_off;  // offset (elements of the arithmetic type) of its velocity snapshot, 2 * nx * ny
+    long long part_off;  // offset (doubles) of its tile partials, 2 per tile
+    int nx, ny, nxp;
+    int per_x, per_y;
+    int tiles, rows;     // tiles per step and rows per tile
+    double om2, om3, om4;
+    double gx, gy;
+};
+
+struct BatchCtl {
+    unsigned long long claim;  // (step << 32) | next tile index
+    unsigned int done;         // tiles finished in the current step
+    int active;
+    long long steps;           // steps completed
+    long long start;           // steps completed when the run began
+    int status;
+    double r;                  // last residual
+};
+
+struct BatchRun {
+    const BatchChan *ch;
+    BatchCtl *ctl;
+    int n;
+    void *fa, *fb;  // the state after s steps lives in fa for even s, fb for odd s
+    void *snap;
+    double *part;
+    int *active_count;
+    unsigned long long *progress;
+    int *error;
+    double tol;     // < 0: never converge (fixed number of steps)
+    int K;
+    long long max_steps;   // per channel, counted from the run's start
+    long long spin_limit;  // scans without any progress anywhere before giving up
+};
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T *p);
+template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<float>(const float *p) { return __ldcg(p); }
+
+template <typename T>
+__device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
+
+// pull of one D2Q9 node of a channel (walls or periodic per axis); f is the
+// channel's base, all offsets within a channel fit in 32 bits
+template <int ST>
+__device__ __forceinline__ void gather_chan(const BatchChan &C, const typename Store<ST>::T *f, int x, int y,
+                                            typename Store<ST>::R *G) {
+    typedef typename Store<ST>::R R;
+    typedef typename Store<ST>::T T;
+    const int plane = (int)C.plane;
+    const int own = y * C.nxp + x;
+    const bool interior = x > 0 && x < C.nx - 1 && y > 0 && y < C.ny - 1;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = Lat<D2Q9>::cx(i), cy = Lat<D2Q9>::cy(i);
+        int idx;
+        if (interior) {
+            idx = i * plane + own - (cx + cy * C.nxp);
+        } else {
+            int sx = x - cx, sy = y - cy;
+            bool wall = false;
+            if (sx < 0) { if (C.per_x) sx += C.nx; else wall = true; }
+            else if (sx >= C.nx) { if (C.per_x) sx -= C.nx; else wall = true; }
+            if (sy < 0) { if (C.per_y) sy += C.ny; else wall = true; }
+            else if (sy >= C.ny) { if (C.per_y) sy -= C.ny; else wall = true; }
+            idx = wall ? opp<D2Q9>(i) * plane + own : i * plane + sy * C.nxp + sx;
+        }
+        G[gpos<D2Q9>(i)] = (R)ld_cg<T>(f + idx);
+    }
+}
+
+// sum of two doubles over the block (blockDim.x <= 256); thread 0 gets it
+__device__ __forceinline__ void block_sum_batch(double (&v)[2]) {
+    __shared__ double sh[8][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[wid][0] = v[0];
+        sh[wid][1] = v[1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[w][0];
+            b += sh[w][1];
+        }
+        v[0] = a;
+        v[1] = b;
+    }
+}
+
+// batch storage is FP32 or FP64 (loads through L2: ld.global.cg)
+template <int COLL, int ST>
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
+    typedef typename Store<ST>::T T;
+    typedef typename Store<ST>::R R;
+    __shared__ int s_c, s_tile, s_quit;
+    __shared__ long long s_step;
+    long long empty = 0;
+    unsigned long long seen = 0;
+    int cursor = blockIdx.x % r.n;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_c = -1;
+            s_quit = 0;
+            int c = cursor;
+            for (int k = 0; k < r.n; ++k, c = (c + 1 == r.n) ? 0 : c + 1) {
+                if (!vload(&r.ctl[c].active)) continue;
+                const int tiles = r.ch[c].tiles;
+                const unsigned long long w = vload(&r.ctl[c].claim);
+                if ((int)(w & 0xffffffffull) >= tiles) continue;
+                const unsigned long long w2 = atomicAdd(&r.ctl[c].claim, 1ull);
+                if ((int)(w2 & 0xffffffffull) < tiles) {
+                    s_c = c;
+                    s_step = (long long)(w2 >> 32);
+                    s_tile = (int)(w2 & 0xffffffffull);
+                    cursor = c;
+                    break;
+                }
+            }
+            if (s_c < 0) {
+                if (vload(r.active_count) == 0 || vload(r.error) != 0) {
+                    s_quit = 1;
+                } else {
+                    const unsigned long long pg = vload(r.progress);
+                    if (pg != seen) {
+                        seen = pg;
+                        empty = 0;
+                    } else if (++empty > r.spin_limit) {
+                        atomicExch(r.error, (int)LBM_ERR_TIMEOUT);
+                        s_quit = 1;
+                    }
+                    __nanosleep(200);
+                }
+            } else {
+                empty = 0;
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_quit) break;
+        const int c = s_c;
+        if (c >= 0) {
+            const BatchChan C = r.ch[c];
+            const long long step = s_step;
+            const int tile = s_tile;
+            const T *fin = (const T *)((step & 1) ? r.fb : r.fa) + C.off;
+            T *fout = (T *)((step & 1) ? r.fa : r.fb) + C.off;
+            const long long start = r.ctl[c].start;
+            const bool check = ((step - start) % r.K) == 0;
+            const int y0 = tile * C.rows;
+            const int y1 = min(y0 + C.rows, C.ny);
+            const int nn = (y1 - y0) * C.nx;
+            R *snap = (R *)r.snap + C.snap_off;
+            const int N = C.nx * C.ny;
+            const R om2 = R(C.om2), om3 = R(C.om3), om4 = R(C.om4), gx = R(C.gx), gy = R(C.gy);
+            double v[2] = {0.0, 0.0};
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+                const int yy = (int)((unsigned)idx / (unsigned)C.nx);
+                const int x = idx - yy * C.nx;
+                const int y = y0 + yy;
+                R G[9];
+                gather_chan<ST>(C, fin, x, y, G);
+                if (check) {
+                    R drho = 0, jx = 0, jy = 0;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const R w = G[gpos<D2Q9>(i)];
+                        drho += w;
+                        jx += Lat<D2Q9>::cx(i) * w;
+                        jy += Lat<D2Q9>::cy(i) * w;
+                    }
+                    const R rho = R(1) + drho;
+                    const R ux = jx / rho + R(0.5) * gx, uy = jy / rho + R(0.5) * gy;
+                    const int n = y * C.nx + x;
+                    const R dx = ux - ld_cg<R>(snap + n), dy = uy - ld_cg<R>(snap + N + n);
+                    v[0] += (double)(dx * dx + dy * dy);
+                    v[1] += (double)(ux * ux + uy * uy);
+                    snap[n] = ux;
+                    snap[N + n] = uy;
+                }
+                if (COLL == SMRT) collide_smrt<D2Q9>(G, gx, gy, R(0), om2, om3, om4);
+                else collide_bgk<D2Q9>(G, gx, gy, R(0), om2);
+                T *dst = fout + (y * C.nxp + x);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[gpos<D2Q9>(i)]);
+            }
+            if (check) {
+                block_sum_batch(v);
+                if (threadIdx.x == 0) {
+                    r.part[C.part_off + 2 * tile + 0] = v[0];
+                    r.part[C.part_off + 2 * tile + 1] = v[1];
+                }
+            }
+            // every thread orders its stores (populations, snapshot) at GPU
+            // scope before the tile is counted done
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned prev = atomicAdd(&r.ctl[c].done, 1u);
+                if (prev == (unsigned)(C.tiles - 1)) {
+                    // last tile of this step: close it
+                    __threadfence();
+                    const long long done_steps = step + 1;
+                    bool retire = false;
+                    int status = 0;
+                    if (check && step > start) {
+                        double num = 0.0, den = 0.0;
+                        for (int t = 0; t < C.tiles; ++t) {
+                            num += ld_cg<double>(r.part + C.part_off + 2 * t);
+                            den += ld_cg<double>(r.part + C.part_off + 2 * t + 1);
+                        }
+                        const double rr = den > 0.0 ? sqrt(num) / ((double)r.K * sqrt(den)) : (num > 0.0 ? INFINITY : 0.0);
+                        r.ctl[c].r = rr;
+                        if (!isfinite(num) || !isfinite(den)) {
+                            retire = true;
+                            status = (int)LBM_ERR_UNSTABLE;
+                        } else if (r.tol >= 0.0 && rr <= r.tol) {
+                            retire = true;
+                            status = (int)LBM_OK;
+                        }
+                    }
+                    if (!retire && done_steps - start >= r.max_steps) {
+                        retire = true;
+                        status = r.tol >= 0.0 ? (int)LBM_NOT_CONVERGED : (int)LBM_OK;
+                    }
+                    r.ctl[c].steps = done_steps;
+                    atomicExch(&r.ctl[c].done, 0u);
+                    if (retire) {
+                        r.ctl[c].status = status;
+                        __threadfence();
+                        atomicExch(&r.ctl[c].active, 0);
+                        atomicSub(r.active_count, 1);
+                    } else {
+                        __threadfence();
+                        atomicExch(&r.ctl[c].claim, (unsigned long long)done_steps << 32);
+                    }
+                    atomicAdd(r.progress, 1ull);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// start of a run: every channel active from its current step
+__global__ void k_batch_reset(BatchCtl *ctl, int n, int *active_count, unsigned long long *progress, int *error) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) {
+        const long long s = ctl[c].steps;
+        ctl[c].claim = (unsigned long long)s << 32;
+        ctl[c].done = 0u;
+        ctl[c].active = 1;
+        ctl[c].start = s;
+        ctl[c].status = 1;
+        ctl[c].r = -1.0;
+    }
+    if (c == 0) {
+        *active_count = n;
+        *progress = 0ull;
+        *error = 0;
+    }
+}
+
+}  // namespace lbm
+
+// ----------------------------------------------------------------- host side
+struct lbm_batch {
+    int n = 0;
+    int collision = 0, storage = 0;
+    std::vector<lbm_desc> desc;
+    std::vector<KParams> kp;    // per channel, pointing into the arenas
+    std::vector<BatchChan> ch;
+    std::vector<long long> steps;
+    void *fa = nullptr, *fb = nullptr, *snap = nullptr;
+    double *part = nullptr;
+    double *g_dev = nullptr;    // per channel 4 doubles
+    float *g32_dev = nullptr;   // per channel 4 floats
+    double *fields = nullptr;   // initial rho0 / u0, per channel, when given
+    std::vector<long long> field_off;
+    BatchChan *ch_dev = nullptr;
+    BatchCtl *ctl_dev = nullptr;
+    int *active_count = nullptr, *error = nullptr;
+    unsigned long long *progress = nullptr;
+    double *partials = nullptr, *red = nullptr, *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int block = 256, tile_nodes = 2048;
+    long long spin_limit = 1ll << 26;
+    size_t arena_elems = 0;
+    std::string err;
+};
+
+namespace {
+
+size_t elem_bytes(int st) { return st == LBM_F64 ? 8 : 4; }
+
+lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
+    if (b) b->err = m;
+    set_thread_error(m.c_str());
+    return st;
+}
+
+#define B_CUDA(b, call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e__ = (call);                                                             \
+        if (e__ != cudaSuccess)                                                               \
+            return bfail((b), e__ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,  \
+                         std::string(#call) + ": " + cudaGetErrorString(e__));                \
+    } while (0)
+
+template <typename T>
+lbm_status balloc(lbm_batch *b, T **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LBM_ERR_OOM, "device allocation failed");
+    }
+    *p = (T *)q;
+    return LBM_OK;
+}
+
+lbm_status build_tiles(lbm_batch *b) {
+    long long part_off = 0;
+    for (int c = 0; c < b->n; ++c) {
+        BatchChan &C = b->ch[c];
+        C.rows = std::max(1, std::min(C.ny, (b->tile_nodes + C.nx - 1) / C.nx));
+        C.tiles = (C.ny + C.rows - 1) / C.rows;
+        C.part_off = part_off;
+        part_off += 2LL * C.ny;  // room for the finest tiling (one row per tile)
+    }
+    B_CUDA(b, cudaMemcpyAsync(b->ch_dev, b->ch.data(), sizeof(BatchChan) * b->n, cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+typedef void (*BatchKernel)(const BatchRun);
+
+BatchKernel batch_kernel(int coll, int st) {
+    if (coll == LBM_SMRT) return st == LBM_F64 ? k_batch<SMRT, ST_F64> : k_batch<SMRT, ST_F32>;
+    return st == LBM_F64 ? k_batch<BGK, ST_F64> : k_batch<BGK, ST_F32>;
+}
+
+// one run: reset + persistent kernel, captured in a graph and launched once
+lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
+    BatchKernel kern = batch_kernel(b->collision, b->storage);
+    int dev = 0, sms = 0, per_sm = 0;
+    B_CUDA(b, cudaGetDevice(&dev));
+    B_CUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    B_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->block, 0));
+    if (per_sm < 1) return bfail(b, LBM_ERR_ARG, "batch block size does not fit on an SM");
+    BatchRun r;
+    r.ch = b->ch_dev;
+    r.ctl = b->ctl_dev;
+    r.n = b->n;
+    r.fa = b->fa;
+    r.fb = b->fb;
+    r.snap = b->snap;
+    r.part = b->part;
+    r.active_count = b->active_count;
+    r.progress = b->progress;
+    r.error = b->error;
+    r.tol = tol;
+    r.K = K;
+    r.max_steps = max_steps;
+    r.spin_limit = b->spin_limit;
+    const int grid = sms * per_sm;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    B_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    k_batch_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->ctl_dev, b->n, b->active_count, b->progress,
+                                                            b->error);
+    kern<<<grid, b->block, 0, b->stream>>>(r);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    e = cudaGraphLaunch(ge, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+    int errflag = 0;
+    B_CUDA(b, cudaMemcpy(&errflag, b->error, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<BatchCtl> ctl(b->n);
+    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < b->n; ++c) b->steps[c] = ctl[c].steps;
+    if (errflag) return bfail(b, (lbm_status)errflag, "batch kernel stopped: no progress within the scan limit");
+    return LBM_OK;
+}
+
+lbm_status init_channels(lbm_batch *b) {
+    const Launchers &L = launchers_d2q9();
+    std::vector<BatchCtl> ctl(b->n);
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_desc &d = b->desc[c];
+        const double *rho0 = d.rho0 ? b->fields + b->field_off[c] : nullptr;
+        const double *u0 = d.u0 ? b->fields + b->field_off[c] + (size_t)d.nx * d.ny : nullptr;
+        const size_t eb = elem_bytes(b->storage);
+        void *A = (char *)b->fa + b->ch[c].off * eb;
+        void *B = (char *)b->fb + b->ch[c].off * eb;
+        cudaError_t e = L.init(b->collision, b->storage, false, b->kp[c], rho0, u0, B, b->stream);
+        if (e == cudaSuccess) e = L.unstream(b->storage, false, b->kp[c], B, A, b->stream);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch init: ") + cudaGetErrorString(e));
+        b->steps[c] = 0;
+        ctl[c] = BatchCtl{};
+    }
+    size_t snap_elems = 0;
+    for (int c = 0; c < b->n; ++c) snap_elems += 2ull * b->ch[c].nx * b->ch[c].ny;
+    B_CUDA(b, cudaMemsetAsync(b->snap, 0, snap_elems * elem_bytes(b->storage), b->stream));
+    B_CUDA(b, cudaMemcpyAsync(b->ctl_dev, ctl.data(), sizeof(BatchCtl) * b->n, cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+const void *channel_state(const lbm_batch *b, int c) {
+    const size_t eb = elem_bytes(b->storage);
+    return (const char *)((b->steps[c] & 1) ? b->fb : b->fa) + b->ch[c].off * eb;
+}
+
+lbm_status ensure_tmp(lbm_batch *b, size_t bytes) {
+    if (b->tmp_bytes >= bytes) return LBM_OK;
+    if (b->tmp) cudaFree(b->tmp);
+    b->tmp = nullptr;
+    b->tmp_bytes = 0;
+    lbm_status st = balloc(b, &b->tmp, bytes);
+    if (st == LBM_OK) b->tmp_bytes = bytes;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    void *ptrs[] = {b->fa, b->fb, b->snap, b->part, b->g_dev, b->g32_dev, b->fields, b->ch_dev, b->ctl_dev,
+                    b->active_count, b->error, b->progress, b->partials, b->red, b->tmp};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1) return bfail(nullptr, LBM_ERR_ARG, "need at least one description");
+    const lbm_desc &d0 = descs[0];
+    if (d0.lattice != LBM_D2Q9) return bfail(nullptr, LBM_ERR_ARG, "batches are D2Q9");
+    if (d0.storage != LBM_F32 && d0.storage != LBM_F64) return bfail(nullptr, LBM_ERR_ARG, "batch storage is F32 or F64");
+    if (d0.collision != LBM_BGK && d0.collision != LBM_SMRT) return bfail(nullptr, LBM_ERR_ARG, "bad collision");
+    for (int c = 0; c < n; ++c) {
+        const lbm_desc &d = descs[c];
+        if (d.lattice != d0.lattice || d.collision != d0.collision || d.storage != d0.storage)
+            return bfail(nullptr, LBM_ERR_ARG, "channels must share lattice, collision and storage");
+        if (d.nx < 1 || d.ny < 1 || d.nz != 1 || d.ny > 65535) return bfail(nullptr, LBM_ERR_ARG, "bad channel sizes");
+        if (d.solid) return bfail(nullptr, LBM_ERR_ARG, "batch channels take no solid mask");
+        if (d.force_kind != LBM_G_NONE && d.force_kind != LBM_G_UNIFORM)
+            return bfail(nullptr, LBM_ERR_ARG, "batch channels take a uniform force or none");
+        if (d.force_kind == LBM_G_UNIFORM && !d.g) return bfail(nullptr, LBM_ERR_ARG, "force values are NULL");
+        if (d.collision == LBM_BGK && !(d.tau[2] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2] must be > 1/2");
+        if (d.collision == LBM_SMRT)
+            for (int k = 2; k <= 4; ++k)
+                if (!(d.tau[k] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");
+    }
+    lbm_batch *b = new lbm_batch();
+    b->n = n;
+    b->collision = d0.collision;
+    b->storage = d0.storage;
+    b->desc.assign(descs, descs + n);
+    b->ch.resize(n);
+    b->kp.resize(n);
+    b->steps.assign(n, 0);
+    b->field_off.assign(n, 0);
+    lbm_status st = LBM_OK;
+    if (d0.stream) {
+        b->stream = (cudaStream_t)d0.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    long long off = 0, snap_off = 0, parts = 0, fields = 0;
+    for (int c = 0; c < n; ++c) {
+        const lbm_desc &d = descs[c];
+        BatchChan &C = b->ch[c];
+        C.nx = d.nx;
+        C.ny = d.ny;
+        C.nxp = (d.nx + 31) / 32 * 32;
+        C.plane = (long long)C.nxp * d.ny;
+        C.off = off;
+        off += 9LL * C.plane;
+        C.snap_off = snap_off;
+        snap_off += 2LL * d.nx * d.ny;
+        parts += 2LL * d.ny;
+        C.per_x = d.periodic[0] ? 1 : 0;
+        C.per_y = d.periodic[1] ? 1 : 0;
+        C.om2 = 1.0 / d.tau[2];
+        C.om3 = d.collision == LBM_SMRT ? 1.0 / d.tau[3] : 0.0;
+        C.om4 = d.collision == LBM_SMRT ? 1.0 / d.tau[4] : 0.0;
+        C.gx = d.force_kind == LBM_G_UNIFORM ? d.g[0] : 0.0;
+        C.gy = d.force_kind == LBM_G_UNIFORM ? d.g[1] : 0.0;
+        b->field_off[c] = fields;
+        if (d.rho0 || d.u0) fields += 3LL * d.nx * d.ny;
+    }
+    b->arena_elems = (size_t)off;
+    const size_t eb = elem_bytes(b->storage);
+    if ((st = balloc(b, &b->fa, (size_t)off * eb)) || (st = balloc(b, &b->fb, (size_t)off * eb)) ||
+        (st = balloc(b, &b->snap, (size_t)snap_off * eb)) || (st = balloc(b, &b->part, (size_t)parts * 8)) ||
+        (st = balloc(b, &b->g_dev, (size_t)n * 4 * 8)) || (st = balloc(b, &b->g32_dev, (size_t)n * 4 * 4)) ||
+        (st = balloc(b, &b->ch_dev, sizeof(BatchChan) * n)) || (st = balloc(b, &b->ctl_dev, sizeof(BatchCtl) * n)) ||
+        (st = balloc(b, &b->active_count, 16)) || (st = balloc(b, &b->error, 16)) ||
+        (st = balloc(b, &b->progress, 16)) ||
+        (st = balloc(b, &b->partials, (size_t)kMomGridMax * kPartials * 8)) || (st = balloc(b, &b->red, 64)) ||
+        (fields && (st = balloc(b, &b->fields, (size_t)fields * 8)))) {
+        std::string m = b->err;
+        lbm_batch_destroy(b);
+        return bfail(nullptr, st, m);
+    }
+    // per-channel force copies and launch parameters for the shared kernels
+    std::vector<double> g(4 * (size_t)n, 0.0);
+    std::vector<float> g32(4 * (size_t)n, 0.f);
+    for (int c = 0; c < n; ++c) {
+        g[4 * c + 0] = b->ch[c].gx;
+        g[4 * c + 1] = b->ch[c].gy;
+        g32[4 * c + 0] = (float)b->ch[c].gx;
+        g32[4 * c + 1] = (float)b->ch[c].gy;
+        const lbm_desc &d = descs[c];
+        KParams &k = b->kp[c];
+        k = KParams{};
+        k.nx = d.nx;
+        k.ny = d.ny;
+        k.nz = 1;
+        k.nxp = b->ch[c].nxp;
+        k.plane = b->ch[c].plane;
+        k.per[0] = b->ch[c].per_x;
+        k.per[1] = b->ch[c].per_y;
+        k.per[2] = 1;
+        k.force_kind = d.force_kind == LBM_G_UNIFORM ? G_UNIFORM : G_NONE;
+        k.g = b->g_dev + 4 * c;
+        k.g32 = b->g32_dev + 4 * c;
+        for (int m = 0; m < 5; ++m) {
+            k.om[m] = d.tau[m] > 0.0 ? 1.0 / d.tau[m] : 0.0;
+            k.om32[m] = (float)k.om[m];
+        }
+        fill_offsets<D2Q9>(k);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->g_dev, g.data(), g.size() * 8, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->g32_dev, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->fa, 0, (size_t)off * eb, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->fb, 0, (size_t)off * eb, b->stream);
+    for (int c = 0; c < n && e == cudaSuccess; ++c) {
+        const lbm_desc &d = descs[c];
+        const size_t N = (size_t)d.nx * d.ny;
+        if (d.rho0 || d.u0) {
+            std::vector<double> f(3 * N, 0.0);
+            for (size_t i = 0; i < N; ++i) f[i] = d.rho0 ? d.rho0[i] : 1.0;
+            if (d.u0)
+                for (size_t i = 0; i < 2 * N; ++i) f[N + i] = d.u0[i];
+            e = cudaMemcpyAsync(b->fields + b->field_off[c], f.data(), f.size() * 8, cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return bfail(nullptr, LBM_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    }
+    if ((st = build_tiles(b)) != LBM_OK || (st = init_channels(b)) != LBM_OK) {
+        std::string m = b->err;
+        lbm_batch_destroy(b);
+        return bfail(nullptr, st, m);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_reset(lbm_batch *b) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    return init_channels(b);
+}
+
+lbm_status lbm_batch_set_tiles(lbm_batch *b, int block, int tile_nodes) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (!(block == 64 || block == 128 || block == 256)) return bfail(b, LBM_ERR_ARG, "block must be 64, 128 or 256");
+    if (tile_nodes < 32 || tile_nodes > (1 << 20)) return bfail(b, LBM_ERR_ARG, "tile_nodes out of range");
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    b->block = block;
+    b->tile_nodes = tile_nodes;
+    return build_tiles(b);
+}
+
+lbm_status lbm_batch_set_spin_limit(lbm_batch *b, int64_t scans) {
+    if (!b || scans < 1) return bfail(b, LBM_ERR_ARG, "bad spin limit");
+    b->spin_limit = scans;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    return batch_run(b, -1.0, 1 << 30, nsteps);
+}
+
+lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_steps, int64_t *steps_out,
+                                   int *st_out, double *r_out) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (!(tol >= 0.0) || K < 1 || max_steps < 1) return bfail(b, LBM_ERR_ARG, "need tol >= 0, K >= 1, max_steps >= 1");
+    lbm_status st = batch_run(b, tol, K, max_steps);
+    if (st != LBM_OK && st != LBM_ERR_TIMEOUT) return st;
+    std::vector<BatchCtl> ctl(b->n);
+    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < b->n; ++c) {
+        if (steps_out) steps_out[c] = ctl[c].steps;
+        if (st_out) st_out[c] = ctl[c].status;
+        if (r_out) r_out[c] = ctl[c].r;
+    }
+    return st;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nodes, double *ms) {
+    if (!b || steps < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    static const int blocks[] = {128, 256};
+    static const int tiles[] = {512, 1024, 2048, 4096, 8192};
+    cudaEvent_t e0, e1;
+    B_CUDA(b, cudaEventCreate(&e0));
+    B_CUDA(b, cudaEventCreate(&e1));
+    double best = 1e300;
+    int bb = b->block, bt = b->tile_nodes;
+    lbm_status st = LBM_OK;
+    for (int bl : blocks)
+        for (int tn : tiles) {
+            if ((st = lbm_batch_set_tiles(b, bl, tn)) != LBM_OK) break;
+            if (cudaEventRecord(e0, b->stream) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
+            if ((st = lbm_batch_step(b, steps)) != LBM_OK) break;
+            float t = 0.f;
+            if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                st = LBM_ERR_CUDA;
+                break;
+            }
+            if (t < best) {
+                best = t;
+                bb = bl;
+                bt = tn;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    if ((st = lbm_batch_set_tiles(b, bb, bt)) != LBM_OK) return st;
+    if ((st = init_channels(b)) != LBM_OK) return st;  // tuning advanced the state: start again
+    if (block) *block = bb;
+    if (tile_nodes) *tile_nodes = bt;
+    if (ms) *ms = best / steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u) {
+    if (!b || i < 0 || i >= b->n) return bfail(b, LBM_ERR_ARG, "bad channel index");
+    const lbm_desc &d = b->desc[i];
+    const size_t N = (size_t)d.nx * d.ny;
+    lbm_status st = ensure_tmp(b, 3 * N * 8);
+    if (st != LBM_OK) return st;
+    int nb = 0;
+    cudaError_t e = launchers_d2q9().moments(b->storage, false, b->kp[i], channel_state(b, i), b->tmp, b->tmp + N,
+                                             b->partials, nullptr, b->stream, &nb);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, b->tmp, N * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, b->tmp + N, 2 * N * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch moments: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f) {
+    if (!b || i < 0 || i >= b->n || !f) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    const lbm_desc &d = b->desc[i];
+    const size_t N = (size_t)d.nx * d.ny;
+    lbm_status st = ensure_tmp(b, 9 * N * 8);
+    if (st != LBM_OK) return st;
+    cudaError_t e = launchers_d2q9().get_pops(b->storage, false, b->kp[i], channel_state(b, i), b->tmp, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, b->tmp, 9 * N * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch export: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch *b, int i, int64_t *steps, int *tiles, int *rows) {
+    if (!b || i < 0 || i >= b->n) return bfail(nullptr, LBM_ERR_ARG, "bad channel index");
+    if (steps) *steps = b->steps[i];
+    if (tiles) *tiles = b->ch[i].tiles;
+    if (rows) *rows = b->ch[i].rows;
+    return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+"""Batched persistent launch: every channel must evolve exactly as it does on
+its own (same kernels' arithmetic), match the FP64 oracle in FP64, stop on
+the same residual check as the plain run-to-steady loop, and report a
+bounded-wait timeout as an error status without harming the context."""
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+import oracle as O
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _channels(n, seed, nx=(5, 90), ny=(3, 40)):
+    rng = W.SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        cx, cy = rng.randint(*nx), rng.randint(*ny)
+        t2 = 0.55 + 0.9 * rng.uniform(1)[0]
+        gx = 10 ** (-7 + 2 * rng.uniform(1)[0])
+        out.append({"shape": (cx, cy, 1), "tau": (1.0, 1.0, t2, 1.0, 1.0), "periodic": (1, 0, 1), "g": [gx, 0.0]})
+    return out
+
+
+@pytest.mark.parametrize("coll,storage", [("SMRT", "F32"), ("BGK", "F32"), ("SMRT", "F64")])
+def test_batch_matches_single_lattices(coll, storage):
+    import paper_2212_07494_gb300 as P
+    chans = _channels(12, 7)
+    # a channel with initial velocity, to exercise rho0/u0 upload
+    rho0, u0 = W.random_near_equilibrium("D2Q9", (33, 17, 1), seed=4, du=0.01)
+    chans.append({"shape": (33, 17, 1), "tau": (1, 1, 0.7, 0.9, 1.1), "periodic": (1, 1, 1), "g": [1e-5, -2e-6],
+                  "rho0": rho0, "u0": u0})
+    b = P.Batch(chans, coll, storage)
+    b.set_tiles(128, 256)   # several tiles per step for the larger channels
+    b.step(37)
+    for i, ch in enumerate(chans):
+        s = P.Lattice("D2Q9", coll, ch["shape"], ch["tau"], storage, ch["periodic"], g=ch["g"],
+                      rho0=ch.get("rho0"), u0=ch.get("u0"))
+        s.step(37)
+        fb, fs = b.populations(i), s.populations()
+        tol = 1e-15 if storage == "F64" else 2e-7 * np.abs(fs - fs.mean()).max()
+        assert np.abs(fb - fs).max() <= tol, (i, np.abs(fb - fs).max())
+        assert b.info(i)[0] == 37
+        s.close()
+    b.close()
+
+
+def test_batch_channel_matches_oracle_f64():
+    import paper_2212_07494_gb300 as P
+    chans = _channels(6, 11)
+    b = P.Batch(chans, "SMRT", "F64")
+    b.step(150)
+    for i, ch in enumerate(chans):
+        orc = O.Sim(O.D2Q9, O.SMRT, ch["shape"], ch["periodic"], ch["tau"], g=ch["g"])
+        orc.step(150)
+        _, ub = b.moments(i)
+        _, uo, _ = orc.moments()
+        assert rel_l2(ub, uo) < 1e-12
+    b.close()
+
+
+def test_run_to_steady_agrees_with_plain_loop():
+    """Fast-converging channels (large viscosity, narrow): the batch stops one
+    step after the check that meets tol, at the same residual as a plain
+    lbm_residual loop on the same channel."""
+    import paper_2212_07494_gb300 as P
+    chans = [{"shape": (nx, ny, 1), "tau": (1, 1, t, 1, 1), "periodic": (1, 0, 1), "g": [g, 0.0]}
+             for nx, ny, t, g in [(40, 12, 1.4, 1e-5), (17, 9, 1.2, 3e-6), (64, 16, 1.5, 1e-6), (8, 5, 0.9, 1e-5)]]
+    tol, K = 1e-6, 100
+    b = P.Batch(chans, "SMRT", "F32")
+    status, steps, st, r = b.run_to_steady(tol, K, max_steps=200000)
+    assert status == 0
+    assert np.all(st == 0), st
+    for i, ch in enumerate(chans):
+        s = P.Lattice("D2Q9", "SMRT", ch["shape"], ch["tau"], "F32", ch["periodic"], g=ch["g"])
+        n = 0
+        while True:
+            rr = s.residual(K)
+            n += K
+            if rr <= tol:
+                break
+        assert steps[i] == n + 1, (i, steps[i], n)
+        assert abs(r[i] - rr) <= 1e-6 * rr, (r[i], rr)
+        s.close()
+    b.close()
+
+
+def test_run_to_steady_reports_not_converged():
+    import paper_2212_07494_gb300 as P
+    chans = _channels(5, 3)
+    b = P.Batch(chans, "SMRT", "F32")
+    status, steps, st, r = b.run_to_steady(1e-30, 50, max_steps=400)
+    assert status == 0
+    assert np.all(st == P.LBM_NOT_CONVERGED) and np.all(steps == 400)
+    b.close()
+
+
+def test_bounded_scan_times_out_cleanly():
+    """With a scan limit of one, CTAs that find no tile to claim give up at
+    once: the run returns LBM_ERR_TIMEOUT (no hang, no fault) and the batch
+    stays usable."""
+    import paper_2212_07494_gb300 as P
+    chans = _channels(2, 5, nx=(40, 60), ny=(8, 12))
+    b = P.Batch(chans, "SMRT", "F32")
+    b.set_spin_limit(1)
+    status, steps, st, r = b.run_to_steady(0.0, 10, max_steps=100000)
+    assert status == -5, status
+    b.set_spin_limit(1 << 26)
+    b.reset()
+    b.step(10)
+    assert all(b.info(i)[0] == 10 for i in range(len(chans)))
+    b.close()
+
+
+def test_batch_autotune_and_reset():
+    import paper_2212_07494_gb300 as P
+    chans = _channels(20, 9)
+    b = P.Batch(chans, "SMRT", "F32")
+    bl, tn, ms = b.autotune(20)
+    assert bl in (128, 256) and tn in (512, 1024, 2048, 4096, 8192) and ms > 0
+    assert all(b.info(i)[0] == 0 for i in range(len(chans)))
+    b.close()
