@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch"],
+                    help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady state")
+    ap.add_argument("--plain-stride", type=int, default=16, help="batch: every n-th channel runs the plain solver")
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--K", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -369,6 +374,87 @@ def run_e2e(P, torch, wl, n, steps, C, local, ws, dist):
             "what": "lbm_create from host u0/g, lbm_residual every check interval, lbm_moments to host"}
 
 
+def run_batch(args, ws, rank, local):
+    """512 independent force-driven channels (periodic x, walls in y; seeded
+    sizes, tau_2 and g_x) run to the K-step residual tol: one persistent
+    launch for all channels vs the plain solver (one lattice at a time,
+    lbm_residual every K steps) on every plain-stride-th channel, its time
+    scaled to all channels.  Equal error: both stop at the same r_K <= tol;
+    the final fields of the two are compared channel by channel."""
+    import torch
+
+    import paper_2212_07494_gb300 as P
+
+    torch.cuda.set_device(local)
+    chans = W.batch_channels()
+    spec = [{"shape": (c.nx, c.ny, 1), "tau": (1.0, 1.0, c.tau2, 1.0, 1.0), "periodic": (1, 0, 1),
+             "g": [c.gx, 0.0]} for c in chans]
+    b = P.Batch(spec, "SMRT", "F32")
+    block, tile, ms_tune = b.autotune(200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, steps, st, r = b.run_to_steady(args.tol, args.K, max_steps=50_000_000)
+    t_batch = time.perf_counter() - t0
+    nodes = np.array([c.nx * c.ny for c in chans], np.float64)
+    updates = float((steps * nodes).sum())
+    idx = list(range(0, len(chans), max(1, args.plain_stride)))
+    t_plain = 0.0
+    errs, plain_steps = [], []
+    for i in idx:
+        sp = spec[i]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat = P.Lattice("D2Q9", "SMRT", sp["shape"], sp["tau"], "F32", sp["periodic"], g=sp["g"])
+        n = 0
+        while True:
+            rr = lat.residual(args.K)
+            n += args.K
+            if rr <= args.tol or n >= 50_000_000:
+                break
+        _, u_plain, _ = lat.moments()
+        t_plain += time.perf_counter() - t1
+        lat.close()
+        plain_steps.append(n)
+        _, u_b = b.moments(i)
+        errs.append(float(np.linalg.norm(u_b - u_plain) / np.linalg.norm(u_plain)))
+    scale = len(chans) / len(idx)
+    t_plain_est = t_plain * scale
+    # distance of each steady profile from the no-slip Poiseuille parabola
+    # (mean over x), an accuracy statement independent of both solvers
+    para = []
+    for i, c in enumerate(chans):
+        _, u = b.moments(i)
+        nu = (c.tau2 - 0.5) / 3.0
+        y = np.arange(c.ny) + 0.5
+        ua = c.gx / (2 * nu) * (y * (c.ny - y))
+        para.append(float(np.linalg.norm(u[0, 0].mean(axis=1) - ua) / np.linalg.norm(ua)))
+    b.close()
+    peak, peak_kind = measured_peaks()
+    line = {"metric": "wall time to steady state vs plain at equal error", "value": t_batch, "unit": "s",
+            "n_gpus": 1, "steps": int(steps.max()), "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_channels_d2q9_smrt_f32_512", "channels": len(chans),
+                       "nx": "U[32,512]", "ny": "U[16,256]", "tau2": "U[0.55,1.5]", "tau3": 1.0, "tau4": 1.0,
+                       "gx": "log-U[1e-7,1e-5]", "redraws": int(sum(c.redraws for c in chans)),
+                       "seed": 2212074941, "tol": args.tol, "K": args.K, "tiles": {"block": block, "tile_nodes": tile}},
+            "batch": {"seconds": t_batch, "node_updates": updates, "mlups": updates / t_batch / 1e6,
+                      "hbm_gbs": updates * 72 / t_batch / 1e9, "hbm_frac": updates * 72 / t_batch / 1e9 / peak,
+                      "converged": int((st == 0).sum()), "not_converged": int((st == 1).sum()),
+                      "unstable": int((st == -4).sum()), "status": int(status),
+                      "steps_min": int(steps.min()), "steps_median": float(np.median(steps)),
+                      "steps_max": int(steps.max())},
+            "plain": {"seconds_measured": t_plain, "channels_measured": len(idx), "seconds_extrapolated": t_plain_est,
+                      "how": f"every {args.plain_stride}th channel run alone (lbm_create, lbm_residual every K), "
+                             f"time x {scale:g}"},
+            "speedup_vs_plain": t_plain_est / t_batch,
+            "equal_error": {"max_rel_l2_batch_vs_plain": max(errs), "plain_vs_batch_steps_diff_max":
+                            int(max(abs(int(steps[i]) - 1 - p) for i, p in zip(idx, plain_steps))),
+                            "rel_l2_vs_noslip_parabola_median": float(np.median(para)),
+                            "rel_l2_vs_noslip_parabola_max": float(max(para))}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -376,6 +462,8 @@ def main():
         print(f"warning: --gpus {args.gpus} but WORLD_SIZE {ws}", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch":
+        run_batch(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
 

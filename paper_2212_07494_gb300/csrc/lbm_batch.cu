@@ -3,11 +3,15 @@
 // steady-state residual.
 //
 // Work unit: a tile = a band of rows of one channel for one time step.  A CTA
-// claims a tile through the channel's packed word (step << 32 | next tile),
-// pulls, collides and stores it, then counts it done; the CTA finishing the
-// last tile of a step closes the step: at check steps it sums the tiles' FP64
-// residual partials in tile order, decides convergence, and publishes the next
-// step (or retires the channel).  Steps of one channel are thus ordered by the
+// claims a tile through the channel's packed claim word (step | tiles of the
+// step | next tile), pulls, collides and stores it, then counts it done; the
+// CTA finishing the last tile of a step closes the step: at check steps it
+// sums the tiles' FP64 residual partials in tile order, decides convergence,
+// and publishes the next step (or retires the channel).  The tile count of
+// the next step follows the work left: active nodes / (2 x resident CTAs),
+// clamped to [2 x CTA size, the tuned maximum] -- large tiles while many
+// channels run, small ones when few channels (the slowest) remain, so a
+// lone channel's step is spread over many CTAs.  Steps of one channel are thus ordered by the
 // done counter; different channels run independently.  No CTA waits for a
 // particular other CTA: a CTA that finds nothing to claim scans again, and the
 // scan is bounded by a no-progress counter that sets an error flag and exits.
@@ -31,16 +35,25 @@ struct BatchChan {
     long long off;       // element offset of the channel's Q planes in each population arena
     long long plane;     // nxp * ny
     long long snap_off;  // offset (elements of the arithmetic type) of its velocity snapshot, 2 * nx * ny
-    long long part_off;  // offset (doubles) of its tile partials, 2 per tile
+    long long part_off;  // offset (doubles) of its tile partials, 2 per tile, room for ny tiles
     int nx, ny, nxp;
     int per_x, per_y;
-    int tiles, rows;     // tiles per step and rows per tile
     double om2, om3, om4;
     double gx, gy;
 };
 
+// claim word: bits [0,13) next tile, [13,26) tiles of this step (<= 4096),
+// [26,64) step.  Claimers only add when the tile field is below the tile
+// count, so it overshoots by at most the number of CTAs (< 4096).
+constexpr int kTileBits = 13;
+constexpr unsigned long long kTileMask = (1ull << kTileBits) - 1;
+constexpr int kMaxTiles = 4096;
+__host__ __device__ inline unsigned long long claim_word(long long step, int tiles) {
+    return ((unsigned long long)step << (2 * kTileBits)) | ((unsigned long long)tiles << kTileBits);
+}
+
 struct BatchCtl {
-    unsigned long long claim;  // (step << 32) | next tile index
+    unsigned long long claim;  // claim_word(step, tiles) + next tile index
     unsigned int done;         // tiles finished in the current step
     int active;
     long long steps;           // steps completed
@@ -53,6 +66,10 @@ struct BatchRun {
     const BatchChan *ch;
     BatchCtl *ctl;
     int n;
+    int grid;                  // resident CTAs
+    int tile_min, tile_max;    // nodes per tile
+    long long *active_nodes;   // nodes of channels still running
+    unsigned *active_bits;     // bit c: channel c still running
     void *fa, *fb;  // the state after s steps lives in fa for even s, fb for odd s
     void *snap;
     double *part;
@@ -125,53 +142,94 @@ __device__ __forceinline__ void block_sum_batch(double (&v)[2]) {
     }
 }
 
+// tiles per step for a channel of nx x ny with `active` nodes still running
+__host__ __device__ inline int tiles_for(int nx, int ny, long long active, int grid, int tile_min, int tile_max) {
+    long long target = active / (2LL * grid);
+    if (target < tile_min) target = tile_min;
+    if (target > tile_max) target = tile_max;
+    int rows = (int)((target + nx - 1) / nx);
+    const int min_rows = (ny + kMaxTiles - 1) / kMaxTiles;
+    if (rows < min_rows) rows = min_rows;
+    if (rows < 1) rows = 1;
+    if (rows > ny) rows = ny;
+    return (ny + rows - 1) / rows;
+}
+
 // batch storage is FP32 or FP64 (loads through L2: ld.global.cg)
 template <int COLL, int ST>
 __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
     typedef typename Store<ST>::T T;
     typedef typename Store<ST>::R R;
-    __shared__ int s_c, s_tile, s_quit;
+    __shared__ int s_c, s_tile, s_tiles, s_quit;
     __shared__ long long s_step;
     long long empty = 0;
     unsigned long long seen = 0;
-    int cursor = blockIdx.x % r.n;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_c = -1;
-            s_quit = 0;
-            int c = cursor;
-            for (int k = 0; k < r.n; ++k, c = (c + 1 == r.n) ? 0 : c + 1) {
-                if (!vload(&r.ctl[c].active)) continue;
-                const int tiles = r.ch[c].tiles;
-                const unsigned long long w = vload(&r.ctl[c].claim);
-                if ((int)(w & 0xffffffffull) >= tiles) continue;
-                const unsigned long long w2 = atomicAdd(&r.ctl[c].claim, 1ull);
-                if ((int)(w2 & 0xffffffffull) < tiles) {
-                    s_c = c;
-                    s_step = (long long)(w2 >> 32);
-                    s_tile = (int)(w2 & 0xffffffffull);
-                    cursor = c;
-                    break;
-                }
-            }
-            if (s_c < 0) {
-                if (vload(r.active_count) == 0 || vload(r.error) != 0) {
-                    s_quit = 1;
-                } else {
-                    const unsigned long long pg = vload(r.progress);
-                    if (pg != seen) {
-                        seen = pg;
-                        empty = 0;
-                    } else if (++empty > r.spin_limit) {
-                        atomicExch(r.error, (int)LBM_ERR_TIMEOUT);
-                        s_quit = 1;
+        // warp 0 looks for a claimable tile: the active-channel bitmap is read
+        // 32 words per load, the claim words of a word's channels in one round,
+        // and the lowest-index (highest-priority) claimable channel is claimed
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int fc = -1, ft = 0, fn = 0;
+            long long fs = 0;
+            const int nwords = (r.n + 31) >> 5;
+            for (int wb = 0; wb < nwords && fc < 0; wb += 32) {
+                const int wi = wb + lane;
+                const unsigned bits = wi < nwords ? vload(r.active_bits + wi) : 0u;
+                unsigned nz = __ballot_sync(0xffffffffu, bits != 0u);
+                while (nz != 0u && fc < 0) {
+                    const int src = __ffs(nz) - 1;
+                    nz &= nz - 1u;
+                    const unsigned wbits = __shfl_sync(0xffffffffu, bits, src);
+                    const int c = (wb + src) * 32 + lane;
+                    bool ok = (wbits >> lane) & 1u;
+                    if (ok) {
+                        const unsigned long long w = vload(&r.ctl[c].claim);
+                        ok = (int)(w & kTileMask) < (int)((w >> kTileBits) & kTileMask);
                     }
-                    __nanosleep(200);
+                    unsigned m = __ballot_sync(0xffffffffu, ok);
+                    while (m != 0u) {
+                        const int pick = __ffs(m) - 1;
+                        m &= m - 1u;
+                        unsigned long long w2 = 0ull;
+                        if (lane == pick) w2 = atomicAdd(&r.ctl[c].claim, 1ull);
+                        w2 = __shfl_sync(0xffffffffu, w2, pick);
+                        const int t2 = (int)(w2 & kTileMask), n2 = (int)((w2 >> kTileBits) & kTileMask);
+                        if (t2 < n2) {
+                            fc = (wb + src) * 32 + pick;
+                            fs = (long long)(w2 >> (2 * kTileBits));
+                            ft = t2;
+                            fn = n2;
+                            break;
+                        }
+                    }
                 }
-            } else {
-                empty = 0;
             }
-            __threadfence();
+            if (lane == 0) {
+                s_c = fc;
+                s_step = fs;
+                s_tile = ft;
+                s_tiles = fn;
+                s_quit = 0;
+                if (fc < 0) {
+                    if (vload(r.active_count) == 0 || vload(r.error) != 0) {
+                        s_quit = 1;
+                    } else {
+                        const unsigned long long pg = vload(r.progress);
+                        if (pg != seen) {
+                            seen = pg;
+                            empty = 0;
+                        } else if (++empty > r.spin_limit) {
+                            atomicExch(r.error, (int)LBM_ERR_TIMEOUT);
+                            s_quit = 1;
+                        }
+                        __nanosleep(100);
+                    }
+                } else {
+                    empty = 0;
+                }
+                __threadfence();
+            }
         }
         __syncthreads();
         if (s_quit) break;
@@ -180,46 +238,61 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
             const BatchChan C = r.ch[c];
             const long long step = s_step;
             const int tile = s_tile;
+            const int ntiles = s_tiles;
+            const int rows = (C.ny + ntiles - 1) / ntiles;
             const T *fin = (const T *)((step & 1) ? r.fb : r.fa) + C.off;
             T *fout = (T *)((step & 1) ? r.fa : r.fb) + C.off;
             const long long start = r.ctl[c].start;
             const bool check = ((step - start) % r.K) == 0;
-            const int y0 = tile * C.rows;
-            const int y1 = min(y0 + C.rows, C.ny);
-            const int nn = (y1 - y0) * C.nx;
+            const int y0 = tile * rows;
+            const int y1 = min(y0 + rows, C.ny);
+            const int nn = y1 > y0 ? (y1 - y0) * C.nx : 0;  // the last tiles may be empty
             R *snap = (R *)r.snap + C.snap_off;
             const int N = C.nx * C.ny;
             const R om2 = R(C.om2), om3 = R(C.om3), om4 = R(C.om4), gx = R(C.gx), gy = R(C.gy);
             double v[2] = {0.0, 0.0};
-            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-                const int yy = (int)((unsigned)idx / (unsigned)C.nx);
-                const int x = idx - yy * C.nx;
-                const int y = y0 + yy;
-                R G[9];
-                gather_chan<ST>(C, fin, x, y, G);
-                if (check) {
-                    R drho = 0, jx = 0, jy = 0;
+            // two nodes per thread per pass, all loads issued first
+            for (int base = threadIdx.x; base < nn; base += 2 * blockDim.x) {
+                R G[2][9];
+                int xs[2], ys[2];
+                bool on[2];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const R w = G[gpos<D2Q9>(i)];
-                        drho += w;
-                        jx += Lat<D2Q9>::cx(i) * w;
-                        jy += Lat<D2Q9>::cy(i) * w;
-                    }
-                    const R rho = R(1) + drho;
-                    const R ux = jx / rho + R(0.5) * gx, uy = jy / rho + R(0.5) * gy;
-                    const int n = y * C.nx + x;
-                    const R dx = ux - ld_cg<R>(snap + n), dy = uy - ld_cg<R>(snap + N + n);
-                    v[0] += (double)(dx * dx + dy * dy);
-                    v[1] += (double)(ux * ux + uy * uy);
-                    snap[n] = ux;
-                    snap[N + n] = uy;
+                for (int k = 0; k < 2; ++k) {
+                    const int idx = base + k * blockDim.x;
+                    on[k] = idx < nn;
+                    const int yy = (int)((unsigned)idx / (unsigned)C.nx);
+                    xs[k] = idx - yy * C.nx;
+                    ys[k] = y0 + yy;
+                    if (on[k]) gather_chan<ST>(C, fin, xs[k], ys[k], G[k]);
                 }
-                if (COLL == SMRT) collide_smrt<D2Q9>(G, gx, gy, R(0), om2, om3, om4);
-                else collide_bgk<D2Q9>(G, gx, gy, R(0), om2);
-                T *dst = fout + (y * C.nxp + x);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[gpos<D2Q9>(i)]);
+                for (int k = 0; k < 2; ++k) {
+                    if (!on[k]) continue;
+                    const int x = xs[k], y = ys[k];
+                    if (check) {
+                        R drho = 0, jx = 0, jy = 0;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const R w = G[k][gpos<D2Q9>(i)];
+                            drho += w;
+                            jx += Lat<D2Q9>::cx(i) * w;
+                            jy += Lat<D2Q9>::cy(i) * w;
+                        }
+                        const R rho = R(1) + drho;
+                        const R ux = jx / rho + R(0.5) * gx, uy = jy / rho + R(0.5) * gy;
+                        const int n = y * C.nx + x;
+                        const R dx = ux - ld_cg<R>(snap + n), dy = uy - ld_cg<R>(snap + N + n);
+                        v[0] += (double)(dx * dx + dy * dy);
+                        v[1] += (double)(ux * ux + uy * uy);
+                        snap[n] = ux;
+                        snap[N + n] = uy;
+                    }
+                    if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4);
+                    else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
+                    T *dst = fout + (y * C.nxp + x);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[k][gpos<D2Q9>(i)]);
+                }
             }
             if (check) {
                 block_sum_batch(v);
@@ -235,7 +308,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
             if (threadIdx.x == 0) {
                 __threadfence();
                 const unsigned prev = atomicAdd(&r.ctl[c].done, 1u);
-                if (prev == (unsigned)(C.tiles - 1)) {
+                if (prev == (unsigned)(ntiles - 1)) {
                     // last tile of this step: close it
                     __threadfence();
                     const long long done_steps = step + 1;
@@ -243,7 +316,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                     int status = 0;
                     if (check && step > start) {
                         double num = 0.0, den = 0.0;
-                        for (int t = 0; t < C.tiles; ++t) {
+                        for (int t = 0; t < ntiles; ++t) {
                             num += ld_cg<double>(r.part + C.part_off + 2 * t);
                             den += ld_cg<double>(r.part + C.part_off + 2 * t + 1);
                         }
@@ -267,10 +340,13 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                         r.ctl[c].status = status;
                         __threadfence();
                         atomicExch(&r.ctl[c].active, 0);
+                        atomicAnd(r.active_bits + (c >> 5), ~(1u << (c & 31)));
+                        atomicAdd((unsigned long long *)r.active_nodes, (unsigned long long)(-(long long)C.nx * C.ny));
                         atomicSub(r.active_count, 1);
                     } else {
+                        const int nt = tiles_for(C.nx, C.ny, vload(r.active_nodes), r.grid, r.tile_min, r.tile_max);
                         __threadfence();
-                        atomicExch(&r.ctl[c].claim, (unsigned long long)done_steps << 32);
+                        atomicExch(&r.ctl[c].claim, claim_word(done_steps, nt));
                     }
                     atomicAdd(r.progress, 1ull);
                 }
@@ -281,21 +357,24 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
 }
 
 // start of a run: every channel active from its current step
-__global__ void k_batch_reset(BatchCtl *ctl, int n, int *active_count, unsigned long long *progress, int *error) {
+__global__ void k_batch_reset(BatchRun r, long long total_nodes) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) {
+    if (c < r.n) {
+        BatchCtl *ctl = r.ctl;
         const long long s = ctl[c].steps;
-        ctl[c].claim = (unsigned long long)s << 32;
+        ctl[c].claim = claim_word(s, tiles_for(r.ch[c].nx, r.ch[c].ny, total_nodes, r.grid, r.tile_min, r.tile_max));
         ctl[c].done = 0u;
         ctl[c].active = 1;
         ctl[c].start = s;
         ctl[c].status = 1;
         ctl[c].r = -1.0;
+        atomicOr(r.active_bits + (c >> 5), 1u << (c & 31));
     }
     if (c == 0) {
-        *active_count = n;
-        *progress = 0ull;
-        *error = 0;
+        *r.active_count = r.n;
+        *r.active_nodes = total_nodes;
+        *r.progress = 0ull;
+        *r.error = 0;
     }
 }
 
@@ -319,11 +398,17 @@ struct lbm_batch {
     BatchCtl *ctl_dev = nullptr;
     int *active_count = nullptr, *error = nullptr;
     unsigned long long *progress = nullptr;
+    long long *active_nodes = nullptr;
+    unsigned *active_bits = nullptr;
+    long long total_nodes = 0;
+    std::vector<int> order;     // position -> channel index given by the caller
+    std::vector<int> pos_of;    // channel index -> position (priority order)
+    int last_grid = 0;
     double *partials = nullptr, *red = nullptr, *tmp = nullptr;
     size_t tmp_bytes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int block = 256, tile_nodes = 2048;
+    int block = 128, tile_nodes = 2048;
     long long spin_limit = 1ll << 26;
     size_t arena_elems = 0;
     std::string err;
@@ -361,12 +446,12 @@ lbm_status balloc(lbm_batch *b, T **p, size_t bytes) {
 
 lbm_status build_tiles(lbm_batch *b) {
     long long part_off = 0;
+    b->total_nodes = 0;
     for (int c = 0; c < b->n; ++c) {
         BatchChan &C = b->ch[c];
-        C.rows = std::max(1, std::min(C.ny, (b->tile_nodes + C.nx - 1) / C.nx));
-        C.tiles = (C.ny + C.rows - 1) / C.rows;
         C.part_off = part_off;
         part_off += 2LL * C.ny;  // room for the finest tiling (one row per tile)
+        b->total_nodes += (long long)C.nx * C.ny;
     }
     B_CUDA(b, cudaMemcpyAsync(b->ch_dev, b->ch.data(), sizeof(BatchChan) * b->n, cudaMemcpyHostToDevice, b->stream));
     B_CUDA(b, cudaStreamSynchronize(b->stream));
@@ -392,6 +477,14 @@ lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
     r.ch = b->ch_dev;
     r.ctl = b->ctl_dev;
     r.n = b->n;
+    // at most 4000 CTAs: the tile field of the claim word overshoots the tile
+    // count (<= 4096) by at most the number of concurrent claimers (< 8192 - 4096)
+    r.grid = std::min(sms * per_sm, 4000);
+    r.tile_min = 2 * b->block;
+    r.tile_max = std::max(b->tile_nodes, 2 * b->block);
+    r.active_nodes = b->active_nodes;
+    r.active_bits = b->active_bits;
+    b->last_grid = r.grid;
     r.fa = b->fa;
     r.fb = b->fb;
     r.snap = b->snap;
@@ -403,12 +496,12 @@ lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
     r.K = K;
     r.max_steps = max_steps;
     r.spin_limit = b->spin_limit;
-    const int grid = sms * per_sm;
+    const int grid = r.grid;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     B_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    k_batch_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->ctl_dev, b->n, b->active_count, b->progress,
-                                                            b->error);
+    cudaMemsetAsync(b->active_bits, 0, (size_t)((b->n + 31) / 32) * 4, b->stream);
+    k_batch_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>(r, b->total_nodes);
     kern<<<grid, b->block, 0, b->stream>>>(r);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
@@ -474,8 +567,9 @@ extern "C" {
 void lbm_batch_destroy(lbm_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    void *ptrs[] = {b->fa, b->fb, b->snap, b->part, b->g_dev, b->g32_dev, b->fields, b->ch_dev, b->ctl_dev,
-                    b->active_count, b->error, b->progress, b->partials, b->red, b->tmp};
+    void *ptrs[] = {b->fa,      b->fb,       b->snap,         b->part,  b->g_dev,    b->g32_dev,
+                    b->fields,  b->ch_dev,   b->ctl_dev,      b->active_count, b->error, b->progress,
+                    b->active_nodes, b->active_bits, b->partials, b->red, b->tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -508,7 +602,28 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
     b->n = n;
     b->collision = d0.collision;
     b->storage = d0.storage;
-    b->desc.assign(descs, descs + n);
+    // priority order: longest diffusive time scale L^2 / nu first (L: the
+    // extent between walls, else the largest extent), so that the channels
+    // needing the most steps are always served first
+    b->order.resize(n);
+    b->pos_of.resize(n);
+    {
+        std::vector<std::pair<double, int>> key(n);
+        for (int c = 0; c < n; ++c) {
+            const lbm_desc &d = descs[c];
+            const double L = !d.periodic[1] ? d.ny : (!d.periodic[0] ? d.nx : std::max(d.nx, d.ny));
+            const double nu = (d.tau[2] - 0.5) / 3.0;
+            key[c] = {-(L * L / nu), c};
+        }
+        std::stable_sort(key.begin(), key.end());
+        for (int p = 0; p < n; ++p) {
+            b->order[p] = key[p].second;
+            b->pos_of[key[p].second] = p;
+        }
+    }
+    b->desc.resize(n);
+    for (int p = 0; p < n; ++p) b->desc[p] = descs[b->order[p]];
+    descs = b->desc.data();
     b->ch.resize(n);
     b->kp.resize(n);
     b->steps.assign(n, 0);
@@ -553,7 +668,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         (st = balloc(b, &b->g_dev, (size_t)n * 4 * 8)) || (st = balloc(b, &b->g32_dev, (size_t)n * 4 * 4)) ||
         (st = balloc(b, &b->ch_dev, sizeof(BatchChan) * n)) || (st = balloc(b, &b->ctl_dev, sizeof(BatchCtl) * n)) ||
         (st = balloc(b, &b->active_count, 16)) || (st = balloc(b, &b->error, 16)) ||
-        (st = balloc(b, &b->progress, 16)) ||
+        (st = balloc(b, &b->progress, 16)) || (st = balloc(b, &b->active_nodes, 16)) ||
+        (st = balloc(b, &b->active_bits, (size_t)((n + 31) / 32) * 4)) ||
         (st = balloc(b, &b->partials, (size_t)kMomGridMax * kPartials * 8)) || (st = balloc(b, &b->red, 64)) ||
         (fields && (st = balloc(b, &b->fields, (size_t)fields * 8)))) {
         std::string m = b->err;
@@ -654,18 +770,21 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_
     if (st != LBM_OK && st != LBM_ERR_TIMEOUT) return st;
     std::vector<BatchCtl> ctl(b->n);
     B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
-    for (int c = 0; c < b->n; ++c) {
-        if (steps_out) steps_out[c] = ctl[c].steps;
-        if (st_out) st_out[c] = ctl[c].status;
-        if (r_out) r_out[c] = ctl[c].r;
+    for (int p = 0; p < b->n; ++p) {
+        const int c = b->order[p];
+        if (steps_out) steps_out[c] = ctl[p].steps;
+        if (st_out) st_out[c] = ctl[p].status;
+        if (r_out) r_out[c] = ctl[p].r;
     }
     return st;
 }
 
 lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nodes, double *ms) {
     if (!b || steps < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
-    static const int blocks[] = {128, 256};
-    static const int tiles[] = {512, 1024, 2048, 4096, 8192};
+    // the largest tile (used while many channels run); tiles shrink on their
+    // own as channels retire
+    static const int blocks[] = {64, 128, 256};
+    static const int tiles[] = {1024, 2048, 4096, 8192};
     cudaEvent_t e0, e1;
     B_CUDA(b, cudaEventCreate(&e0));
     B_CUDA(b, cudaEventCreate(&e1));
@@ -702,6 +821,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nod
 
 lbm_status lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u) {
     if (!b || i < 0 || i >= b->n) return bfail(b, LBM_ERR_ARG, "bad channel index");
+    i = b->pos_of[i];
     const lbm_desc &d = b->desc[i];
     const size_t N = (size_t)d.nx * d.ny;
     lbm_status st = ensure_tmp(b, 3 * N * 8);
@@ -718,6 +838,7 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u) {
 
 lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f) {
     if (!b || i < 0 || i >= b->n || !f) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    i = b->pos_of[i];
     const lbm_desc &d = b->desc[i];
     const size_t N = (size_t)d.nx * d.ny;
     lbm_status st = ensure_tmp(b, 9 * N * 8);
@@ -731,9 +852,14 @@ lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f) {
 
 lbm_status lbm_batch_info(const lbm_batch *b, int i, int64_t *steps, int *tiles, int *rows) {
     if (!b || i < 0 || i >= b->n) return bfail(nullptr, LBM_ERR_ARG, "bad channel index");
+    i = b->pos_of[i];
     if (steps) *steps = b->steps[i];
-    if (tiles) *tiles = b->ch[i].tiles;
-    if (rows) *rows = b->ch[i].rows;
+    // tiling a run starts with (all channels active)
+    const int grid = b->last_grid > 0 ? b->last_grid : 1;
+    const int t = tiles_for(b->ch[i].nx, b->ch[i].ny, b->total_nodes, grid, 2 * b->block,
+                            std::max(b->tile_nodes, 2 * b->block));
+    if (tiles) *tiles = t;
+    if (rows) *rows = (b->ch[i].ny + t - 1) / t;
     return LBM_OK;
 }
 
