@@ -184,8 +184,8 @@ const char *lbm_last_error(const lbm_handle *h);
  * all tiles of its current step are done.  Every K steps a channel computes
  * its residual r_K (as lbm_residual) and retires once r_K <= tol.
  * Channels share lattice (D2Q9), collision and storage (LBM_F32 or LBM_F64);
- * each takes its own nx, ny, periodic flags, tau and uniform (or no) force;
- * no solid masks.  The descriptions' rho0/u0 are copied.  The stream of
+ * each takes its own nx, ny, periodic flags, tau, uniform (or no) force and
+ * optional solid mask (halfway bounce-back at solid nodes).  The descriptions' rho0/u0 are copied.  The stream of
  * descs[0] is used (NULL => the library makes one). */
 typedef struct lbm_batch lbm_batch;
 

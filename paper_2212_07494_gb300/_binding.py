@@ -458,14 +458,15 @@ def lbm_batch_destroy(b):
 
 class Batch:
     """Independent D2Q9 channels in one persistent launch.  ``channels`` is a
-    list of dicts with keys shape, tau, periodic, g (uniform), rho0, u0."""
+    list of dicts with keys shape, tau, periodic, g (uniform), solid, rho0, u0."""
 
     def __init__(self, channels, collision="SMRT", storage="F32", stream=None):
         self._keep = []
         descs = []
         for ch in channels:
             d, keep = make_desc("D2Q9", collision, ch["shape"], ch["tau"], storage, ch.get("periodic", (1, 0, 1)),
-                                g=ch.get("g"), rho0=ch.get("rho0"), u0=ch.get("u0"), stream=stream)
+                                g=ch.get("g"), solid=ch.get("solid"), rho0=ch.get("rho0"), u0=ch.get("u0"),
+                                stream=stream)
             descs.append(d)
             self._keep.append(keep)
         self.shapes = [tuple((list(ch["shape"]) + [1, 1])[:3]) for ch in channels]

@@ -36,6 +36,7 @@ struct BatchChan {
     long long plane;     // nxp * ny
     long long snap_off;  // offset (elements of the arithmetic type) of its velocity snapshot, 2 * nx * ny
     long long part_off;  // offset (doubles) of its tile partials, 2 per tile, room for ny tiles
+    long long solid_off; // offset of its obstacle mask (nxp * ny bytes) in the mask arena, -1: none
     int nx, ny, nxp;
     int per_x, per_y;
     double om2, om3, om4;
@@ -66,6 +67,7 @@ struct BatchRun {
     const BatchChan *ch;
     BatchCtl *ctl;
     int n;
+    const unsigned char *solid;  // mask arena
     int grid;                  // resident CTAs
     int tile_min, tile_max;    // nodes per tile
     long long *active_nodes;   // nodes of channels still running
@@ -89,10 +91,12 @@ template <> __device__ __forceinline__ float ld_cg<float>(const float *p) { retu
 template <typename T>
 __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
 
-// pull of one D2Q9 node of a channel (walls or periodic per axis); f is the
-// channel's base, all offsets within a channel fit in 32 bits
+// pull of one D2Q9 node of a channel (walls or periodic per axis, halfway
+// bounce-back at solid nodes when the channel has a mask); f is the channel's
+// base, all offsets within a channel fit in 32 bits
 template <int ST>
-__device__ __forceinline__ void gather_chan(const BatchChan &C, const typename Store<ST>::T *f, int x, int y,
+__device__ __forceinline__ void gather_chan(const BatchChan &C, const typename Store<ST>::T *f,
+                                            const unsigned char *solid, int x, int y,
                                             typename Store<ST>::R *G) {
     typedef typename Store<ST>::R R;
     typedef typename Store<ST>::T T;
@@ -102,18 +106,20 @@ __device__ __forceinline__ void gather_chan(const BatchChan &C, const typename S
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = Lat<D2Q9>::cx(i), cy = Lat<D2Q9>::cy(i);
-        int idx;
+        int src;
+        bool wall = false;
         if (interior) {
-            idx = i * plane + own - (cx + cy * C.nxp);
+            src = own - (cx + cy * C.nxp);
         } else {
             int sx = x - cx, sy = y - cy;
-            bool wall = false;
             if (sx < 0) { if (C.per_x) sx += C.nx; else wall = true; }
             else if (sx >= C.nx) { if (C.per_x) sx -= C.nx; else wall = true; }
             if (sy < 0) { if (C.per_y) sy += C.ny; else wall = true; }
             else if (sy >= C.ny) { if (C.per_y) sy -= C.ny; else wall = true; }
-            idx = wall ? opp<D2Q9>(i) * plane + own : i * plane + sy * C.nxp + sx;
+            src = sy * C.nxp + sx;
         }
+        if (solid && i != 0 && !wall) wall = solid[src] != 0;
+        const int idx = wall ? opp<D2Q9>(i) * plane + own : i * plane + src;
         G[gpos<D2Q9>(i)] = (R)ld_cg<T>(f + idx);
     }
 }
@@ -248,6 +254,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
             const int y1 = min(y0 + rows, C.ny);
             const int nn = y1 > y0 ? (y1 - y0) * C.nx : 0;  // the last tiles may be empty
             R *snap = (R *)r.snap + C.snap_off;
+            const unsigned char *solid = C.solid_off >= 0 ? r.solid + C.solid_off : nullptr;
             const int N = C.nx * C.ny;
             const R om2 = R(C.om2), om3 = R(C.om3), om4 = R(C.om4), gx = R(C.gx), gy = R(C.gy);
             double v[2] = {0.0, 0.0};
@@ -263,7 +270,8 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                     const int yy = (int)((unsigned)idx / (unsigned)C.nx);
                     xs[k] = idx - yy * C.nx;
                     ys[k] = y0 + yy;
-                    if (on[k]) gather_chan<ST>(C, fin, xs[k], ys[k], G[k]);
+                    if (on[k] && solid) on[k] = solid[ys[k] * C.nxp + xs[k]] == 0;
+                    if (on[k]) gather_chan<ST>(C, fin, solid, xs[k], ys[k], G[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -393,6 +401,7 @@ struct lbm_batch {
     double *g_dev = nullptr;    // per channel 4 doubles
     float *g32_dev = nullptr;   // per channel 4 floats
     double *fields = nullptr;   // initial rho0 / u0, per channel, when given
+    unsigned char *solid = nullptr;  // obstacle masks of the channels that have one
     std::vector<long long> field_off;
     BatchChan *ch_dev = nullptr;
     BatchCtl *ctl_dev = nullptr;
@@ -477,6 +486,7 @@ lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
     r.ch = b->ch_dev;
     r.ctl = b->ctl_dev;
     r.n = b->n;
+    r.solid = b->solid;
     // at most 4000 CTAs: the tile field of the claim word overshoots the tile
     // count (<= 4096) by at most the number of concurrent claimers (< 8192 - 4096)
     r.grid = std::min(sms * per_sm, 4000);
@@ -531,8 +541,9 @@ lbm_status init_channels(lbm_batch *b) {
         const size_t eb = elem_bytes(b->storage);
         void *A = (char *)b->fa + b->ch[c].off * eb;
         void *B = (char *)b->fb + b->ch[c].off * eb;
-        cudaError_t e = L.init(b->collision, b->storage, false, b->kp[c], rho0, u0, B, b->stream);
-        if (e == cudaSuccess) e = L.unstream(b->storage, false, b->kp[c], B, A, b->stream);
+        const bool mask = b->kp[c].solid != nullptr;
+        cudaError_t e = L.init(b->collision, b->storage, mask, b->kp[c], rho0, u0, B, b->stream);
+        if (e == cudaSuccess) e = L.unstream(b->storage, mask, b->kp[c], B, A, b->stream);
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch init: ") + cudaGetErrorString(e));
         b->steps[c] = 0;
         ctl[c] = BatchCtl{};
@@ -569,7 +580,7 @@ void lbm_batch_destroy(lbm_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     void *ptrs[] = {b->fa,      b->fb,       b->snap,         b->part,  b->g_dev,    b->g32_dev,
                     b->fields,  b->ch_dev,   b->ctl_dev,      b->active_count, b->error, b->progress,
-                    b->active_nodes, b->active_bits, b->partials, b->red, b->tmp};
+                    b->active_nodes, b->active_bits, b->partials, b->red, b->tmp, b->solid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -589,7 +600,6 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         if (d.lattice != d0.lattice || d.collision != d0.collision || d.storage != d0.storage)
             return bfail(nullptr, LBM_ERR_ARG, "channels must share lattice, collision and storage");
         if (d.nx < 1 || d.ny < 1 || d.nz != 1 || d.ny > 65535) return bfail(nullptr, LBM_ERR_ARG, "bad channel sizes");
-        if (d.solid) return bfail(nullptr, LBM_ERR_ARG, "batch channels take no solid mask");
         if (d.force_kind != LBM_G_NONE && d.force_kind != LBM_G_UNIFORM)
             return bfail(nullptr, LBM_ERR_ARG, "batch channels take a uniform force or none");
         if (d.force_kind == LBM_G_UNIFORM && !d.g) return bfail(nullptr, LBM_ERR_ARG, "force values are NULL");
@@ -638,7 +648,7 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         }
         b->own_stream = true;
     }
-    long long off = 0, snap_off = 0, parts = 0, fields = 0;
+    long long off = 0, snap_off = 0, parts = 0, fields = 0, solid_bytes = 0;
     for (int c = 0; c < n; ++c) {
         const lbm_desc &d = descs[c];
         BatchChan &C = b->ch[c];
@@ -660,6 +670,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         C.gy = d.force_kind == LBM_G_UNIFORM ? d.g[1] : 0.0;
         b->field_off[c] = fields;
         if (d.rho0 || d.u0) fields += 3LL * d.nx * d.ny;
+        C.solid_off = d.solid ? solid_bytes : -1;
+        if (d.solid) solid_bytes += C.plane;
     }
     b->arena_elems = (size_t)off;
     const size_t eb = elem_bytes(b->storage);
@@ -671,7 +683,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         (st = balloc(b, &b->progress, 16)) || (st = balloc(b, &b->active_nodes, 16)) ||
         (st = balloc(b, &b->active_bits, (size_t)((n + 31) / 32) * 4)) ||
         (st = balloc(b, &b->partials, (size_t)kMomGridMax * kPartials * 8)) || (st = balloc(b, &b->red, 64)) ||
-        (fields && (st = balloc(b, &b->fields, (size_t)fields * 8)))) {
+        (fields && (st = balloc(b, &b->fields, (size_t)fields * 8))) ||
+        (solid_bytes && (st = balloc(b, &b->solid, (size_t)solid_bytes)))) {
         std::string m = b->err;
         lbm_batch_destroy(b);
         return bfail(nullptr, st, m);
@@ -696,6 +709,7 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         k.per[1] = b->ch[c].per_y;
         k.per[2] = 1;
         k.force_kind = d.force_kind == LBM_G_UNIFORM ? G_UNIFORM : G_NONE;
+        k.solid = d.solid ? b->solid + b->ch[c].solid_off : nullptr;
         k.g = b->g_dev + 4 * c;
         k.g32 = b->g32_dev + 4 * c;
         for (int m = 0; m < 5; ++m) {
@@ -705,6 +719,15 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         fill_offsets<D2Q9>(k);
     }
     cudaError_t e = cudaMemcpyAsync(b->g_dev, g.data(), g.size() * 8, cudaMemcpyHostToDevice, b->stream);
+    for (int c = 0; c < n && e == cudaSuccess; ++c) {
+        const lbm_desc &d = descs[c];
+        if (!d.solid) continue;
+        std::vector<unsigned char> m((size_t)b->ch[c].plane, 0);
+        for (int y = 0; y < d.ny; ++y)
+            for (int x = 0; x < d.nx; ++x) m[(size_t)y * b->ch[c].nxp + x] = d.solid[(size_t)y * d.nx + x] ? 1 : 0;
+        e = cudaMemcpyAsync(b->solid + b->ch[c].solid_off, m.data(), m.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->g32_dev, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->fa, 0, (size_t)off * eb, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->fb, 0, (size_t)off * eb, b->stream);
@@ -827,8 +850,8 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u) {
     lbm_status st = ensure_tmp(b, 3 * N * 8);
     if (st != LBM_OK) return st;
     int nb = 0;
-    cudaError_t e = launchers_d2q9().moments(b->storage, false, b->kp[i], channel_state(b, i), b->tmp, b->tmp + N,
-                                             b->partials, nullptr, b->stream, &nb);
+    cudaError_t e = launchers_d2q9().moments(b->storage, b->kp[i].solid != nullptr, b->kp[i], channel_state(b, i),
+                                             b->tmp, b->tmp + N, b->partials, nullptr, b->stream, &nb);
     if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, b->tmp, N * 8, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, b->tmp + N, 2 * N * 8, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -843,7 +866,8 @@ lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f) {
     const size_t N = (size_t)d.nx * d.ny;
     lbm_status st = ensure_tmp(b, 9 * N * 8);
     if (st != LBM_OK) return st;
-    cudaError_t e = launchers_d2q9().get_pops(b->storage, false, b->kp[i], channel_state(b, i), b->tmp, b->stream);
+    cudaError_t e = launchers_d2q9().get_pops(b->storage, b->kp[i].solid != nullptr, b->kp[i], channel_state(b, i),
+                                              b->tmp, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, b->tmp, 9 * N * 8, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch export: ") + cudaGetErrorString(e));

@@ -14,7 +14,8 @@ namespace lbm {
 //  non-finite count, fluid-node count}
 constexpr int kPartials = 8;
 constexpr int kMomBlock = 256;
-constexpr int kMomGridMax = 1216;   // 8 blocks per SM on 152 SMs
+constexpr int kMomNpt = 4;          // nodes per thread per work item
+constexpr int kMomGridMax = 608;    // 4 blocks per SM on 152 SMs: one wave
 
 struct StepCfg {
     int bdx;  // threads per block along x
@@ -47,9 +48,11 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
 // record a message for lbm_last_error(NULL) (thread-local)
 void set_thread_error(const char *msg);
 
-inline int moments_grid(const KParams &p) {
-    const long long items = (long long)((p.nx + kMomBlock - 1) / kMomBlock) * p.ny * p.nz;
-    return (int)(items < kMomGridMax ? items : kMomGridMax);
+inline int moments_grid(const KParams &p, int resident) {
+    const long long items = (long long)((p.nx + kMomBlock * kMomNpt - 1) / (kMomBlock * kMomNpt)) * p.ny * p.nz;
+    long long g = items < kMomGridMax ? items : kMomGridMax;
+    if (resident > 0 && g > resident) g = resident;
+    return (int)g;
 }
 
 // totals out[0..6] = {M, Px, Py, Pz, residual num, residual den, non-finite}

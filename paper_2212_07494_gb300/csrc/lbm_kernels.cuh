@@ -68,27 +68,34 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 }
 
 // Macroscopic fields of the current state (Eq. half_F) and the FP64 check.
-// A fixed grid walks the rows (grid-stride, so the partial sums and their
-// order do not depend on the domain); per-node arithmetic runs in the
-// storage's arithmetic type and only the accumulation is FP64.  Partials per
-// block: {sum (rho - 1), sum rho u_x, sum rho u_y, sum rho u_z,
-//         sum |u - uprev|^2, sum |u|^2, non-finite count, fluid count}.
+// A fixed grid walks the work items (row segments of kMomBlock * kMomNpt
+// nodes; grid-stride, so the partial sums and their order do not depend on
+// how the hardware schedules blocks); each thread takes kMomNpt nodes of a
+// segment and issues all their loads before any arithmetic.  Per-node
+// arithmetic runs in the storage's arithmetic type, which also sums the
+// kMomNpt nodes of a work item; the accumulation over the domain is FP64 and
+// the node counts are integers.  Partials per block: {sum (rho - 1), sum rho u_x, sum rho u_y,
+// sum rho u_z, sum |u - uprev|^2, sum |u|^2, non-finite count, fluid count}.
 // rho/u outputs (unpadded FP64) and uprev (unpadded, arithmetic type; read
 // for the residual, then overwritten with u) are optional.
 template <int L, int ST, bool MASK>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const typename Store<ST>::T *__restrict__ f,
-                                                       double *rho_out, double *u_out, double *partials,
-                                                       typename Store<ST>::R *uprev) {
+                                                       double *__restrict__ rho_out, double *__restrict__ u_out,
+                                                       double *__restrict__ partials,
+                                                       typename Store<ST>::R *__restrict__ uprev) {
     typedef typename Store<ST>::R R;
     constexpr int D = Lat<L>::D;
+    constexpr int NG = Grid<D>::N;
+    constexpr int SEG = kMomBlock * kMomNpt;
     // work items (row segment, row) walked with 32-bit counters: a row is
     // (y, z), at most 65535^2 of them, and segments per row are few
-    const int segs = (p.nx + kMomBlock - 1) / kMomBlock;
+    const int segs = (p.nx + SEG - 1) / SEG;
     const unsigned rows = (unsigned)p.ny * (unsigned)p.nz;
     const long long N = (long long)p.nx * p.ny * p.nz;
     double v[kPartials];
 #pragma unroll
     for (int k = 0; k < kPartials; ++k) v[k] = 0.0;
+    long long fluid = 0, nonfinite = 0;
     unsigned row = blockIdx.x / segs;
     int seg = blockIdx.x % segs;
     const unsigned drow = gridDim.x / segs;
@@ -100,55 +107,85 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
             if (row >= rows) break;
         }
         const int y = (int)(row % (unsigned)p.ny), z = (int)(row / (unsigned)p.ny);
-        const int x = seg * kMomBlock + threadIdx.x;
-        if (x >= p.nx) continue;
-        const long long own = node_index(p, x, y, z);
-        const long long n = ((long long)z * p.ny + y) * p.nx + x;
-        const bool fluid = !MASK || p.solid[own] == 0;
-        R drho = R(0), u[3] = {R(0), R(0), R(0)};
-        if (fluid) {
-            R G[Grid<D>::N];
-            gather<L, ST, MASK>(p, f, x, y, z, G);
-            R j[3] = {R(0), R(0), R(0)};
+        R G[kMomNpt][NG];
+        bool on[kMomNpt], fl[kMomNpt];
+        R up[kMomNpt][3];
 #pragma unroll
-            for (int i = 0; i < Lat<L>::Q; ++i) {
-                const R w = G[gpos<L>(i)];
-                drho += w;
-                if (Lat<L>::cx(i)) j[0] += Lat<L>::cx(i) > 0 ? w : -w;
-                if (Lat<L>::cy(i)) j[1] += Lat<L>::cy(i) > 0 ? w : -w;
-                if (D == 3 && Lat<L>::cz(i)) j[2] += Lat<L>::cz(i) > 0 ? w : -w;
-            }
-            const R rho = R(1) + drho;
-            R g3[3];
-            load_force<L>(p, y, own, g3[0], g3[1], g3[2]);
-            bool finite = isfinite(rho);
+        for (int k = 0; k < kMomNpt; ++k) {
+            const int x = seg * SEG + k * kMomBlock + threadIdx.x;
+            on[k] = x < p.nx;
+            fl[k] = on[k] && (!MASK || p.solid[node_index(p, x, y, z)] == 0);
+            if (fl[k]) gather<L, ST, MASK>(p, f, x, y, z, G[k]);
+        }
+        // the snapshot is read for all nodes of the work item before any of
+        // it is overwritten, so these loads overlap the gathers
+        if (uprev) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                u[a] = j[a] / rho + R(0.5) * g3[a];
-                finite = finite && isfinite(u[a]);
-                v[1 + a] += (double)(j[a] + R(0.5) * rho * g3[a]);   // rho u
-            }
-            v[0] += (double)drho;
-            v[6] += finite ? 0.0 : 1.0;
-            v[7] += 1.0;
-            if (uprev) {
-                R dd = R(0), uu = R(0);
+            for (int k = 0; k < kMomNpt; ++k) {
+                const long long n = ((long long)z * p.ny + y) * p.nx + seg * SEG + k * kMomBlock + threadIdx.x;
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const R d = u[a] - uprev[a * N + n];
-                    dd += d * d;
-                    uu += u[a] * u[a];
-                    uprev[a * N + n] = u[a];
-                }
-                v[4] += (double)dd;
-                v[5] += (double)uu;
+                for (int a = 0; a < D; ++a) up[k][a] = fl[k] ? uprev[a * N + n] : R(0);
             }
         }
-        if (rho_out) rho_out[n] = fluid ? 1.0 + (double)drho : 1.0;
-        if (u_out)
+        R g3[3];
+        const bool per_node_force = p.force_kind == G_FIELD;
+        if (!per_node_force) load_force<L>(p, y, 0, g3[0], g3[1], g3[2]);
+        // the kMomNpt nodes of this work item are summed in the arithmetic
+        // type (each node's value is of that type), then added to the FP64
+        // accumulators once per work item
+        R sdrho = R(0), sj[3] = {R(0), R(0), R(0)}, sdd = R(0), suu = R(0);
 #pragma unroll
-            for (int a = 0; a < D; ++a) u_out[a * N + n] = (double)u[a];
+        for (int k = 0; k < kMomNpt; ++k) {
+            if (!on[k]) continue;
+            const int x = seg * SEG + k * kMomBlock + threadIdx.x;
+            const long long own = node_index(p, x, y, z);
+            const long long n = ((long long)z * p.ny + y) * p.nx + x;
+            R drho = R(0), u[3] = {R(0), R(0), R(0)};
+            if (fl[k]) {
+                R j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                for (int i = 0; i < Lat<L>::Q; ++i) {
+                    const R w = G[k][gpos<L>(i)];
+                    drho += w;
+                    if (Lat<L>::cx(i)) j[0] += Lat<L>::cx(i) > 0 ? w : -w;
+                    if (Lat<L>::cy(i)) j[1] += Lat<L>::cy(i) > 0 ? w : -w;
+                    if (D == 3 && Lat<L>::cz(i)) j[2] += Lat<L>::cz(i) > 0 ? w : -w;
+                }
+                const R rho = R(1) + drho;
+                if (per_node_force) load_force<L>(p, y, own, g3[0], g3[1], g3[2]);
+                bool finite = isfinite(rho);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    u[a] = j[a] / rho + R(0.5) * g3[a];
+                    finite = finite && isfinite(u[a]);
+                    sj[a] += j[a] + R(0.5) * rho * g3[a];   // rho u
+                }
+                sdrho += drho;
+                nonfinite += finite ? 0 : 1;
+                ++fluid;
+                if (uprev) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const R d = u[a] - up[k][a];
+                        sdd += d * d;
+                        suu += u[a] * u[a];
+                        uprev[a * N + n] = u[a];
+                    }
+                }
+            }
+            if (rho_out) rho_out[n] = fl[k] ? 1.0 + (double)drho : 1.0;
+            if (u_out)
+#pragma unroll
+                for (int a = 0; a < D; ++a) u_out[a * N + n] = (double)u[a];
+        }
+        v[0] += (double)sdrho;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[1 + a] += (double)sj[a];
+        v[4] += (double)sdd;
+        v[5] += (double)suu;
     }
+    v[6] = (double)nonfinite;
+    v[7] = (double)fluid;
     block_sum(v);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -284,7 +321,19 @@ template <int L> struct Dispatch {
                                  void *uprev, cudaStream_t s, int *nb) {
         typedef typename Store<ST>::T T;
         typedef typename Store<ST>::R R;
-        *nb = moments_grid(p);
+        // one wave of resident blocks (fixed for a device and build, so the
+        // partial sums keep a fixed order), at most kMomGridMax
+        static int resident = 0;
+        if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_moments<L, ST, MASK>, kMomBlock, 0);
+            if (e != cudaSuccess) return e;
+            resident = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        *nb = moments_grid(p, resident);
         k_moments<L, ST, MASK><<<*nb, kMomBlock, 0, s>>>(p, (const T *)f, rho, u, partials, (R *)uprev);
         return cudaGetLastError();
     }

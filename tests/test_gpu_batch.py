@@ -46,6 +46,35 @@ def test_batch_matches_single_lattices(coll, storage):
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["F32", "F64"])
+def test_batch_channels_with_obstacles(storage):
+    """Seeded obstacle channels (as the surrogate's data) match single masked
+    lattices, and in FP64 the oracle."""
+    import paper_2212_07494_gb300 as P
+    chans = []
+    for k in range(5):
+        solid, t2, g = W.obstacle_channel(100 + k, nx=96, ny=48, radius=(3, 8))
+        chans.append({"shape": (96, 48, 1), "tau": (1, 1, t2, 1, 1), "periodic": (1, 0, 1), "g": [g, 0.0],
+                      "solid": solid})
+    chans.append(_channels(1, 1)[0])  # and one without a mask
+    b = P.Batch(chans, "SMRT", storage)
+    b.set_tiles(128, 512)
+    b.step(60)
+    for i, ch in enumerate(chans):
+        s = P.Lattice("D2Q9", "SMRT", ch["shape"], ch["tau"], storage, ch["periodic"], g=ch["g"],
+                      solid=ch.get("solid"))
+        s.step(60)
+        fb, fs = b.populations(i), s.populations()
+        tol = 1e-15 if storage == "F64" else 2e-7
+        assert np.abs(fb - fs).max() <= tol, (i, np.abs(fb - fs).max())
+        if storage == "F64" and ch.get("solid") is not None:
+            orc = O.Sim(O.D2Q9, O.SMRT, ch["shape"], ch["periodic"], ch["tau"], g=ch["g"], solid=ch["solid"])
+            orc.step(60)
+            assert rel_l2(b.moments(i)[1], orc.moments()[1]) < 1e-12
+        s.close()
+    b.close()
+
+
 def test_batch_channel_matches_oracle_f64():
     import paper_2212_07494_gb300 as P
     chans = _channels(6, 11)
