@@ -1,0 +1,192 @@
+"""FP64 CPU reference of the surrogate network (TEST INFRASTRUCTURE ONLY).
+
+The surrogate maps steady-flow inputs (obstacle mask, relaxation time, force)
+on an H x W grid to the steady (rho, u) fields.  Architecture (the one the GPU
+kernels implement): a 4-level U-Net with widths 32/64/128/256; every level has
+two 3x3 convolutions (zero padding 1, bias) each followed by ReLU; 2x2 average
+pooling going down; nearest-neighbour 2x upsampling followed by a 3x3
+conv + ReLU going up; concatenation [up path, skip] before the two decoder
+convolutions; a linear 3x3 head with 3 outputs.  Loss: weighted mean squared
+error sum(m (y - t)^2) / (3 sum m) with per-pixel weights m.
+
+Tensors are NHWC float64.  Parameters use the canonical flat layout shared
+with the CUDA library: for each layer in LAYERS order, W[co][ky][kx][ci]
+followed by b[co].
+
+This module is plain numpy, written from the definitions above; it shares no
+code with the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASE = 32
+# (name, input channels, output channels, relu)
+LAYERS = [
+    ("enc1a", 3, 32, True), ("enc1b", 32, 32, True),
+    ("enc2a", 32, 64, True), ("enc2b", 64, 64, True),
+    ("enc3a", 64, 128, True), ("enc3b", 128, 128, True),
+    ("bota", 128, 256, True), ("botb", 256, 256, True),
+    ("up3", 256, 128, True), ("dec3a", 256, 128, True), ("dec3b", 128, 128, True),
+    ("up2", 128, 64, True), ("dec2a", 128, 64, True), ("dec2b", 64, 64, True),
+    ("up1", 64, 32, True), ("dec1a", 64, 32, True), ("dec1b", 32, 32, True),
+    ("head", 32, 3, False),
+]
+
+
+def layer_slices():
+    """(name, cin, cout, relu, w_offset, b_offset) for each layer, and the total."""
+    out, off = [], 0
+    for name, ci, co, relu in LAYERS:
+        out.append((name, ci, co, relu, off, off + 9 * ci * co))
+        off += 9 * ci * co + co
+    return out, off
+
+
+def unpack(params):
+    sl, total = layer_slices()
+    assert params.size == total
+    P = {}
+    for name, ci, co, relu, wo, bo in sl:
+        P[name] = (params[wo:wo + 9 * ci * co].reshape(co, 3, 3, ci), params[bo:bo + co])
+    return P
+
+
+def pack(P):
+    sl, total = layer_slices()
+    out = np.zeros(total)
+    for name, ci, co, relu, wo, bo in sl:
+        W, b = P[name]
+        out[wo:wo + 9 * ci * co] = W.ravel()
+        out[bo:bo + co] = b
+    return out
+
+
+def _cols(x):
+    """im2col of a 3x3, pad-1 convolution: (N, H, W, 9, C), tap index ky*3+kx."""
+    N, H, W, C = x.shape
+    xp = np.zeros((N, H + 2, W + 2, C))
+    xp[:, 1:-1, 1:-1] = x
+    return np.stack([xp[:, ky:ky + H, kx:kx + W] for ky in range(3) for kx in range(3)], axis=3)
+
+
+def conv(x, W, b):
+    """y[n,i,j,o] = b[o] + sum_{ky,kx,c} W[o,ky,kx,c] x[n, i+ky-1, j+kx-1, c]."""
+    N, H, Wd, C = x.shape
+    co = W.shape[0]
+    cols = _cols(x).reshape(N * H * Wd, 9 * C)
+    return (cols @ W.reshape(co, 9 * C).T + b).reshape(N, H, Wd, co)
+
+
+def conv_backward(x, W, dy):
+    """Gradients of conv: (dx, dW, db)."""
+    N, H, Wd, C = x.shape
+    co = W.shape[0]
+    cols = _cols(x).reshape(N * H * Wd, 9 * C)
+    g = dy.reshape(N * H * Wd, co)
+    dW = (g.T @ cols).reshape(co, 3, 3, C)
+    db = g.sum(axis=0)
+    dcols = (g @ W.reshape(co, 9 * C)).reshape(N, H, Wd, 3, 3, C)
+    dxp = np.zeros((N, H + 2, Wd + 2, C))
+    for ky in range(3):
+        for kx in range(3):
+            dxp[:, ky:ky + H, kx:kx + Wd] += dcols[:, :, :, ky, kx]
+    return dxp[:, 1:-1, 1:-1], dW, db
+
+
+def pool(x):
+    N, H, W, C = x.shape
+    return x.reshape(N, H // 2, 2, W // 2, 2, C).mean(axis=(2, 4))
+
+
+def pool_backward(dy):
+    return np.repeat(np.repeat(dy, 2, axis=1), 2, axis=2) * 0.25
+
+
+def up(x):
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def up_backward(dy):
+    N, H, W, C = dy.shape
+    return dy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
+
+
+def relu(z):
+    return np.maximum(z, 0.0)
+
+
+def forward(params, x):
+    """Returns (y, cache)."""
+    P = unpack(params)
+    cache = {}
+
+    def layer(name, inp):
+        W, b = P[name]
+        z = conv(inp, W, b)
+        cache[name] = (inp, z)
+        return relu(z) if dict((l[0], l[3]) for l in LAYERS)[name] else z
+
+    e1 = layer("enc1b", layer("enc1a", x))
+    e2 = layer("enc2b", layer("enc2a", pool(e1)))
+    e3 = layer("enc3b", layer("enc3a", pool(e2)))
+    bb = layer("botb", layer("bota", pool(e3)))
+    u3 = layer("up3", up(bb))
+    d3 = layer("dec3b", layer("dec3a", np.concatenate([u3, e3], axis=3)))
+    u2 = layer("up2", up(d3))
+    d2 = layer("dec2b", layer("dec2a", np.concatenate([u2, e2], axis=3)))
+    u1 = layer("up1", up(d2))
+    d1 = layer("dec1b", layer("dec1a", np.concatenate([u1, e1], axis=3)))
+    y = layer("head", d1)
+    return y, cache
+
+
+def loss(y, t, m):
+    """sum m (y - t)^2 / (3 sum m), m: (N, H, W) weights."""
+    return float((m[..., None] * (y - t) ** 2).sum() / (3.0 * m.sum()))
+
+
+def backward(params, cache, y, t, m):
+    """Gradient of loss(forward(params, x), t, m) with respect to params."""
+    P = unpack(params)
+    relu_of = dict((l[0], l[3]) for l in LAYERS)
+    grads = {}
+    dy = 2.0 * m[..., None] * (y - t) / (3.0 * m.sum())
+
+    def back(name, dout):
+        inp, z = cache[name]
+        dz = dout * (z > 0) if relu_of[name] else dout
+        dx, dW, db = conv_backward(inp, P[name][0], dz)
+        grads[name] = (dW, db)
+        return dx
+
+    dd1 = back("dec1a", back("dec1b", back("head", dy)))
+    du1, de1 = dd1[..., :32], dd1[..., 32:]
+    dd2 = up_backward(back("up1", du1))
+    dd2 = back("dec2a", back("dec2b", dd2))
+    du2, de2 = dd2[..., :64], dd2[..., 64:]
+    dd3 = up_backward(back("up2", du2))
+    dd3 = back("dec3a", back("dec3b", dd3))
+    du3, de3 = dd3[..., :128], dd3[..., 128:]
+    dbb = up_backward(back("up3", du3))
+    dp3 = back("bota", back("botb", dbb))
+    de3 = de3 + pool_backward(dp3)
+    dp2 = back("enc3a", back("enc3b", de3))
+    de2 = de2 + pool_backward(dp2)
+    dp1 = back("enc2a", back("enc2b", de2))
+    de1 = de1 + pool_backward(dp1)
+    back("enc1a", back("enc1b", de1))
+    return pack(grads)
+
+
+def init_params(seed: int):
+    """He-normal weights (std sqrt(2 / (9 cin))), zero biases, drawn with the
+    project's seeded generator (lbm_workloads.SplitMix64)."""
+    import lbm_workloads as W
+    rng = W.SplitMix64(seed)
+    sl, total = layer_slices()
+    out = np.zeros(total)
+    for name, ci, co, relu_, wo, bo in sl:
+        std = np.sqrt(2.0 / (9 * ci)) if relu_ else np.sqrt(1.0 / (9 * ci))
+        out[wo:wo + 9 * ci * co] = rng.normal(9 * ci * co) * std
+    return out
