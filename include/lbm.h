@@ -227,6 +227,38 @@ lbm_status lbm_batch_info(const lbm_batch *b, int i, int64_t *steps, int *tiles,
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---------------------------------------------------------------- surrogate
+ * The steady-flow surrogate of the warm start: a U-Net on an H x W grid
+ * (H, W multiples of 8) mapping per-node inputs x[n][y][x][3] (FP32) to
+ * outputs y[n][y][x][3] (FP32).  Architecture: 4 levels of widths
+ * 32/64/128/256, two 3x3 convolutions + ReLU per level, 2x2 average pooling
+ * down, nearest 2x upsampling + 3x3 conv + ReLU up, concatenation
+ * [up path, skip], linear 3x3 head.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores, FP32 master weights and Adam moments.
+ * Loss: sum_p m[p] sum_c (y - t)^2 * scale (scale = 1 / (3 sum m) gives the
+ * weighted mean).  Parameters (host, FP32) in the canonical layout: per layer
+ * W[co][ky][kx][ci] then b[co], layers in the order enc1a enc1b enc2a enc2b
+ * enc3a enc3b bota botb up3 dec3a dec3b up2 dec2a dec2b up1 dec1a dec1b head.
+ * All *_dev pointers are device arrays of n * H * W pixels. */
+typedef struct lbm_unet lbm_unet;
+
+lbm_status lbm_unet_create(int H, int W, int max_batch, void *stream, lbm_unet **out);
+int64_t lbm_unet_num_params(const lbm_unet *u);
+lbm_status lbm_unet_set_params(lbm_unet *u, const float *host);  /* resets Adam */
+lbm_status lbm_unet_get_params(lbm_unet *u, float *host);
+lbm_status lbm_unet_forward(lbm_unet *u, const float *x_dev, float *y_dev, int n);
+/* Loss and parameter gradient (host outputs nullable; synchronises if given). */
+lbm_status lbm_unet_grad(lbm_unet *u, const float *x_dev, const float *t_dev, const float *m_dev, int n,
+                         float scale, double *loss_host, float *grad_host);
+/* One Adam step from the last gradient (Kingma & Ba, bias-corrected). */
+lbm_status lbm_unet_adam(lbm_unet *u, float lr, float beta1, float beta2, float eps);
+/* Forward, backward and Adam (beta 0.9 / 0.999, eps 1e-8); loss to loss_dev
+ * (nullable).  Asynchronous. */
+lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_dev, const float *m_dev, int n,
+                               float scale, float lr, double *loss_dev);
+const char *lbm_unet_last_error(const lbm_unet *u);
+void lbm_unet_destroy(lbm_unet *u);
+
 /* lbm_check_noalloc -- the FP64 check of lbm_check_device for callers that
  * cannot allocate device memory.  The paper has no counterpart: it is a
  * service of this library.

@@ -116,21 +116,36 @@ def relu(z):
     return np.maximum(z, 0.0)
 
 
-def forward(params, x):
-    """Returns (y, cache)."""
+def bf16(a):
+    """Round to bfloat16, nearest-even, through float32 (the precision in
+    which the GPU kernels hold a value before storing it as bfloat16)."""
+    f = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, x, storage="fp64"):
+    """Returns (y, cache).  storage="bf16" rounds the weights, the input and
+    every stored activation to bfloat16 where the GPU stores them (the
+    arithmetic stays FP64; biases and the head's output are not rounded)."""
     P = unpack(params)
     cache = {}
+    rnd = bf16 if storage == "bf16" else (lambda a: a)
+    relu_of = dict((l[0], l[3]) for l in LAYERS)
 
     def layer(name, inp):
         W, b = P[name]
-        z = conv(inp, W, b)
+        z = conv(inp, rnd(W), b)
         cache[name] = (inp, z)
-        return relu(z) if dict((l[0], l[3]) for l in LAYERS)[name] else z
+        return rnd(relu(z)) if relu_of[name] else z
 
+    x = rnd(x)
+    pool_ = lambda a: rnd(pool(a))
     e1 = layer("enc1b", layer("enc1a", x))
-    e2 = layer("enc2b", layer("enc2a", pool(e1)))
-    e3 = layer("enc3b", layer("enc3a", pool(e2)))
-    bb = layer("botb", layer("bota", pool(e3)))
+    e2 = layer("enc2b", layer("enc2a", pool_(e1)))
+    e3 = layer("enc3b", layer("enc3a", pool_(e2)))
+    bb = layer("botb", layer("bota", pool_(e3)))
     u3 = layer("up3", up(bb))
     d3 = layer("dec3b", layer("dec3a", np.concatenate([u3, e3], axis=3)))
     u2 = layer("up2", up(d3))
@@ -146,9 +161,13 @@ def loss(y, t, m):
     return float((m[..., None] * (y - t) ** 2).sum() / (3.0 * m.sum()))
 
 
-def backward(params, cache, y, t, m):
-    """Gradient of loss(forward(params, x), t, m) with respect to params."""
+def backward(params, cache, y, t, m, storage="fp64"):
+    """Gradient of loss(forward(params, x), t, m) with respect to params (the
+    exact derivative of the forward pass; with storage="bf16" the weights
+    are the rounded ones the forward pass used)."""
     P = unpack(params)
+    if storage == "bf16":
+        P = {k: (bf16(W), b) for k, (W, b) in P.items()}
     relu_of = dict((l[0], l[3]) for l in LAYERS)
     grads = {}
     dy = 2.0 * m[..., None] * (y - t) / (3.0 * m.sum())

@@ -517,3 +517,124 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ surrogate
+def _unet_lib():
+    L = library()
+    if not getattr(L, "_unet_ready", False):
+        U = C.c_void_p
+        fp = C.c_void_p
+        L.lbm_unet_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(U)]
+        L.lbm_unet_num_params.argtypes = [U]
+        L.lbm_unet_num_params.restype = C.c_int64
+        L.lbm_unet_set_params.argtypes = [U, C.POINTER(C.c_float)]
+        L.lbm_unet_get_params.argtypes = [U, C.POINTER(C.c_float)]
+        L.lbm_unet_forward.argtypes = [U, fp, fp, C.c_int]
+        L.lbm_unet_grad.argtypes = [U, fp, fp, fp, C.c_int, C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)]
+        L.lbm_unet_adam.argtypes = [U, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.lbm_unet_train_step.argtypes = [U, fp, fp, fp, C.c_int, C.c_float, C.c_float, C.c_void_p]
+        L.lbm_unet_last_error.argtypes = [U]
+        L.lbm_unet_last_error.restype = C.c_char_p
+        L.lbm_unet_destroy.argtypes = [U]
+        L.lbm_unet_destroy.restype = None
+        for n in ("lbm_unet_create", "lbm_unet_set_params", "lbm_unet_get_params", "lbm_unet_forward",
+                  "lbm_unet_grad", "lbm_unet_adam", "lbm_unet_train_step"):
+            getattr(L, n).restype = C.c_int
+        L._unet_ready = True
+    return L
+
+
+def _ucheck(status, u=None):
+    if status != 0:
+        m = _unet_lib().lbm_unet_last_error(u) if u is not None else library().lbm_last_error(None)
+        raise LbmError(status, m.decode() if m else "")
+
+
+def lbm_unet_create(H, W, max_batch, stream=None):
+    u = C.c_void_p()
+    _ucheck(_unet_lib().lbm_unet_create(int(H), int(W), int(max_batch), stream, C.byref(u)))
+    return u
+
+
+def lbm_unet_num_params(u):
+    return int(_unet_lib().lbm_unet_num_params(u))
+
+
+def lbm_unet_set_params(u, params):
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    _ucheck(_unet_lib().lbm_unet_set_params(u, p.ctypes.data_as(C.POINTER(C.c_float))), u)
+
+
+def lbm_unet_get_params(u, out):
+    _ucheck(_unet_lib().lbm_unet_get_params(u, out.ctypes.data_as(C.POINTER(C.c_float))), u)
+
+
+def lbm_unet_forward(u, x_ptr, y_ptr, n):
+    _ucheck(_unet_lib().lbm_unet_forward(u, x_ptr, y_ptr, int(n)), u)
+
+
+def lbm_unet_grad(u, x_ptr, t_ptr, m_ptr, n, scale, want_grad=True):
+    loss = C.c_double()
+    g = np.empty(lbm_unet_num_params(u), np.float32) if want_grad else None
+    _ucheck(_unet_lib().lbm_unet_grad(u, x_ptr, t_ptr, m_ptr, int(n), float(scale), C.byref(loss),
+                                      g.ctypes.data_as(C.POINTER(C.c_float)) if g is not None else None), u)
+    return loss.value, g
+
+
+def lbm_unet_adam(u, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _ucheck(_unet_lib().lbm_unet_adam(u, float(lr), float(beta1), float(beta2), float(eps)), u)
+
+
+def lbm_unet_train_step(u, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr=None):
+    _ucheck(_unet_lib().lbm_unet_train_step(u, x_ptr, t_ptr, m_ptr, int(n), float(scale), float(lr), loss_ptr), u)
+
+
+def lbm_unet_destroy(u):
+    _unet_lib().lbm_unet_destroy(u)
+
+
+class UNet:
+    """The surrogate network (see lbm.h).  Device tensors are passed as raw
+    pointers (e.g. torch ``data_ptr()``), float32, layout [n][H][W][3]."""
+
+    def __init__(self, H, W, max_batch, stream=None):
+        self.H, self.W, self.B = H, W, max_batch
+        self.u = lbm_unet_create(H, W, max_batch, stream)
+        self.n = lbm_unet_num_params(self.u)
+
+    def set_params(self, p):
+        lbm_unet_set_params(self.u, p)
+
+    def params(self):
+        out = np.empty(self.n, np.float32)
+        lbm_unet_get_params(self.u, out)
+        return out
+
+    def forward(self, x_ptr, y_ptr, n):
+        lbm_unet_forward(self.u, x_ptr, y_ptr, n)
+
+    def grad(self, x_ptr, t_ptr, m_ptr, n, scale, want_grad=True):
+        return lbm_unet_grad(self.u, x_ptr, t_ptr, m_ptr, n, scale, want_grad)
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        lbm_unet_adam(self.u, lr, beta1, beta2, eps)
+
+    def train_step(self, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr=None):
+        lbm_unet_train_step(self.u, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr)
+
+    def close(self):
+        if getattr(self, "u", None) is not None:
+            lbm_unet_destroy(self.u)
+            self.u = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_unet_last_error(u):
+    m = _unet_lib().lbm_unet_last_error(u)
+    return m.decode() if m else ""

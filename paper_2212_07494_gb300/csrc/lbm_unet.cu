@@ -1,0 +1,880 @@
+// lbm_unet.cu -- the steady-flow surrogate: a 4-level U-Net (widths
+// 32/64/128/256, 3x3 convolutions with ReLU, 2x2 average pooling, nearest 2x
+// upsampling followed by a convolution, skip concatenation, linear 3x3 head)
+// trained with a weighted mean-squared error and Adam, entirely in this file's
+// kernels.
+//
+// Activations are NHWC bfloat16; every contraction accumulates in FP32 on the
+// tensor cores (mma.sync m16n8k16 BF16, operands staged by cp.async and read
+// with ldmatrix).  Convolutions are implicit GEMMs:
+//   forward      y[p][co]  = sum_{tap,ci} x[p+tap][ci] W[co][tap][ci]
+//   input grad   dx[p][ci] = sum_{tap,co} dz[p-tap][co] W[co][tap][ci]
+//                (the same kernel with the flipped, transposed weights)
+//   weight grad  dW[co][tap][ci] = sum_p dz[p][co] x[p+tap][ci]
+//                (split over pixel chunks, FP32 atomics)
+// Concatenation is free: producers write into channel slices of one buffer.
+// Master weights and Adam moments are FP32; each update repacks the BF16
+// copies used by the forward and input-gradient kernels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace unet {
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// 16-byte global -> shared copy; zero-filled when !valid (no bytes are read)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// --------------------------------------------------------------- convolution
+struct ConvArgs {
+    const bf16 *x;
+    int xc, xo;          // input channel stride / offset (multiples of 8)
+    const bf16 *w;       // [wrows][9][cin]
+    const float *bias;   // [cout] or null
+    bf16 *y;             // output (null: only yf)
+    int yc, yo;
+    float *yf;           // optional FP32 output [pixel][yfc], channels < yfc
+    int yfc;
+    const bf16 *gate;    // optional: result *= (gate[p][go + co] > 0)
+    int gc, go;
+    int N, H, W, cin, cout, wrows;
+    int relu;
+};
+
+constexpr int CBM = 128, CBN = 64, CPAD = 8;
+
+template <int BK>
+__global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
+    __shared__ __align__(16) bf16 As[2][CBM][BK + CPAD];
+    __shared__ __align__(16) bf16 Bs[2][CBN][BK + CPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const long long M = (long long)a.N * a.H * a.W;
+    const long long m0 = (long long)blockIdx.x * CBM;
+    const int co0 = blockIdx.y * CBN;
+    constexpr int ACH = BK / 8;                 // 16-byte chunks per tile row
+    constexpr int AREP = CBM * ACH / 256;       // A chunks per thread
+    constexpr int BCH = CBN * ACH;              // B chunks per tile
+    // pixel coordinates of this thread's A rows (fixed over the K loop)
+    int an[AREP], ay[AREP], ax[AREP], arow[AREP], acc_[AREP];
+#pragma unroll
+    for (int i = 0; i < AREP; ++i) {
+        const int q = tid + i * 256;
+        arow[i] = q / ACH;
+        acc_[i] = q % ACH;
+        const long long m = m0 + arow[i];
+        if (m < M) {
+            const int hw = a.H * a.W;
+            an[i] = (int)(m / hw);
+            const int r = (int)(m - (long long)an[i] * hw);
+            ay[i] = r / a.W;
+            ax[i] = r - ay[i] * a.W;
+        } else {
+            an[i] = -1;
+            ay[i] = ax[i] = 0;
+        }
+    }
+    const int cblocks = a.cin / BK;
+    const int KB = 9 * cblocks;
+    auto load = [&](int kb, int buf) {
+        const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int i = 0; i < AREP; ++i) {
+            const int yy = ay[i] + dy, xx = ax[i] + dx;
+            const bool ok = an[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = ok ? a.x + ((long long)(an[i] * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 + acc_[i] * 8 : a.x;
+            cp_async16(&As[buf][arow[i]][acc_[i] * 8], src, ok);
+        }
+        for (int q = tid; q < BCH; q += 256) {
+            const int r = q / ACH, cc = q % ACH;
+            const int co = co0 + r;
+            const bool ok = co < a.wrows;
+            const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + cc * 8 : a.w;
+            cp_async16(&Bs[buf][r][cc * 8], src, ok);
+        }
+        cp_async_commit();
+    };
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    load(0, 0);
+    for (int kb = 0; kb < KB; ++kb) {
+        const int buf = kb & 1;
+        if (kb + 1 < KB) {
+            load(kb + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+            unsigned af[2][4], bfr[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldsm_x4(af[mt], &As[buf][wm * 32 + mt * 16 + (lane & 15)][ks * 16 + (lane >> 4) * 8]);
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                ldsm_x4(bfr[p], &Bs[buf][wn * 32 + p * 16 + (lane & 7) + (lane >> 4) * 8][ks * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma16816(acc[mt][nt], af[mt], bfr[nt >> 1][(nt & 1) * 2], bfr[nt >> 1][(nt & 1) * 2 + 1]);
+        }
+        __syncthreads();
+    }
+    // epilogue: bias, ReLU, gate, store
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long m = m0 + wm * 32 + mt * 16 + (lane >> 2) + h * 8;
+                const int co = co0 + wn * 32 + nt * 8 + (lane & 3) * 2;
+                if (m >= M || co >= a.cout) continue;
+                float v[2] = {acc[mt][nt][h * 2], acc[mt][nt][h * 2 + 1]};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (co + e >= a.cout) continue;
+                    if (a.bias) v[e] += a.bias[co + e];
+                    if (a.relu) v[e] = fmaxf(v[e], 0.f);
+                    if (a.gate && !(__bfloat162float(a.gate[m * a.gc + a.go + co + e]) > 0.f)) v[e] = 0.f;
+                    if (a.yf && co + e < a.yfc) a.yf[m * a.yfc + co + e] = v[e];
+                }
+                if (a.y) {
+                    bf16 *dst = a.y + m * a.yc + a.yo + co;
+                    if (co + 1 < a.cout) {
+                        *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn(v[0], v[1]);
+                    } else {
+                        dst[0] = __float2bfloat16_rn(v[0]);
+                    }
+                }
+            }
+}
+
+// ------------------------------------------------------------ weight gradient
+struct WgradArgs {
+    const bf16 *dz;
+    int dzc, dzo;   // gradient with respect to the conv output (pre-activation)
+    const bf16 *x;
+    int xc, xo;     // conv input
+    float *dw;      // [wrows][9][cin]
+    int N, H, W, cin, cout;
+    int pix;        // pixels per block
+};
+
+constexpr int WBM = 64, WBN = 32, WBK = 32, WPAD = 8;
+
+__global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
+    __shared__ __align__(16) bf16 As[2][WBK][WBM + WPAD];  // [pixel][co]
+    __shared__ __align__(16) bf16 Bs[2][WBK][WBN + WPAD];  // [pixel][ci]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const long long P = (long long)a.N * a.H * a.W;
+    const long long p_begin = (long long)blockIdx.x * a.pix;
+    const long long p_end = p_begin + a.pix < P ? p_begin + a.pix : P;
+    const int co0 = blockIdx.y * WBM;
+    const int cblocks = (a.cin + WBN - 1) / WBN;
+    const int tap = blockIdx.z / cblocks, ci0 = (blockIdx.z % cblocks) * WBN;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int hw = a.H * a.W;
+    auto load = [&](long long p0, int buf) {
+        // A: 32 pixels x 64 co = 256 chunks, two per thread
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = tid + i * 128;
+            const int r = q >> 3, cc = q & 7;
+            const long long p = p0 + r;
+            const int co = co0 + cc * 8;
+            const bool ok = p < p_end && co < a.cout;
+            const bf16 *src = ok ? a.dz + p * a.dzc + a.dzo + co : a.dz;
+            cp_async16(&As[buf][r][cc * 8], src, ok);
+        }
+        // B: 32 pixels x 32 ci = 128 chunks, one per thread (input shifted by the tap)
+        {
+            const int r = tid >> 2, cc = tid & 3;
+            const long long p = p0 + r;
+            bool ok = p < p_end && ci0 + cc * 8 < a.cin;
+            const bf16 *src = a.x;
+            if (ok) {
+                const int n = (int)(p / hw);
+                const int rr = (int)(p - (long long)n * hw);
+                const int yy = rr / a.W + dy, xx = rr % a.W + dx;
+                ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                if (ok) src = a.x + ((long long)(n * a.H + yy) * a.W + xx) * a.xc + a.xo + ci0 + cc * 8;
+            }
+            cp_async16(&Bs[buf][r][cc * 8], src, ok);
+        }
+        cp_async_commit();
+    };
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    const int KB = (int)((p_end - p_begin + WBK - 1) / WBK);
+    if (KB > 0) load(p_begin, 0);
+    for (int kb = 0; kb < KB; ++kb) {
+        const int buf = kb & 1;
+        if (kb + 1 < KB) {
+            load(p_begin + (long long)(kb + 1) * WBK, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < WBK / 16; ++ks) {
+            unsigned af[2][4], bfr[4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldsm_x4_t(af[mt], &As[buf][ks * 16 + (lane & 7) + (lane >> 4) * 8][wm * 32 + mt * 16 + ((lane >> 3) & 1) * 8]);
+            ldsm_x4_t(bfr, &Bs[buf][ks * 16 + (lane & 7) + ((lane >> 3) & 1) * 8][wn * 16 + (lane >> 4) * 8]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) mma16816(acc[mt][nt], af[mt], bfr[nt * 2], bfr[nt * 2 + 1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = co0 + wm * 32 + mt * 16 + (lane >> 2) + (e >> 1) * 8;
+                const int ci = ci0 + wn * 16 + nt * 8 + (lane & 3) * 2 + (e & 1);
+                if (co < a.cout && ci < a.cin) atomicAdd(a.dw + ((long long)co * 9 + tap) * a.cin + ci, acc[mt][nt][e]);
+            }
+}
+
+// ------------------------------------------------------------- small kernels
+// bias gradient: db[c] += sum_p dz[p][c]; block = 256 pixels x all channels
+__global__ void k_bias_grad(const bf16 *dz, int dzc, int dzo, int C, long long P, float *db) {
+    const int c = threadIdx.x;
+    if (c >= C) return;
+    const long long p0 = (long long)blockIdx.x * 256;
+    float s = 0.f;
+    for (int i = 0; i < 256; ++i) {
+        const long long p = p0 + i;
+        if (p >= P) break;
+        s += __bfloat162float(dz[p * dzc + dzo + c]);
+    }
+    atomicAdd(db + c, s);
+}
+
+// 2x2 average pooling: y[n][i][j] = mean of x[n][2i..2i+1][2j..2j+1]
+__global__ void k_pool(const bf16 *x, int xc, int xo, bf16 *y, int yc, int yo, int N, int H, int W, int C) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Ho * Wo * C;
+    if (idx >= total) return;
+    const int c = (int)(idx % C);
+    const long long q = idx / C;
+    const int j = (int)(q % Wo), i = (int)((q / Wo) % Ho), n = (int)(q / ((long long)Wo * Ho));
+    auto at = [&](int yy, int xx) {
+        return __bfloat162float(x[((long long)(n * H + yy) * W + xx) * xc + xo + c]);
+    };
+    const float s = 0.25f * (at(2 * i, 2 * j) + at(2 * i, 2 * j + 1) + at(2 * i + 1, 2 * j) + at(2 * i + 1, 2 * j + 1));
+    y[((long long)(n * Ho + i) * Wo + j) * yc + yo + c] = __float2bfloat16_rn(s);
+}
+
+// pooling backward at the fine resolution, gated by the fine activation:
+// dst[n][y][x][c] (+)= 0.25 dy[n][y/2][x/2][c] * (gate > 0)
+__global__ void k_pool_back(const bf16 *dy, int dyc, int dyo, const bf16 *gate, int gc, int go, bf16 *dst, int dc, int dof,
+                            int N, int H, int W, int C, int accumulate) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * H * W * C;
+    if (idx >= total) return;
+    const int c = (int)(idx % C);
+    const long long p = idx / C;
+    const int x = (int)(p % W), yv = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    const long long pc = ((long long)(n * (H / 2) + yv / 2) * (W / 2) + x / 2);
+    float v = 0.25f * __bfloat162float(dy[pc * dyc + dyo + c]);
+    if (!(__bfloat162float(gate[p * gc + go + c]) > 0.f)) v = 0.f;
+    bf16 *d = dst + p * dc + dof + c;
+    if (accumulate) v += __bfloat162float(*d);
+    *d = __float2bfloat16_rn(v);
+}
+
+// nearest 2x upsampling: y[n][i][j] = x[n][i/2][j/2]
+__global__ void k_up(const bf16 *x, int xc, int xo, bf16 *y, int yc, int yo, int N, int H, int W, int C) {
+    // H, W: fine (output) sizes
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * H * W * C;
+    if (idx >= total) return;
+    const int c = (int)(idx % C);
+    const long long p = idx / C;
+    const int j = (int)(p % W), i = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    y[p * yc + yo + c] = x[((long long)(n * (H / 2) + i / 2) * (W / 2) + j / 2) * xc + xo + c];
+}
+
+// upsampling backward at the coarse resolution, gated by the coarse activation
+__global__ void k_up_back(const bf16 *dy, int dyc, int dyo, const bf16 *gate, int gc, int go, bf16 *dst, int dc, int dof,
+                          int N, int H, int W, int C) {
+    // H, W: coarse sizes
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * H * W * C;
+    if (idx >= total) return;
+    const int c = (int)(idx % C);
+    const long long p = idx / C;
+    const int j = (int)(p % W), i = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    const int W2 = 2 * W, H2 = 2 * H;
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            s += __bfloat162float(dy[((long long)(n * H2 + 2 * i + a) * W2 + 2 * j + b) * dyc + dyo + c]);
+    if (!(__bfloat162float(gate[p * gc + go + c]) > 0.f)) s = 0.f;
+    dst[p * dc + dof + c] = __float2bfloat16_rn(s);
+}
+
+// inputs [p][3] FP32 -> [p][16] BF16 (channels 3..15 zero)
+__global__ void k_pack_input(const float *x, bf16 *y, long long P) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[p * 16 + c] = __float2bfloat16_rn(c < 3 ? x[p * 3 + c] : 0.f);
+}
+
+// weighted MSE: loss += sum m (y - t)^2 * scale; dz[p][c] = 2 m (y - t) scale
+// (c < 3; channels 3..dzc-1 zero), scale = 1 / (3 sum m)
+__global__ void k_loss(const float *y, const float *t, const float *m, long long P, float scale, bf16 *dz, int dzc,
+                       double *loss) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (p < P) {
+        const float w = m[p];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = y[p * 3 + c] - t[p * 3 + c];
+            l += (double)(w * d * d) * scale;
+            dz[p * dzc + c] = __float2bfloat16_rn(2.f * w * d * scale);
+        }
+        for (int c = 3; c < dzc; ++c) dz[p * dzc + c] = __float2bfloat16_rn(0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+}
+
+// Adam on the FP32 master parameters (Kingma & Ba, bias-corrected)
+__global__ void k_adam(float *p, float *m, float *v, const float *g, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of one layer: w[co][tap][ci] and wt[ci][8 - tap][co]
+__global__ void k_pack_weights(const float *wf, bf16 *w, bf16 *wt, int coutp, int cinp) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)coutp * 9 * cinp;
+    if (i >= n) return;
+    const int ci = (int)(i % cinp);
+    const int tap = (int)((i / cinp) % 9);
+    const int co = (int)(i / (9LL * cinp));
+    const bf16 v = __float2bfloat16_rn(wf[i]);
+    w[i] = v;
+    wt[((long long)ci * 9 + (8 - tap)) * coutp + co] = v;
+}
+
+}  // namespace unet
+
+// ====================================================================== host
+using namespace unet;
+
+namespace {
+
+struct Layer {
+    const char *name;
+    int cin, cout, relu;
+    int cinp, coutp;          // padded: input 16 for the 3-channel input, head 32 outputs
+    size_t woff, boff;        // offsets in the FP32 master buffer (padded layout)
+    size_t canon_w, canon_b;  // offsets in the canonical layout
+    bf16 *w = nullptr, *wt = nullptr;
+};
+
+const struct { const char *name; int cin, cout, relu; } kArch[] = {
+    {"enc1a", 3, 32, 1},   {"enc1b", 32, 32, 1},   {"enc2a", 32, 64, 1},   {"enc2b", 64, 64, 1},
+    {"enc3a", 64, 128, 1}, {"enc3b", 128, 128, 1}, {"bota", 128, 256, 1},  {"botb", 256, 256, 1},
+    {"up3", 256, 128, 1},  {"dec3a", 256, 128, 1}, {"dec3b", 128, 128, 1}, {"up2", 128, 64, 1},
+    {"dec2a", 128, 64, 1}, {"dec2b", 64, 64, 1},   {"up1", 64, 32, 1},     {"dec1a", 64, 32, 1},
+    {"dec1b", 32, 32, 1},  {"head", 32, 3, 0},
+};
+constexpr int kL = sizeof(kArch) / sizeof(kArch[0]);
+enum { E1A, E1B, E2A, E2B, E3A, E3B, BA, BB, U3, D3A, D3B, U2, D2A, D2B, U1, D1A, D1B, HEAD };
+
+}  // namespace
+
+struct lbm_unet {
+    int H = 0, W = 0, B = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Layer L[kL];
+    size_t nparam = 0, ncanon = 0;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // padded FP32
+    int adam_t = 0;
+    // activations (bf16, NHWC) and gradients
+    bf16 *x0, *e1a, *cat1, *p1, *e2a, *cat2, *p2, *e3a, *cat3, *p3, *ba, *bb, *u3in, *d3a, *d3, *u2in, *d2a, *d2, *u1in,
+        *d1a, *d1;
+    bf16 *g_head, *g_d1, *g_d1a, *g_cat1, *g_u1in, *g_d2, *g_d2a, *g_cat2, *g_u2in, *g_d3, *g_d3a, *g_cat3, *g_u3in, *g_bb,
+        *g_ba, *g_p3, *g_e3a, *g_p2, *g_e2a, *g_p1, *g_e1a;
+    float *yf = nullptr;
+    double *loss = nullptr;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+namespace {
+
+lbm_status ufail(lbm_unet *u, lbm_status st, const std::string &m) {
+    if (u) u->err = m;
+    lbm::set_thread_error(m.c_str());
+    return st;
+}
+
+#define U_CUDA(u, call)                                                                           \
+    do {                                                                                          \
+        cudaError_t e__ = (call);                                                                 \
+        if (e__ != cudaSuccess)                                                                   \
+            return ufail((u), e__ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,      \
+                         std::string(#call) + ": " + cudaGetErrorString(e__));                    \
+    } while (0)
+
+template <typename T>
+lbm_status ualloc(lbm_unet *u, T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return ufail(u, LBM_ERR_OOM, "device allocation failed");
+    }
+    u->allocs.push_back(q);
+    *p = (T *)q;
+    return LBM_OK;
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H, int W, bf16 *y, int yc, int yo,
+                bool forward, const bf16 *gate = nullptr, int gc = 0, int go = 0, float *yf = nullptr, int yfc = 0) {
+    const Layer &l = u->L[li];
+    ConvArgs a{};
+    a.x = x;
+    a.xc = xc;
+    a.xo = xo;
+    a.N = n;
+    a.H = H;
+    a.W = W;
+    a.y = y;
+    a.yc = yc;
+    a.yo = yo;
+    a.yf = yf;
+    a.yfc = yfc;
+    a.gate = gate;
+    a.gc = gc;
+    a.go = go;
+    if (forward) {
+        a.w = l.w;
+        a.bias = u->p + l.boff;
+        a.cin = l.cinp;
+        a.cout = l.cout;
+        a.wrows = l.coutp;
+        a.relu = l.relu;
+    } else {
+        // input gradient: conv of dz (coutp channels) with the flipped transpose
+        a.w = l.wt;
+        a.bias = nullptr;
+        a.cin = l.coutp;
+        a.cout = l.cinp;
+        a.wrows = l.cinp;
+        a.relu = 0;
+    }
+    const long long M = (long long)n * H * W;
+    dim3 grid(nblk(M, CBM), nblk(a.cout, CBN));
+    if (a.cin % 32 == 0) k_conv<32><<<grid, 256, 0, u->stream>>>(a);
+    else k_conv<16><<<grid, 256, 0, u->stream>>>(a);
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, int xc, int xo, int n, int H, int W) {
+    const Layer &l = u->L[li];
+    WgradArgs a{};
+    a.dz = dz;
+    a.dzc = dzc;
+    a.dzo = 0;
+    a.x = x;
+    a.xc = xc;
+    a.xo = xo;
+    a.dw = u->g + l.woff;
+    a.N = n;
+    a.H = H;
+    a.W = W;
+    a.cin = l.cinp;
+    a.cout = l.coutp;
+    const long long P = (long long)n * H * W;
+    a.pix = 2048;
+    dim3 grid(nblk(P, a.pix), nblk(l.coutp, WBM), 9 * ((l.cinp + WBN - 1) / WBN));
+    k_wgrad<<<grid, 128, 0, u->stream>>>(a);
+    U_CUDA(u, cudaGetLastError());
+    k_bias_grad<<<nblk(P, 256), ((l.coutp + 31) / 32) * 32, 0, u->stream>>>(dz, dzc, 0, l.cout, P, u->g + l.boff);
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status repack(lbm_unet *u) {
+    for (int i = 0; i < kL; ++i) {
+        const Layer &l = u->L[i];
+        const long long n = (long long)l.coutp * 9 * l.cinp;
+        k_pack_weights<<<nblk(n, 256), 256, 0, u->stream>>>(u->p + l.woff, l.w, l.wt, l.coutp, l.cinp);
+        U_CUDA(u, cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+lbm_status forward(lbm_unet *u, const float *xin, int n) {
+    const int H = u->H, W = u->W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4, H8 = H / 8, W8 = W / 8;
+    lbm_status st;
+    const long long P = (long long)n * H * W;
+    k_pack_input<<<nblk(P, 256), 256, 0, u->stream>>>(xin, u->x0, P);
+    U_CUDA(u, cudaGetLastError());
+#define FW(li, x, xc, xo, h, w, y, yc, yo) \
+    if ((st = conv(u, li, x, xc, xo, n, h, w, y, yc, yo, true)) != LBM_OK) return st;
+    FW(E1A, u->x0, 16, 0, H, W, u->e1a, 32, 0);
+    FW(E1B, u->e1a, 32, 0, H, W, u->cat1, 64, 32);
+    k_pool<<<nblk((long long)n * H2 * W2 * 32, 256), 256, 0, u->stream>>>(u->cat1, 64, 32, u->p1, 32, 0, n, H, W, 32);
+    FW(E2A, u->p1, 32, 0, H2, W2, u->e2a, 64, 0);
+    FW(E2B, u->e2a, 64, 0, H2, W2, u->cat2, 128, 64);
+    k_pool<<<nblk((long long)n * H4 * W4 * 64, 256), 256, 0, u->stream>>>(u->cat2, 128, 64, u->p2, 64, 0, n, H2, W2, 64);
+    FW(E3A, u->p2, 64, 0, H4, W4, u->e3a, 128, 0);
+    FW(E3B, u->e3a, 128, 0, H4, W4, u->cat3, 256, 128);
+    k_pool<<<nblk((long long)n * H8 * W8 * 128, 256), 256, 0, u->stream>>>(u->cat3, 256, 128, u->p3, 128, 0, n, H4, W4, 128);
+    FW(BA, u->p3, 128, 0, H8, W8, u->ba, 256, 0);
+    FW(BB, u->ba, 256, 0, H8, W8, u->bb, 256, 0);
+    k_up<<<nblk((long long)n * H4 * W4 * 256, 256), 256, 0, u->stream>>>(u->bb, 256, 0, u->u3in, 256, 0, n, H4, W4, 256);
+    FW(U3, u->u3in, 256, 0, H4, W4, u->cat3, 256, 0);
+    FW(D3A, u->cat3, 256, 0, H4, W4, u->d3a, 128, 0);
+    FW(D3B, u->d3a, 128, 0, H4, W4, u->d3, 128, 0);
+    k_up<<<nblk((long long)n * H2 * W2 * 128, 256), 256, 0, u->stream>>>(u->d3, 128, 0, u->u2in, 128, 0, n, H2, W2, 128);
+    FW(U2, u->u2in, 128, 0, H2, W2, u->cat2, 128, 0);
+    FW(D2A, u->cat2, 128, 0, H2, W2, u->d2a, 64, 0);
+    FW(D2B, u->d2a, 64, 0, H2, W2, u->d2, 64, 0);
+    k_up<<<nblk((long long)n * H * W * 64, 256), 256, 0, u->stream>>>(u->d2, 64, 0, u->u1in, 64, 0, n, H, W, 64);
+    FW(U1, u->u1in, 64, 0, H, W, u->cat1, 64, 0);
+    FW(D1A, u->cat1, 64, 0, H, W, u->d1a, 32, 0);
+    FW(D1B, u->d1a, 32, 0, H, W, u->d1, 32, 0);
+#undef FW
+    if ((st = conv(u, HEAD, u->d1, 32, 0, n, H, W, nullptr, 0, 0, true, nullptr, 0, 0, u->yf, 3)) != LBM_OK) return st;
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
+// gradients of the weighted MSE into u->g (zeroed first); loss into u->loss
+lbm_status backward(lbm_unet *u, const float *t, const float *m, int n, float scale) {
+    const int H = u->H, W = u->W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4, H8 = H / 8, W8 = W / 8;
+    const long long P = (long long)n * H * W;
+    lbm_status st;
+    U_CUDA(u, cudaMemsetAsync(u->g, 0, u->nparam * sizeof(float), u->stream));
+    U_CUDA(u, cudaMemsetAsync(u->loss, 0, sizeof(double), u->stream));
+    k_loss<<<nblk(P, 256), 256, 0, u->stream>>>(u->yf, t, m, P, scale, u->g_head, 32, u->loss);
+    U_CUDA(u, cudaGetLastError());
+#define WG(li, dz, dzc, x, xc, xo, h, w) \
+    if ((st = wgrad(u, li, dz, dzc, x, xc, xo, n, h, w)) != LBM_OK) return st;
+#define DG(li, dz, dzc, h, w, y, yc, yo, gate, gc, go) \
+    if ((st = conv(u, li, dz, dzc, 0, n, h, w, y, yc, yo, false, gate, gc, go)) != LBM_OK) return st;
+    // head and decoder level 1
+    WG(HEAD, u->g_head, 32, u->d1, 32, 0, H, W);
+    DG(HEAD, u->g_head, 32, H, W, u->g_d1, 32, 0, u->d1, 32, 0);
+    WG(D1B, u->g_d1, 32, u->d1a, 32, 0, H, W);
+    DG(D1B, u->g_d1, 32, H, W, u->g_d1a, 32, 0, u->d1a, 32, 0);
+    WG(D1A, u->g_d1a, 32, u->cat1, 64, 0, H, W);
+    DG(D1A, u->g_d1a, 32, H, W, u->g_cat1, 64, 0, u->cat1, 64, 0);  // [dz up1 | dz enc1b (decoder part)]
+    WG(U1, u->g_cat1, 64, u->u1in, 64, 0, H, W);
+    DG(U1, u->g_cat1, 64, H, W, u->g_u1in, 64, 0, nullptr, 0, 0);
+    k_up_back<<<nblk((long long)n * H2 * W2 * 64, 256), 256, 0, u->stream>>>(u->g_u1in, 64, 0, u->d2, 64, 0, u->g_d2, 64, 0,
+                                                                            n, H2, W2, 64);
+    // decoder level 2
+    WG(D2B, u->g_d2, 64, u->d2a, 64, 0, H2, W2);
+    DG(D2B, u->g_d2, 64, H2, W2, u->g_d2a, 64, 0, u->d2a, 64, 0);
+    WG(D2A, u->g_d2a, 64, u->cat2, 128, 0, H2, W2);
+    DG(D2A, u->g_d2a, 64, H2, W2, u->g_cat2, 128, 0, u->cat2, 128, 0);
+    WG(U2, u->g_cat2, 128, u->u2in, 128, 0, H2, W2);
+    DG(U2, u->g_cat2, 128, H2, W2, u->g_u2in, 128, 0, nullptr, 0, 0);
+    k_up_back<<<nblk((long long)n * H4 * W4 * 128, 256), 256, 0, u->stream>>>(u->g_u2in, 128, 0, u->d3, 128, 0, u->g_d3,
+                                                                             128, 0, n, H4, W4, 128);
+    // decoder level 3
+    WG(D3B, u->g_d3, 128, u->d3a, 128, 0, H4, W4);
+    DG(D3B, u->g_d3, 128, H4, W4, u->g_d3a, 128, 0, u->d3a, 128, 0);
+    WG(D3A, u->g_d3a, 128, u->cat3, 256, 0, H4, W4);
+    DG(D3A, u->g_d3a, 128, H4, W4, u->g_cat3, 256, 0, u->cat3, 256, 0);
+    WG(U3, u->g_cat3, 256, u->u3in, 256, 0, H4, W4);
+    DG(U3, u->g_cat3, 256, H4, W4, u->g_u3in, 256, 0, nullptr, 0, 0);
+    k_up_back<<<nblk((long long)n * H8 * W8 * 256, 256), 256, 0, u->stream>>>(u->g_u3in, 256, 0, u->bb, 256, 0, u->g_bb,
+                                                                             256, 0, n, H8, W8, 256);
+    // bottleneck
+    WG(BB, u->g_bb, 256, u->ba, 256, 0, H8, W8);
+    DG(BB, u->g_bb, 256, H8, W8, u->g_ba, 256, 0, u->ba, 256, 0);
+    WG(BA, u->g_ba, 256, u->p3, 128, 0, H8, W8);
+    DG(BA, u->g_ba, 256, H8, W8, u->g_p3, 128, 0, nullptr, 0, 0);
+    // encoder level 3: dz of enc3b = decoder part + pooling path (gated by enc3b > 0)
+    k_pool_back<<<nblk((long long)n * H4 * W4 * 128, 256), 256, 0, u->stream>>>(u->g_p3, 128, 0, u->cat3, 256, 128,
+                                                                               u->g_cat3, 256, 128, n, H4, W4, 128, 1);
+    WG(E3B, u->g_cat3 + 128, 256, u->e3a, 128, 0, H4, W4);
+    DG(E3B, u->g_cat3 + 128, 256, H4, W4, u->g_e3a, 128, 0, u->e3a, 128, 0);
+    WG(E3A, u->g_e3a, 128, u->p2, 64, 0, H4, W4);
+    DG(E3A, u->g_e3a, 128, H4, W4, u->g_p2, 64, 0, nullptr, 0, 0);
+    k_pool_back<<<nblk((long long)n * H2 * W2 * 64, 256), 256, 0, u->stream>>>(u->g_p2, 64, 0, u->cat2, 128, 64, u->g_cat2,
+                                                                              128, 64, n, H2, W2, 64, 1);
+    WG(E2B, u->g_cat2 + 64, 128, u->e2a, 64, 0, H2, W2);
+    DG(E2B, u->g_cat2 + 64, 128, H2, W2, u->g_e2a, 64, 0, u->e2a, 64, 0);
+    WG(E2A, u->g_e2a, 64, u->p1, 32, 0, H2, W2);
+    DG(E2A, u->g_e2a, 64, H2, W2, u->g_p1, 32, 0, nullptr, 0, 0);
+    k_pool_back<<<nblk((long long)n * H * W * 32, 256), 256, 0, u->stream>>>(u->g_p1, 32, 0, u->cat1, 64, 32, u->g_cat1, 64,
+                                                                            32, n, H, W, 32, 1);
+    WG(E1B, u->g_cat1 + 32, 64, u->e1a, 32, 0, H, W);
+    DG(E1B, u->g_cat1 + 32, 64, H, W, u->g_e1a, 32, 0, u->e1a, 32, 0);
+    WG(E1A, u->g_e1a, 32, u->x0, 16, 0, H, W);
+#undef WG
+#undef DG
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_unet_destroy(lbm_unet *u) {
+    if (!u) return;
+    if (u->stream) cudaStreamSynchronize(u->stream);
+    for (void *p : u->allocs) cudaFree(p);
+    if (u->own_stream && u->stream) cudaStreamDestroy(u->stream);
+    delete u;
+}
+
+lbm_status lbm_unet_create(int H, int W, int max_batch, void *stream, lbm_unet **out) {
+    if (!out) return ufail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (H < 8 || W < 8 || H % 8 || W % 8 || max_batch < 1)
+        return ufail(nullptr, LBM_ERR_ARG, "H and W must be multiples of 8 (>= 8), max_batch >= 1");
+    lbm_unet *u = new lbm_unet();
+    u->H = H;
+    u->W = W;
+    u->B = max_batch;
+    if (stream) {
+        u->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&u->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete u;
+            return ufail(nullptr, LBM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        u->own_stream = true;
+    }
+    size_t off = 0, coff = 0;
+    for (int i = 0; i < kL; ++i) {
+        Layer &l = u->L[i];
+        l.name = kArch[i].name;
+        l.cin = kArch[i].cin;
+        l.cout = kArch[i].cout;
+        l.relu = kArch[i].relu;
+        l.cinp = l.cin < 16 ? 16 : l.cin;
+        l.coutp = l.cout < 32 ? 32 : l.cout;
+        l.woff = off;
+        off += (size_t)l.coutp * 9 * l.cinp;
+        l.boff = off;
+        off += (size_t)l.coutp;
+        l.canon_w = coff;
+        coff += (size_t)l.cout * 9 * l.cin;
+        l.canon_b = coff;
+        coff += (size_t)l.cout;
+    }
+    u->nparam = off;
+    u->ncanon = coff;
+    const size_t B = max_batch;
+    const size_t P1 = B * H * W, P2 = P1 / 4, P3 = P1 / 16, P4 = P1 / 64;
+    lbm_status st = LBM_OK;
+    auto A = [&](bf16 **p, size_t n) {
+        if (st == LBM_OK) st = ualloc(u, p, n);
+    };
+    if ((st = ualloc(u, &u->p, off)) || (st = ualloc(u, &u->m, off)) || (st = ualloc(u, &u->v, off)) ||
+        (st = ualloc(u, &u->g, off)) || (st = ualloc(u, &u->yf, P1 * 3)) || (st = ualloc(u, &u->loss, 1))) {
+        lbm_unet_destroy(u);
+        return ufail(nullptr, st, "device allocation failed");
+    }
+    for (int i = 0; i < kL; ++i) {
+        A(&u->L[i].w, (size_t)u->L[i].coutp * 9 * u->L[i].cinp);
+        A(&u->L[i].wt, (size_t)u->L[i].coutp * 9 * u->L[i].cinp);
+    }
+    A(&u->x0, P1 * 16); A(&u->e1a, P1 * 32); A(&u->cat1, P1 * 64); A(&u->p1, P2 * 32); A(&u->e2a, P2 * 64);
+    A(&u->cat2, P2 * 128); A(&u->p2, P3 * 64); A(&u->e3a, P3 * 128); A(&u->cat3, P3 * 256); A(&u->p3, P4 * 128);
+    A(&u->ba, P4 * 256); A(&u->bb, P4 * 256); A(&u->u3in, P3 * 256); A(&u->d3a, P3 * 128); A(&u->d3, P3 * 128);
+    A(&u->u2in, P2 * 128); A(&u->d2a, P2 * 64); A(&u->d2, P2 * 64); A(&u->u1in, P1 * 64); A(&u->d1a, P1 * 32);
+    A(&u->d1, P1 * 32);
+    A(&u->g_head, P1 * 32); A(&u->g_d1, P1 * 32); A(&u->g_d1a, P1 * 32); A(&u->g_cat1, P1 * 64);
+    A(&u->g_u1in, P1 * 64); A(&u->g_d2, P2 * 64); A(&u->g_d2a, P2 * 64); A(&u->g_cat2, P2 * 128);
+    A(&u->g_u2in, P2 * 128); A(&u->g_d3, P3 * 128); A(&u->g_d3a, P3 * 128); A(&u->g_cat3, P3 * 256);
+    A(&u->g_u3in, P3 * 256); A(&u->g_bb, P4 * 256); A(&u->g_ba, P4 * 256); A(&u->g_p3, P4 * 128);
+    A(&u->g_e3a, P3 * 128); A(&u->g_p2, P3 * 64); A(&u->g_e2a, P2 * 64); A(&u->g_p1, P2 * 32); A(&u->g_e1a, P1 * 32);
+    if (st != LBM_OK) {
+        lbm_unet_destroy(u);
+        return ufail(nullptr, st, "device allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(u->p, 0, off * 4, u->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, off * 4, u->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, off * 4, u->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) {
+        lbm_unet_destroy(u);
+        return ufail(nullptr, LBM_ERR_CUDA, "initialisation failed");
+    }
+    *out = u;
+    return LBM_OK;
+}
+
+int64_t lbm_unet_num_params(const lbm_unet *u) { return u ? (int64_t)u->ncanon : 0; }
+
+// canonical layout (per layer W[co][ky][kx][ci], b[co]) <-> padded master buffer
+lbm_status lbm_unet_set_params(lbm_unet *u, const float *host) {
+    if (!u || !host) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    std::vector<float> pad(u->nparam, 0.f);
+    for (int i = 0; i < kL; ++i) {
+        const Layer &l = u->L[i];
+        for (int co = 0; co < l.cout; ++co) {
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin; ++ci)
+                    pad[l.woff + ((size_t)co * 9 + t) * l.cinp + ci] = host[l.canon_w + ((size_t)co * 9 + t) * l.cin + ci];
+            pad[l.boff + co] = host[l.canon_b + co];
+        }
+    }
+    U_CUDA(u, cudaMemcpyAsync(u->p, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, u->stream));
+    U_CUDA(u, cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream));
+    U_CUDA(u, cudaMemsetAsync(u->v, 0, u->nparam * 4, u->stream));
+    u->adam_t = 0;
+    lbm_status st = repack(u);
+    if (st != LBM_OK) return st;
+    U_CUDA(u, cudaStreamSynchronize(u->stream));
+    return LBM_OK;
+}
+
+static lbm_status copy_out(lbm_unet *u, const float *dev, float *host) {
+    std::vector<float> pad(u->nparam);
+    U_CUDA(u, cudaMemcpyAsync(pad.data(), dev, pad.size() * 4, cudaMemcpyDeviceToHost, u->stream));
+    U_CUDA(u, cudaStreamSynchronize(u->stream));
+    for (int i = 0; i < kL; ++i) {
+        const Layer &l = u->L[i];
+        for (int co = 0; co < l.cout; ++co) {
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin; ++ci)
+                    host[l.canon_w + ((size_t)co * 9 + t) * l.cin + ci] = pad[l.woff + ((size_t)co * 9 + t) * l.cinp + ci];
+            host[l.canon_b + co] = pad[l.boff + co];
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_get_params(lbm_unet *u, float *host) {
+    if (!u || !host) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    return copy_out(u, u->p, host);
+}
+
+lbm_status lbm_unet_forward(lbm_unet *u, const float *x_dev, float *y_dev, int n) {
+    if (!u || !x_dev || !y_dev) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    if (n < 1 || n > u->B) return ufail(u, LBM_ERR_ARG, "batch size out of range");
+    lbm_status st = forward(u, x_dev, n);
+    if (st != LBM_OK) return st;
+    U_CUDA(u, cudaMemcpyAsync(y_dev, u->yf, (size_t)n * u->H * u->W * 3 * 4, cudaMemcpyDeviceToDevice, u->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_grad(lbm_unet *u, const float *x_dev, const float *t_dev, const float *m_dev, int n, float scale,
+                         double *loss_host, float *grad_host) {
+    if (!u || !x_dev || !t_dev || !m_dev) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    if (n < 1 || n > u->B) return ufail(u, LBM_ERR_ARG, "batch size out of range");
+    lbm_status st = forward(u, x_dev, n);
+    if (st == LBM_OK) st = backward(u, t_dev, m_dev, n, scale);
+    if (st != LBM_OK) return st;
+    if (loss_host) {
+        U_CUDA(u, cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->stream));
+        U_CUDA(u, cudaStreamSynchronize(u->stream));
+    }
+    if (grad_host) return copy_out(u, u->g, grad_host);
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_adam(lbm_unet *u, float lr, float beta1, float beta2, float eps) {
+    if (!u) return ufail(nullptr, LBM_ERR_ARG, "NULL argument");
+    u->adam_t += 1;
+    const float c1 = 1.f - powf(beta1, (float)u->adam_t), c2 = 1.f - powf(beta2, (float)u->adam_t);
+    k_adam<<<nblk((long long)u->nparam, 256), 256, 0, u->stream>>>(u->p, u->m, u->v, u->g, (long long)u->nparam, lr,
+                                                                   beta1, beta2, eps, c1, c2);
+    U_CUDA(u, cudaGetLastError());
+    return repack(u);
+}
+
+lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_dev, const float *m_dev, int n,
+                               float scale, float lr, double *loss_dev) {
+    if (!u || !x_dev || !t_dev || !m_dev) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    if (n < 1 || n > u->B) return ufail(u, LBM_ERR_ARG, "batch size out of range");
+    lbm_status st = forward(u, x_dev, n);
+    if (st == LBM_OK) st = backward(u, t_dev, m_dev, n, scale);
+    if (st == LBM_OK) st = lbm_unet_adam(u, lr, 0.9f, 0.999f, 1e-8f);
+    if (st != LBM_OK) return st;
+    if (loss_dev) U_CUDA(u, cudaMemcpyAsync(loss_dev, u->loss, sizeof(double), cudaMemcpyDeviceToDevice, u->stream));
+    return LBM_OK;
+}
+
+const char *lbm_unet_last_error(const lbm_unet *u) { return u ? u->err.c_str() : ""; }
+
+}  // extern "C"
