@@ -54,8 +54,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch"],
-                    help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady state")
+    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch", "surrogate"],
+                    help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady "
+                         "state; surrogate: learned warm start of obstacle channels vs cold start")
+    ap.add_argument("--train-cases", type=int, default=2000)
+    ap.add_argument("--held-cases", type=int, default=200)
+    ap.add_argument("--train-seconds", type=float, default=180.0)
+    ap.add_argument("--tol-train", type=float, default=1e-8)
     ap.add_argument("--plain-stride", type=int, default=16, help="batch: every n-th channel runs the plain solver")
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--K", type=int, default=1000)
@@ -455,6 +460,98 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def obstacle_cases(seed, n, nx=256, ny=128):
+    """n seeded obstacle channels (per-case seeds drawn from one stream)."""
+    rng = W.SplitMix64(seed)
+    return [W.obstacle_channel(int(rng.next_u64(1)[0] & 0x7FFFFFFFFFFF), nx=nx, ny=ny) for _ in range(n)]
+
+
+def run_surrogate(args, ws, rank, local):
+    """256 x 128 channels with 1-4 seeded circular obstacles: 2000 steady
+    fields from the batched solver train the U-Net; on 200 held-out cases the
+    predicted (rho, u) start runs to r_K <= tol, against cold starts of the
+    same cases (both batched), and a plain sequential cold solver on every
+    10th held-out case (scaled to all)."""
+    import torch
+
+    import paper_2212_07494_gb300 as P
+    import paper_2212_07494_gb300.surrogate as S
+
+    torch.cuda.set_device(local)
+    H, Wd = 128, 256
+    tol, K, max_steps = args.tol, args.K, 5_000_000
+    train = obstacle_cases(2212074942, args.train_cases)
+    held = obstacle_cases(2212074943, args.held_cases)
+    t0 = time.perf_counter()
+    secs_d, steps_d, st_d, r_d, b = S.solve(train, args.tol_train, K, max_steps)
+    ok = np.where(st_d == 0)[0]
+    X = np.stack([S.features(train[k][0], train[k][1], train[k][2]) for k in ok])
+    Y = np.stack([S.targets(*b.moments(int(k)), train[k][1], train[k][2]) for k in ok])
+    M = np.stack([1.0 - train[k][0][0] for k in ok]).astype(np.float32)
+    b.close()
+    t_data = time.perf_counter() - t0
+    sur = S.Surrogate(H, Wd, batch=8)
+    losses, t_train, nsteps = sur.train(X, Y, M, epochs=1000, lr=1e-3, seconds=args.train_seconds)
+    flops = S.train_flops_per_sample(H, Wd) * 8 * nsteps
+    # held-out: cold (batched), warm (batched, inference included)
+    secs_c, steps_c, st_c, r_c, bc = S.solve(held, tol, K, max_steps)
+    cold = S.final_fields(bc, len(held))
+    bc.close()
+    Xh = np.stack([S.features(s, t2, g) for s, t2, g in held])
+    Yh = sur.predict(Xh)
+    pred_err = [float(np.linalg.norm(S.fields(Yh[k], *held[k])[1] - cold[k][1]) / np.linalg.norm(cold[k][1]))
+                for k in range(len(held))]
+    secs_w, steps_w, st_w, warm, t_inf, fallbacks = S.warm_start(sur, held, tol, K, max_steps)
+    diff = [float(np.linalg.norm(warm[k][1] - cold[k][1]) / np.linalg.norm(cold[k][1])) for k in range(len(held))]
+    # plain sequential cold start on a subset
+    t_plain, n_plain = 0.0, 0
+    for k in range(0, len(held), 10):
+        s_, t2, g = held[k]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat = P.Lattice("D2Q9", "SMRT", (Wd, H, 1), (1, 1, t2, 1, 1), "F32", (1, 0, 1), g=[g, 0.0], solid=s_)
+        n = 0
+        while n < max_steps:
+            n += K
+            if lat.residual(K) <= tol:
+                break
+        lat.close()
+        t_plain += time.perf_counter() - t1
+        n_plain += 1
+    t_plain_est = t_plain * len(held) / max(1, n_plain)
+    sur.close()
+    peak_tf = 1698.0
+    try:
+        peak_tf = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"])
+    except Exception:
+        pass
+    line = {"metric": "wall time to steady state, surrogate warm start vs cold start at equal error",
+            "value": secs_w, "unit": "s", "n_gpus": 1, "steps": int(np.max(steps_w)), "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (solver), bf16 (network)",
+            "data": "synthetic",
+            "config": {"workload": "obstacle_channels_d2q9_smrt_f32_256x128_unet_bf16", "H": H, "W": Wd,
+                       "train_cases": int(len(ok)), "held_out": len(held), "tol": tol, "tol_train": args.tol_train,
+                       "K": K, "seeds": [2212074942, 2212074943], "unet": "4 levels, widths 32/64/128/256"},
+            "cold": {"seconds": secs_c, "steps_mean": float(np.mean(steps_c)), "converged": int((st_c == 0).sum())},
+            "warm": {"seconds_incl_inference": secs_w, "inference_seconds": t_inf,
+                     "steps_mean": float(np.mean(steps_w)), "converged": int((st_w == 0).sum()),
+                     "fallbacks_to_cold": int(fallbacks)},
+            "speedup_vs_cold_batched": secs_c / secs_w,
+            "plain_cold": {"seconds_extrapolated": t_plain_est, "cases_measured": n_plain,
+                           "how": "every 10th held-out case alone (lbm_create, lbm_residual every K), time scaled"},
+            "speedup_vs_plain_cold": t_plain_est / secs_w,
+            "steps_saved_frac_mean": float(1.0 - np.mean(steps_w) / np.mean(steps_c)),
+            "steps_saved_frac_median_per_case": float(np.median(1.0 - steps_w / steps_c)),
+            "equal_error": {"rel_l2_warm_vs_cold_median": float(np.median(diff)), "rel_l2_warm_vs_cold_max": max(diff),
+                            "prediction_rel_l2_u_median": float(np.median(pred_err))},
+            "training": {"data_seconds": t_data, "train_seconds": t_train, "steps": nsteps, "batch": 8,
+                         "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "epochs": len(losses),
+                         "tflops": flops / t_train / 1e12, "frac_of_bf16_sustained": flops / t_train / 1e12 / peak_tf,
+                         "flops_per_sample": S.train_flops_per_sample(H, Wd)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -464,6 +561,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batch":
         run_batch(args, ws, rank, local)
+    elif args.workload == "surrogate":
+        run_surrogate(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
 
