@@ -54,9 +54,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch", "surrogate"],
+    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch", "surrogate", "precision"],
                     help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady "
-                         "state; surrogate: learned warm start of obstacle channels vs cold start")
+                         "state; surrogate: learned warm start of obstacle channels vs cold start; "
+                         "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
+    ap.add_argument("--tgv-n", type=int, default=256)
+    ap.add_argument("--tgv-steps", type=int, default=5000)
+    ap.add_argument("--kol-steps", type=int, default=10000)
     ap.add_argument("--train-cases", type=int, default=2000)
     ap.add_argument("--held-cases", type=int, default=200)
     ap.add_argument("--train-seconds", type=float, default=180.0)
@@ -552,6 +556,64 @@ def run_surrogate(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_precision(args, ws, rank, local):
+    """Storage precision: the 4096^2 Kolmogorov flow (D2Q9 SMRT, 10000 steps)
+    and the 256^3 Taylor-Green vortex (D3Q27 SMRT, Re 1600, 5000 steps) in
+    FP64, FP32, FP16 and BF16 storage.  Errors are relative L2 of u against
+    the FP64 run (the GPU FP64 path, which matches the FP64 oracle to 1e-12 in
+    the parity tests; the oracle itself cannot run these sizes)."""
+    import torch
+
+    import paper_2212_07494_gb300 as P
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=local)
+    peak, _ = measured_peaks()
+
+    def run(label, make, steps):
+        out, ref = {}, None
+        for st in ["F64", "F32", "F16", "BF16"]:
+            lat = make(st)
+            with torch.cuda.stream(stream):
+                bx, npt, _ = lat.autotune(5)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lat.step(steps)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            D, Q, _, bpn = lat.info()
+            rho, u, tot = lat.moments()
+            N = rho.size
+            rec = {"mlups": N / ms / 1e3, "gbs": N * bpn / ms / 1e6, "hbm_frac": N * bpn / ms / 1e6 / peak,
+                   "ms_per_step": ms, "launch": [bx, npt], "finite": bool(np.all(np.isfinite(u)))}
+            if ref is None:
+                ref = u
+            else:
+                rec["rel_l2_u_vs_f64"] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+            out[st] = rec
+            lat.close()
+        return out
+
+    wl = W.kolmogorov(n=args.n, steps=args.kol_steps)
+    kol = run("kolmogorov", lambda st: P.Lattice("D2Q9", "SMRT", wl.shape, wl.tau, st, wl.periodic, g=wl.g,
+                                                 force_kind="rows", u0=wl.u0, torch_stream=stream), wl.steps)
+    del wl
+    tg = W.taylor_green_3d(n=args.tgv_n, steps=args.tgv_steps)
+    tgv = run("tgv", lambda st: P.Lattice("D3Q27", "SMRT", tg.shape, tg.tau, st, tg.periodic, g=tg.g,
+                                          rho0=tg.rho0, u0=tg.u0, torch_stream=stream), tg.steps)
+    line = {"metric": "MLUPS and % of HBM roofline per lattice, with velocity error vs FP64 per storage mode",
+            "value": tgv["F16"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.tgv_steps, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 arithmetic",
+            "data": "synthetic",
+            "config": {"workload": "precision_modes", "kolmogorov": {"n": args.n, "steps": args.kol_steps},
+                       "tgv3d": {"n": args.tgv_n, "steps": args.tgv_steps, "Re": 1600, "U0": 0.05,
+                                 "tau2": tg.tau[2], "lattice": "D3Q27"}},
+            "kolmogorov_d2q9_smrt": kol, "tgv_d3q27_smrt": tgv, "peak_gbs": peak}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -563,6 +625,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "surrogate":
         run_surrogate(args, ws, rank, local)
+    elif args.workload == "precision":
+        run_precision(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
 

@@ -1,0 +1,88 @@
+"""Reduced-precision storage (FP32 / FP16 / BF16 deviations f_i - w_i, FP32
+arithmetic) against the FP64 oracle over many steps.
+
+Tolerance (derived from the arithmetic), two terms:
+- storage: each step rounds every stored deviation to nearest with unit
+  roundoff eps_s (FP32 2^-24, FP16 2^-11, BF16 2^-8); the velocity is a fixed
+  linear combination of the deviations, so one step perturbs it by a
+  relative amount of order eps_s.  Over short runs these perturbations are
+  uncorrelated and viscous damping does not amplify them, so they add up
+  like a random walk, C sqrt(N) eps_s;
+- arithmetic: every reduced mode collides in FP32 (unit roundoff
+  eps_a = 2^-24).  The moment sums, the Hermite projection and the
+  reconstruction round nearly the same numbers the same way on every step,
+  so that error has a consistent sign and grows linearly, C N eps_a.  The
+  4096^2 Kolmogorov flow in FP32 storage shows it: 7.1e-6 after 200 steps,
+  3.6e-4 after 10000 (x50 for x50 steps).
+The bound is C (sqrt(N) eps_s + N eps_a) with C = 4.  Long runs in FP16 or
+BF16 storage leave the random-walk regime once the per-step change of a
+deviation falls below half an ulp of it (the change is lost, the error grows
+linearly); the bench's precision workload reports those errors at full
+size rather than bounding them here.  The one-step comparisons with the
+oracle's storage-rounding emulation live in test_gpu_parity.py."""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+import oracle as O
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+EPS = {"F32": 2.0 ** -24, "F16": 2.0 ** -11, "BF16": 2.0 ** -8}
+EPS_ARITH = 2.0 ** -24
+
+
+def bound(storage, steps):
+    return 4.0 * (math.sqrt(steps) * EPS[storage] + steps * EPS_ARITH)
+
+
+@pytest.fixture(scope="module")
+def kolmogorov_crop():
+    """The 512 x 512 crop of the Kolmogorov workload (periodic, g_x(y) rows,
+    seeded noise), 200 steps of the FP64 oracle."""
+    O.set_threads(0)
+    wl = W.kolmogorov(n=512, steps=200)
+    orc = O.Sim(O.D2Q9, O.SMRT, wl.shape, wl.periodic, wl.tau, g=wl.g, force_kind="rows", u0=wl.u0)
+    orc.step(wl.steps)
+    return wl, orc.moments()[1]
+
+
+@pytest.mark.parametrize("storage", ["F32", "F16", "BF16"])
+def test_kolmogorov_crop_error(storage, kolmogorov_crop):
+    import paper_2212_07494_gb300 as P
+    wl, u_ref = kolmogorov_crop
+    lat = P.Lattice("D2Q9", "SMRT", wl.shape, wl.tau, storage, wl.periodic, g=wl.g, force_kind="rows", u0=wl.u0)
+    lat.step(wl.steps)
+    u = lat.moments()[1]
+    err = rel_l2(u, u_ref)
+    b = bound(storage, wl.steps)
+    print(f"Kolmogorov 512^2, {wl.steps} steps, {storage}: rel L2(u) = {err:.3e} (bound {b:.2e})")
+    assert err < b
+    lat.close()
+
+
+@pytest.fixture(scope="module")
+def tgv_small():
+    """Taylor-Green vortex (U0 = 0.05) on 16^3 with Re = 100 on the length
+    N / 2 pi plus g_x = 1e-6, D3Q27 SMRT, 60 steps of the FP64 oracle."""
+    wl = W.taylor_green_3d(n=16, Re=100.0, steps=60)
+    orc = O.Sim(O.D3Q27, O.SMRT, wl.shape, wl.periodic, wl.tau, g=wl.g, rho0=wl.rho0, u0=wl.u0)
+    orc.step(wl.steps)
+    return wl, orc.moments()[1]
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32", "F16", "BF16"])
+def test_tgv_error(storage, tgv_small):
+    import paper_2212_07494_gb300 as P
+    wl, u_ref = tgv_small
+    lat = P.Lattice("D3Q27", "SMRT", wl.shape, wl.tau, storage, wl.periodic, g=wl.g, rho0=wl.rho0, u0=wl.u0)
+    lat.step(wl.steps)
+    u = lat.moments()[1]
+    err = rel_l2(u, u_ref)
+    b = 1e-12 if storage == "F64" else bound(storage, wl.steps)
+    print(f"TGV 16^3, {wl.steps} steps, {storage}: rel L2(u) = {err:.3e} (bound {b:.2e})")
+    assert err < b
+    lat.close()
