@@ -13,9 +13,9 @@ namespace lbm {
 // {sum (rho - 1), Px, Py, Pz, residual numerator, residual denominator,
 //  non-finite count, fluid-node count}
 constexpr int kPartials = 8;
-constexpr int kMomBlock = 256;
-constexpr int kMomNpt = 4;          // nodes per thread per work item
-constexpr int kMomGridMax = 608;    // 4 blocks per SM on 152 SMs: one wave
+constexpr int kMomBlock = 128;
+constexpr int kMomNpt = 2;          // nodes per thread per work item
+constexpr int kMomGridMax = 1216;   // 8 blocks per SM on 152 SMs: one wave
 
 struct StepCfg {
     int bdx;  // threads per block along x

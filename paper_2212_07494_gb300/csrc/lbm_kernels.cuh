@@ -67,15 +67,38 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
+// Running sum of per-thread values in the arithmetic type.  FP32 uses a
+// compensated pair (Knuth's TwoSum: the rounding error of every addition is
+// kept in lo), which carries the sum to about twice FP32's precision without
+// FP64 instructions per work item (GB300's FP64 pipe is narrow); FP64 sums
+// plainly.  Plain additions and subtractions only, so contraction cannot
+// change the result.
+template <typename R> struct Acc {
+    R s = R(0);
+    __device__ __forceinline__ void add(R x) { s += x; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bp = s - hi;
+        lo += (hi - (s - bp)) + (x - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Macroscopic fields of the current state (Eq. half_F) and the FP64 check.
 // A fixed grid walks the work items (row segments of kMomBlock * kMomNpt
 // nodes; grid-stride, so the partial sums and their order do not depend on
 // how the hardware schedules blocks); each thread takes kMomNpt nodes of a
 // segment and issues all their loads before any arithmetic.  Per-node
-// arithmetic runs in the storage's arithmetic type, which also sums the
-// kMomNpt nodes of a work item; the accumulation over the domain is FP64 and
-// the node counts are integers.  Partials per block: {sum (rho - 1), sum rho u_x, sum rho u_y,
-// sum rho u_z, sum |u - uprev|^2, sum |u|^2, non-finite count, fluid count}.
+// arithmetic runs in the storage's arithmetic type; each thread keeps its
+// running sums in Acc of that type and converts them to FP64 once, for the
+// FP64 block and grid reductions; node counts are integers.  Partials per
+// block: {sum (rho - 1), sum rho u_x, sum rho u_y, sum rho u_z,
+// sum |u - uprev|^2, sum |u|^2, non-finite count, fluid count}.
 // rho/u outputs (unpadded FP64) and uprev (unpadded, arithmetic type; read
 // for the residual, then overwritten with u) are optional.
 template <int L, int ST, bool MASK>
@@ -92,10 +115,8 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
     const int segs = (p.nx + SEG - 1) / SEG;
     const unsigned rows = (unsigned)p.ny * (unsigned)p.nz;
     const long long N = (long long)p.nx * p.ny * p.nz;
-    double v[kPartials];
-#pragma unroll
-    for (int k = 0; k < kPartials; ++k) v[k] = 0.0;
-    long long fluid = 0, nonfinite = 0;
+    Acc<R> a_drho, a_j[3], a_dd, a_uu;
+    int fluid = 0, nonfinite = 0;
     unsigned row = blockIdx.x / segs;
     int seg = blockIdx.x % segs;
     const unsigned drow = gridDim.x / segs;
@@ -130,9 +151,8 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
         R g3[3];
         const bool per_node_force = p.force_kind == G_FIELD;
         if (!per_node_force) load_force<L>(p, y, 0, g3[0], g3[1], g3[2]);
-        // the kMomNpt nodes of this work item are summed in the arithmetic
-        // type (each node's value is of that type), then added to the FP64
-        // accumulators once per work item
+        // the kMomNpt nodes of this work item are summed plainly, then added
+        // to the running sums once per work item
         R sdrho = R(0), sj[3] = {R(0), R(0), R(0)}, sdd = R(0), suu = R(0);
 #pragma unroll
         for (int k = 0; k < kMomNpt; ++k) {
@@ -178,12 +198,19 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
 #pragma unroll
                 for (int a = 0; a < D; ++a) u_out[a * N + n] = (double)u[a];
         }
-        v[0] += (double)sdrho;
+        a_drho.add(sdrho);
 #pragma unroll
-        for (int a = 0; a < D; ++a) v[1 + a] += (double)sj[a];
-        v[4] += (double)sdd;
-        v[5] += (double)suu;
+        for (int a = 0; a < D; ++a) a_j[a].add(sj[a]);
+        a_dd.add(sdd);
+        a_uu.add(suu);
     }
+    double v[kPartials];
+    v[0] = a_drho.value();
+    v[1] = a_j[0].value();
+    v[2] = a_j[1].value();
+    v[3] = D == 3 ? a_j[2].value() : 0.0;
+    v[4] = a_dd.value();
+    v[5] = a_uu.value();
     v[6] = (double)nonfinite;
     v[7] = (double)fluid;
     block_sum(v);
