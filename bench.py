@@ -78,6 +78,22 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Max of x over the ranks (x itself with no process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs the same workload)."""
+    return ws * units_per_rank / seconds
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2212_07494_gb300", "csrc")
@@ -305,17 +321,14 @@ def run_gpu(args, ws, rank, local):
     sampler.stop()
     total_ms = e0.elapsed_time(e1)
     kern_ms = sum(ev_s[c].elapsed_time(ev_e[c]) for c in range(chunks)) / steps
-    t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = reduce_max(total_ms, dist, f"cuda:{local}")
     ck = checks.cpu().numpy()
     finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
     res = float(math.sqrt(ck[-1, 4]) / (C * math.sqrt(ck[-1, 5]))) if chunks > 1 and ck[-1, 5] > 0 else None
     mass_drift = float(abs(ck[-1, 0] - ck[0, 0]) / ck[0, 0])
     lat.close()
 
-    value = ws * N * steps / (total_ms * 1e-3) / 1e6
+    value = job_rate(ws, N * steps, total_ms * 1e-3) / 1e6
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_node * N
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
@@ -372,13 +385,10 @@ def run_e2e(P, torch, wl, n, steps, C, local, ws, dist):
     P.lbm_moments(lat.h, rho.numpy(), u.numpy(), tot)
     dt = time.perf_counter() - t0
     lat.close()
-    tt = torch.tensor([dt], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    dt = float(tt.item())
+    dt = reduce_max(dt, dist, f"cuda:{local}")
     h2d = u0.numel() * 8 + g.numel() * 8
     d2h = (rho.numel() + u.numel()) * 8 + (steps // C) * 7 * 8
-    return {"value": ws * N * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+    return {"value": job_rate(ws, N * steps, dt) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps, "residual_last": r,
             "what": "lbm_create from host u0/g, lbm_residual every check interval, lbm_moments to host"}
 

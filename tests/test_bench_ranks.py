@@ -1,0 +1,67 @@
+"""bench.py's multi-rank aggregation on CPU: two gloo ranks (the GPU runs use
+NCCL with the same calls).  Every rank runs the whole workload (weak
+scaling); the job's time is the slowest rank's and its throughput is the
+units of all ranks over that time."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, times, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    t = bench.reduce_max(times[rank], dist, "cpu")
+    v = bench.job_rate(ws, 1000.0, t)
+    dist.barrier()
+    out.put((rank, t, v))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("times", [(2.0, 3.0), (5.0, 1.0)])
+def test_two_ranks_take_the_slowest_time(times):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, v in res:
+        assert t == max(times)
+        assert v == pytest.approx(2 * 1000.0 / max(times))
+
+
+def test_single_rank_passthrough():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(1.5, None, "cpu") == 1.5
+    assert bench.job_rate(1, 10.0, 2.0) == 5.0
+
+
+def test_reference_arm_prints_on_rank_zero_only(capsys):
+    """Ranks other than 0 of the reference arm exit without work."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        n, steps, warmup = 64, 1, 0
+
+    bench.run_reference(A(), 2, 1)
+    assert capsys.readouterr().out == ""
