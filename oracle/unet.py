@@ -7,7 +7,10 @@ two 3x3 convolutions (zero padding 1, bias) each followed by ReLU; 2x2 average
 pooling going down; nearest-neighbour 2x upsampling followed by a 3x3
 conv + ReLU going up; concatenation [up path, skip] before the two decoder
 convolutions; a linear 3x3 head with 3 outputs.  Loss: weighted mean squared
-error sum(m (y - t)^2) / (3 sum m) with per-pixel weights m.
+error sum(m (y - t)^2) / (3 sum m) with per-pixel weights m.  The input has
+cin channels (3 by default).  Every convolution pads with zeros along y (the
+height); along x (the width) it pads with zeros, or, with periodic_x, wraps
+around, which is the padding of a channel periodic in x.
 
 Tensors are NHWC float64.  Parameters use the canonical flat layout shared
 with the CUDA library: for each layer in LAYERS order, W[co][ky][kx][ci]
@@ -21,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 BASE = 32
-# (name, input channels, output channels, relu)
+# (name, input channels, output channels, relu) for a 3-channel input
 LAYERS = [
     ("enc1a", 3, 32, True), ("enc1b", 32, 32, True),
     ("enc2a", 32, 64, True), ("enc2b", 64, 64, True),
@@ -34,17 +37,22 @@ LAYERS = [
 ]
 
 
-def layer_slices():
+def layers(cin=3):
+    """LAYERS with cin input channels in the first layer."""
+    return [(LAYERS[0][0], cin) + LAYERS[0][2:]] + LAYERS[1:]
+
+
+def layer_slices(cin=3):
     """(name, cin, cout, relu, w_offset, b_offset) for each layer, and the total."""
     out, off = [], 0
-    for name, ci, co, relu in LAYERS:
+    for name, ci, co, relu in layers(cin):
         out.append((name, ci, co, relu, off, off + 9 * ci * co))
         off += 9 * ci * co + co
     return out, off
 
 
-def unpack(params):
-    sl, total = layer_slices()
+def unpack(params, cin=3):
+    sl, total = layer_slices(cin)
     assert params.size == total
     P = {}
     for name, ci, co, relu, wo, bo in sl:
@@ -52,8 +60,8 @@ def unpack(params):
     return P
 
 
-def pack(P):
-    sl, total = layer_slices()
+def pack(P, cin=3):
+    sl, total = layer_slices(cin)
     out = np.zeros(total)
     for name, ci, co, relu, wo, bo in sl:
         W, b = P[name]
@@ -62,27 +70,40 @@ def pack(P):
     return out
 
 
-def _cols(x):
-    """im2col of a 3x3, pad-1 convolution: (N, H, W, 9, C), tap index ky*3+kx."""
+def _pad(x, periodic_x):
+    """One halo cell on each side: zeros along y; along x zeros, or the
+    opposite edge's column when periodic_x."""
     N, H, W, C = x.shape
     xp = np.zeros((N, H + 2, W + 2, C))
     xp[:, 1:-1, 1:-1] = x
+    if periodic_x:
+        xp[:, 1:-1, 0] = x[:, :, W - 1]
+        xp[:, 1:-1, W + 1] = x[:, :, 0]
+    return xp
+
+
+def _cols(x, periodic_x=False):
+    """im2col of a 3x3, pad-1 convolution: (N, H, W, 9, C), tap index ky*3+kx."""
+    N, H, W, C = x.shape
+    xp = _pad(x, periodic_x)
     return np.stack([xp[:, ky:ky + H, kx:kx + W] for ky in range(3) for kx in range(3)], axis=3)
 
 
-def conv(x, W, b):
-    """y[n,i,j,o] = b[o] + sum_{ky,kx,c} W[o,ky,kx,c] x[n, i+ky-1, j+kx-1, c]."""
+def conv(x, W, b, periodic_x=False):
+    """y[n,i,j,o] = b[o] + sum_{ky,kx,c} W[o,ky,kx,c] x[n, i+ky-1, j+kx-1, c]
+    (x[n, i', j', c] = 0 outside the grid along y; along x too, or taken at
+    j' mod W when periodic_x)."""
     N, H, Wd, C = x.shape
     co = W.shape[0]
-    cols = _cols(x).reshape(N * H * Wd, 9 * C)
+    cols = _cols(x, periodic_x).reshape(N * H * Wd, 9 * C)
     return (cols @ W.reshape(co, 9 * C).T + b).reshape(N, H, Wd, co)
 
 
-def conv_backward(x, W, dy):
+def conv_backward(x, W, dy, periodic_x=False):
     """Gradients of conv: (dx, dW, db)."""
     N, H, Wd, C = x.shape
     co = W.shape[0]
-    cols = _cols(x).reshape(N * H * Wd, 9 * C)
+    cols = _cols(x, periodic_x).reshape(N * H * Wd, 9 * C)
     g = dy.reshape(N * H * Wd, co)
     dW = (g.T @ cols).reshape(co, 3, 3, C)
     db = g.sum(axis=0)
@@ -91,7 +112,13 @@ def conv_backward(x, W, dy):
     for ky in range(3):
         for kx in range(3):
             dxp[:, ky:ky + H, kx:kx + Wd] += dcols[:, :, :, ky, kx]
-    return dxp[:, 1:-1, 1:-1], dW, db
+    dx = dxp[:, 1:-1, 1:-1].copy()
+    if periodic_x:
+        # the halo columns are copies of the opposite edge: their gradient
+        # belongs there
+        dx[:, :, Wd - 1] += dxp[:, 1:-1, 0]
+        dx[:, :, 0] += dxp[:, 1:-1, Wd + 1]
+    return dx, dW, db
 
 
 def pool(x):
@@ -125,18 +152,19 @@ def bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(params, x, storage="fp64"):
+def forward(params, x, storage="fp64", periodic_x=False):
     """Returns (y, cache).  storage="bf16" rounds the weights, the input and
     every stored activation to bfloat16 where the GPU stores them (the
-    arithmetic stays FP64; biases and the head's output are not rounded)."""
-    P = unpack(params)
+    arithmetic stays FP64; biases and the head's output are not rounded).
+    The input's last axis gives cin."""
+    P = unpack(params, x.shape[-1])
     cache = {}
     rnd = bf16 if storage == "bf16" else (lambda a: a)
     relu_of = dict((l[0], l[3]) for l in LAYERS)
 
     def layer(name, inp):
         W, b = P[name]
-        z = conv(inp, rnd(W), b)
+        z = conv(inp, rnd(W), b, periodic_x)
         cache[name] = (inp, z)
         return rnd(relu(z)) if relu_of[name] else z
 
@@ -161,11 +189,12 @@ def loss(y, t, m):
     return float((m[..., None] * (y - t) ** 2).sum() / (3.0 * m.sum()))
 
 
-def backward(params, cache, y, t, m, storage="fp64"):
+def backward(params, cache, y, t, m, storage="fp64", periodic_x=False):
     """Gradient of loss(forward(params, x), t, m) with respect to params (the
     exact derivative of the forward pass; with storage="bf16" the weights
     are the rounded ones the forward pass used)."""
-    P = unpack(params)
+    cin = cache["enc1a"][0].shape[-1]
+    P = unpack(params, cin)
     if storage == "bf16":
         P = {k: (bf16(W), b) for k, (W, b) in P.items()}
     relu_of = dict((l[0], l[3]) for l in LAYERS)
@@ -175,7 +204,7 @@ def backward(params, cache, y, t, m, storage="fp64"):
     def back(name, dout):
         inp, z = cache[name]
         dz = dout * (z > 0) if relu_of[name] else dout
-        dx, dW, db = conv_backward(inp, P[name][0], dz)
+        dx, dW, db = conv_backward(inp, P[name][0], dz, periodic_x)
         grads[name] = (dW, db)
         return dx
 
@@ -195,15 +224,15 @@ def backward(params, cache, y, t, m, storage="fp64"):
     dp1 = back("enc2a", back("enc2b", de2))
     de1 = de1 + pool_backward(dp1)
     back("enc1a", back("enc1b", de1))
-    return pack(grads)
+    return pack(grads, cin)
 
 
-def init_params(seed: int):
+def init_params(seed: int, cin=3):
     """He-normal weights (std sqrt(2 / (9 cin))), zero biases, drawn with the
     project's seeded generator (lbm_workloads.SplitMix64)."""
     import lbm_workloads as W
     rng = W.SplitMix64(seed)
-    sl, total = layer_slices()
+    sl, total = layer_slices(cin)
     out = np.zeros(total)
     for name, ci, co, relu_, wo, bo in sl:
         std = np.sqrt(2.0 / (9 * ci)) if relu_ else np.sqrt(1.0 / (9 * ci))

@@ -72,6 +72,7 @@ struct ConvArgs {
     int gc, go;
     int N, H, W, cin, cout, wrows;
     int relu;
+    int wrapx;           // 1: periodic padding along x (the width), else zero padding
 };
 
 constexpr int CBM = 128, CBN = 64, CPAD = 8;
@@ -114,7 +115,9 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
         for (int i = 0; i < AREP; ++i) {
-            const int yy = ay[i] + dy, xx = ax[i] + dx;
+            const int yy = ay[i] + dy;
+            int xx = ax[i] + dx;
+            if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
             const bool ok = an[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
             const bf16 *src = ok ? a.x + ((long long)(an[i] * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 + acc_[i] * 8 : a.x;
             cp_async16(&As[buf][arow[i]][acc_[i] * 8], src, ok);
@@ -201,6 +204,7 @@ struct WgradArgs {
     float *dw;      // [wrows][9][cin]
     int N, H, W, cin, cout;
     int pix;        // pixels per block
+    int wrapx;      // periodic padding along x
 };
 
 constexpr int WBM = 64, WBN = 32, WBK = 32, WPAD = 8;
@@ -239,7 +243,9 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
             if (ok) {
                 const int n = (int)(p / hw);
                 const int rr = (int)(p - (long long)n * hw);
-                const int yy = rr / a.W + dy, xx = rr % a.W + dx;
+                const int yy = rr / a.W + dy;
+                int xx = rr % a.W + dx;
+                if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
                 ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
                 if (ok) src = a.x + ((long long)(n * a.H + yy) * a.W + xx) * a.xc + a.xo + ci0 + cc * 8;
             }
@@ -373,12 +379,12 @@ __global__ void k_up_back(const bf16 *dy, int dyc, int dyo, const bf16 *gate, in
     dst[p * dc + dof + c] = __float2bfloat16_rn(s);
 }
 
-// inputs [p][3] FP32 -> [p][16] BF16 (channels 3..15 zero)
-__global__ void k_pack_input(const float *x, bf16 *y, long long P) {
+// inputs [p][cin] FP32 -> [p][16] BF16 (channels cin..15 zero), cin <= 16
+__global__ void k_pack_input(const float *x, int cin, bf16 *y, long long P) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) y[p * 16 + c] = __float2bfloat16_rn(c < 3 ? x[p * 3 + c] : 0.f);
+    for (int c = 0; c < 16; ++c) y[p * 16 + c] = __float2bfloat16_rn(c < cin ? x[p * cin + c] : 0.f);
 }
 
 // weighted MSE: loss += sum m (y - t)^2 * scale; dz[p][c] = 2 m (y - t) scale
@@ -458,6 +464,8 @@ enum { E1A, E1B, E2A, E2B, E3A, E3B, BA, BB, U3, D3A, D3B, U2, D2A, D2B, U1, D1A
 
 struct lbm_unet {
     int H = 0, W = 0, B = 0;
+    int cin = 3;        // input channels of the first layer
+    int wrapx = 0;      // periodic padding along x in every convolution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Layer L[kL];
@@ -523,6 +531,7 @@ lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H
     a.gate = gate;
     a.gc = gc;
     a.go = go;
+    a.wrapx = u->wrapx;
     if (forward) {
         a.w = l.w;
         a.bias = u->p + l.boff;
@@ -562,6 +571,7 @@ lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, in
     a.W = W;
     a.cin = l.cinp;
     a.cout = l.coutp;
+    a.wrapx = u->wrapx;
     const long long P = (long long)n * H * W;
     a.pix = 2048;
     dim3 grid(nblk(P, a.pix), nblk(l.coutp, WBM), 9 * ((l.cinp + WBN - 1) / WBN));
@@ -587,7 +597,7 @@ lbm_status forward(lbm_unet *u, const float *xin, int n) {
     const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4, H8 = H / 8, W8 = W / 8;
     lbm_status st;
     const long long P = (long long)n * H * W;
-    k_pack_input<<<nblk(P, 256), 256, 0, u->stream>>>(xin, u->x0, P);
+    k_pack_input<<<nblk(P, 256), 256, 0, u->stream>>>(xin, u->cin, u->x0, P);
     U_CUDA(u, cudaGetLastError());
 #define FW(li, x, xc, xo, h, w, y, yc, yo) \
     if ((st = conv(u, li, x, xc, xo, n, h, w, y, yc, yo, true)) != LBM_OK) return st;
@@ -704,15 +714,19 @@ void lbm_unet_destroy(lbm_unet *u) {
     delete u;
 }
 
-lbm_status lbm_unet_create(int H, int W, int max_batch, void *stream, lbm_unet **out) {
+lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch, void *stream, lbm_unet **out) {
     if (!out) return ufail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (H < 8 || W < 8 || H % 8 || W % 8 || max_batch < 1)
         return ufail(nullptr, LBM_ERR_ARG, "H and W must be multiples of 8 (>= 8), max_batch >= 1");
+    if (cin < 1 || cin > 16) return ufail(nullptr, LBM_ERR_ARG, "cin must be in [1, 16]");
+    if (periodic_x != 0 && periodic_x != 1) return ufail(nullptr, LBM_ERR_ARG, "periodic_x must be 0 or 1");
     lbm_unet *u = new lbm_unet();
     u->H = H;
     u->W = W;
     u->B = max_batch;
+    u->cin = cin;
+    u->wrapx = periodic_x;
     if (stream) {
         u->stream = (cudaStream_t)stream;
     } else {
@@ -726,7 +740,7 @@ lbm_status lbm_unet_create(int H, int W, int max_batch, void *stream, lbm_unet *
     for (int i = 0; i < kL; ++i) {
         Layer &l = u->L[i];
         l.name = kArch[i].name;
-        l.cin = kArch[i].cin;
+        l.cin = i == E1A ? cin : kArch[i].cin;
         l.cout = kArch[i].cout;
         l.relu = kArch[i].relu;
         l.cinp = l.cin < 16 ? 16 : l.cin;

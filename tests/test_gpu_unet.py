@@ -15,14 +15,14 @@ from oracle import unet as U
 pytestmark = pytest.mark.gpu
 
 
-def _problem(H, W, n, seed):
+def _problem(H, W, n, seed, cin=3):
     rng = np.random.default_rng(seed)
-    params = U.init_params(seed)
-    sl, total = U.layer_slices()
+    params = U.init_params(seed, cin)
+    sl, total = U.layer_slices(cin)
     for name, ci, co, relu, wo, bo in sl:
         params[bo:bo + co] = 0.05 * rng.normal(size=co)
     params = params.astype(np.float32).astype(np.float64)  # what the GPU holds
-    x = rng.normal(size=(n, H, W, 3))
+    x = rng.normal(size=(n, H, W, cin))
     t = rng.normal(size=(n, H, W, 3))
     m = (rng.uniform(size=(n, H, W)) > 0.2).astype(np.float64)
     return params, x, t, m
@@ -33,46 +33,49 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
 
-@pytest.mark.parametrize("H,W,n", [(24, 40, 2), (64, 128, 1)])
-def test_forward_matches_oracle(H, W, n):
+@pytest.mark.parametrize("H,W,n,cin,periodic_x", [(24, 40, 2, 3, False), (64, 128, 1, 3, False),
+                                                  (24, 40, 2, 5, True), (32, 64, 1, 16, True)])
+def test_forward_matches_oracle(H, W, n, cin, periodic_x):
     import torch
     import paper_2212_07494_gb300 as P
-    params, x, t, m = _problem(H, W, n, 1)
-    net = P.UNet(H, W, n)
+    params, x, t, m = _problem(H, W, n, 1, cin)
+    net = P.UNet(H, W, n, cin=cin, periodic_x=periodic_x)
     net.set_params(params)
     xd = _dev(x)
     yd = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
     net.forward(xd.data_ptr(), yd.data_ptr(), n)
     torch.cuda.synchronize()
     y = yd.cpu().numpy().astype(np.float64)
-    yb, _ = U.forward(params, x, storage="bf16")
-    yr, _ = U.forward(params, x)
+    yb, _ = U.forward(params, x, storage="bf16", periodic_x=periodic_x)
+    yr, _ = U.forward(params, x, periodic_x=periodic_x)
     rel_b = np.linalg.norm(y - yb) / np.linalg.norm(yb)
     rel_64 = np.linalg.norm(y - yr) / np.linalg.norm(yr)
-    print(f"forward {H}x{W}: rel L2 vs BF16-storage reference {rel_b:.2e}, vs FP64 {rel_64:.2e}")
+    print(f"forward {H}x{W} cin {cin} periodic {periodic_x}: rel L2 vs BF16-storage reference {rel_b:.2e}, "
+          f"vs FP64 {rel_64:.2e}")
     assert rel_b < 1e-2, (rel_b, rel_64)
     assert rel_64 < 0.15, rel_64
     net.close()
 
 
-def test_gradient_matches_oracle():
+@pytest.mark.parametrize("cin,periodic_x", [(3, False), (5, True)])
+def test_gradient_matches_oracle(cin, periodic_x):
     import torch
     import paper_2212_07494_gb300 as P
     H, W, n = 24, 40, 2
-    params, x, t, m = _problem(H, W, n, 2)
-    net = P.UNet(H, W, n)
+    params, x, t, m = _problem(H, W, n, 2, cin)
+    net = P.UNet(H, W, n, cin=cin, periodic_x=periodic_x)
     net.set_params(params)
     scale = 1.0 / (3.0 * m.sum())
     xd, td, md = _dev(x), _dev(t), _dev(m)   # keep the tensors alive while the kernels use them
     loss, g = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), n, scale)
     torch.cuda.synchronize()
-    yr, cache = U.forward(params, x, storage="bf16")
+    yr, cache = U.forward(params, x, storage="bf16", periodic_x=periodic_x)
     lr_ = U.loss(yr, t, m)
-    gr = U.backward(params, cache, yr, t, m, storage="bf16")
+    gr = U.backward(params, cache, yr, t, m, storage="bf16", periodic_x=periodic_x)
     g = g.astype(np.float64)
     cos = g @ gr / (np.linalg.norm(g) * np.linalg.norm(gr))
     rel = np.linalg.norm(g - gr) / np.linalg.norm(gr)
-    sl, total = U.layer_slices()
+    sl, total = U.layer_slices(cin)
     per = {name: np.linalg.norm(g[wo:bo + co] - gr[wo:bo + co]) / np.linalg.norm(gr[wo:bo + co])
            for name, ci, co, relu, wo, bo in sl}
     print(f"loss {loss:.6g} vs {lr_:.6g}; grad cos {cos:.5f} rel {rel:.2e}; worst layer "
