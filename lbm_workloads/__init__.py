@@ -194,12 +194,16 @@ def batch_channels(n=512, seed=2212074941, nx=(32, 512), ny=(16, 256), tau2=(0.5
 
 
 def obstacle_channel(seed: int, nx=256, ny=128, tau2=(0.55, 1.2), gx=(1e-7, 1e-5),
-                     radius=(6.0, 20.0), ncirc=(1, 4), clearance=2.0, umax=0.1):
+                     radius=(6.0, 20.0), ncirc=(1, 4), clearance=2.0, umax=0.1, re_max=60.0):
     """256 x 128 channel (periodic x, walls in y) with 1-4 circular obstacles of
     radius U[6, 20], centres uniform with >= clearance cells from the walls and
     from each other (rejection), tau_2 uniform, g_x log-uniform, redrawn while
-    the plain-channel Poiseuille peak exceeds umax.  Returns (solid (1,ny,nx)
-    uint8, tau2, gx)."""
+    the plain-channel Poiseuille peak U = g H^2 / (8 nu) exceeds umax.  Then,
+    so that the flow has a steady state (cylinder wakes shed vortices above a
+    diameter Reynolds number of about 50), g_x alone is redrawn while
+    U (2 r_max) / nu exceeds re_max (re_max=None: no such bound); U
+    overestimates the approach velocity past any obstacle.  Returns
+    (solid (1,ny,nx) uint8, tau2, gx)."""
     rng = SplitMix64(seed)
     while True:
         t2 = tau2[0] + (tau2[1] - tau2[0]) * rng.uniform(1)[0]
@@ -219,6 +223,12 @@ def obstacle_channel(seed: int, nx=256, ny=128, tau2=(0.55, 1.2), gx=(1e-7, 1e-5
         if any(math.hypot(cx - a, cy - b) < r + rb + clearance for a, b, rb in circles):
             continue
         circles.append((cx, cy, r))
+    nu = (t2 - 0.5) / 3.0
+    rmax = max((c[2] for c in circles), default=0.0)
+    while re_max is not None and g * ny * ny / (8.0 * nu) * 2.0 * rmax / nu > re_max:
+        g = math.exp(math.log(gx[0]) + (math.log(gx[1]) - math.log(gx[0])) * rng.uniform(1)[0])
+        if gx[0] * ny * ny / (8.0 * nu) * 2.0 * rmax / nu > re_max:
+            raise ValueError("no g_x in range keeps the flow below re_max")
     yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
     solid = np.zeros((ny, nx), np.uint8)
     for cx, cy, r in circles:

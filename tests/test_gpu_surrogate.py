@@ -1,7 +1,9 @@
 """The learned warm start end to end on a small problem: steady fields from
-the batched solver train the library's U-Net, and its predictions start
-held-out runs that reach the same residual tolerance in fewer steps than
-cold starts, with the same final fields."""
+the batched solver train the library's U-Net (with the mirrored channels),
+its predictions are closer to the held-out steady fields than the
+lubrication estimate they correct, and they start held-out runs that reach
+the same residual tolerance in fewer steps than cold starts, with the same
+final fields."""
 import numpy as np
 import pytest
 
@@ -28,10 +30,14 @@ def test_warm_start_saves_steps():
     secs, steps, st, r, b = S.solve(train, tol, K, 400000)
     assert np.all(st == 0)
     X = np.stack([S.features(s, t2, g) for s, t2, g in train])
-    Y = np.stack([S.targets(*b.moments(k), train[k][1], train[k][2]) for k in range(len(train))])
+    steady = [b.moments(k) for k in range(len(train))]
+    alpha = S.prior_scale(train, steady)
+    Y = np.stack([S.targets(*steady[k], train[k][1], train[k][2], train[k][0], alpha) for k in range(len(train))])
     M = np.stack([1.0 - s[0] for s, _, _ in train]).astype(np.float32)
     b.close()
-    sur = S.Surrogate(32, 64, batch=8, seed=5)
+    Xf, Yf, Mf = S.mirror(X, Y, M)
+    X, Y, M = np.concatenate([X, Xf]), np.concatenate([Y, Yf]), np.concatenate([M, Mf])
+    sur = S.Surrogate(32, 64, batch=8, seed=5, alpha=alpha)
     losses, t_train, n_steps = sur.train(X, Y, M, epochs=80, lr=1e-3)
     assert losses[-1] < 0.2 * losses[0], losses
     cold_s, cold_steps, cold_st, rc, bc = S.solve(held, tol, K, 400000)
@@ -39,14 +45,20 @@ def test_warm_start_saves_steps():
     bc.close()
     Xh = np.stack([S.features(s, t2, g) for s, t2, g in held])
     Yh = sur.predict(Xh)
-    perr = [np.linalg.norm(S.fields(Yh[k], *held[k])[1] - cold[k][1]) / np.linalg.norm(cold[k][1])
+    perr = [np.linalg.norm(S.fields(Yh[k], *held[k], alpha=alpha)[1] - cold[k][1]) / np.linalg.norm(cold[k][1])
             for k in range(len(held))]
-    rerr = [np.linalg.norm(S.fields(Yh[k], *held[k])[0] - cold[k][0]) / max(1e-30, np.linalg.norm(cold[k][0] - 1))
-            for k in range(len(held))]
+    rerr = [np.linalg.norm(S.fields(Yh[k], *held[k], alpha=alpha)[0] - cold[k][0]) /
+            max(1e-30, np.linalg.norm(cold[k][0] - 1)) for k in range(len(held))]
+    lerr = [np.linalg.norm(S.fields(np.zeros_like(Yh[k]), *held[k], alpha=alpha)[1] - cold[k][1]) /
+            np.linalg.norm(cold[k][1]) for k in range(len(held))]
     warm_s, warm_steps, warm_st, warm, t_inf, fb = S.warm_start(sur, held, tol, K, 400000)
     _, wu_steps, wu_st, wu, _, _ = S.warm_start(sur, held, tol, K, 400000, use_rho=False)
+    _, lub_steps, lub_st, _, _, _ = S.warm_start(None, held, tol, K, 400000)
     print("train losses", losses[0], losses[-1], "u pred err", np.round(perr, 3), "rho err", np.round(rerr, 3))
-    print("cold", cold_steps, "warm", warm_steps, "warm u only", wu_steps)
+    print("lubrication estimate u err", np.round(lerr, 3), "scale", alpha)
+    print("cold", cold_steps, "warm", warm_steps, "warm u only", wu_steps, "lubrication only", lub_steps)
+    # the network improves on the physics estimate it starts from
+    assert np.median(perr) < np.median(lerr), (np.median(perr), np.median(lerr))
     assert np.all(cold_st == 0) and np.all(warm_st == 0)
     # fewer steps to the same tolerance
     assert warm_steps.mean() < 0.8 * cold_steps.mean(), (warm_steps, cold_steps)
