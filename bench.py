@@ -500,11 +500,17 @@ def run_surrogate(args, ws, rank, local):
     secs_d, steps_d, st_d, r_d, b = S.solve(train, args.tol_train, K, max_steps)
     ok = np.where(st_d == 0)[0]
     X = np.stack([S.features(train[k][0], train[k][1], train[k][2]) for k in ok])
-    Y = np.stack([S.targets(*b.moments(int(k)), train[k][1], train[k][2]) for k in ok])
+    steady = [b.moments(int(k)) for k in ok]
+    alpha = S.prior_scale([train[k] for k in ok], steady)
+    Y = np.stack([S.targets(*steady[j], train[k][1], train[k][2], train[k][0], alpha) for j, k in enumerate(ok)])
+    del steady
     M = np.stack([1.0 - train[k][0][0] for k in ok]).astype(np.float32)
     b.close()
+    Xf, Yf, Mf = S.mirror(X, Y, M)
+    X, Y, M = np.concatenate([X, Xf]), np.concatenate([Y, Yf]), np.concatenate([M, Mf])
+    del Xf, Yf, Mf
     t_data = time.perf_counter() - t0
-    sur = S.Surrogate(H, Wd, batch=8)
+    sur = S.Surrogate(H, Wd, batch=8, alpha=alpha)
     losses, t_train, nsteps = sur.train(X, Y, M, epochs=1000, lr=1e-3, seconds=args.train_seconds)
     flops = S.train_flops_per_sample(H, Wd) * 8 * nsteps
     # held-out: cold (batched), warm (batched, inference included)
@@ -513,8 +519,18 @@ def run_surrogate(args, ws, rank, local):
     bc.close()
     Xh = np.stack([S.features(s, t2, g) for s, t2, g in held])
     Yh = sur.predict(Xh)
-    pred_err = [float(np.linalg.norm(S.fields(Yh[k], *held[k])[1] - cold[k][1]) / np.linalg.norm(cold[k][1]))
-                for k in range(len(held))]
+    pred_err = [float(np.linalg.norm(S.fields(Yh[k], *held[k], alpha=alpha)[1] - cold[k][1]) /
+                      np.linalg.norm(cold[k][1])) for k in range(len(held))]
+    lub_err = [float(np.linalg.norm(S.fields(0 * Yh[k], *held[k], alpha=alpha)[1] - cold[k][1]) /
+                     np.linalg.norm(cold[k][1])) for k in range(len(held))]
+    # the fit on training cases, for comparison with the held-out error
+    tr = [int(k) for k in ok[:50]]
+    Yt = sur.predict(np.stack([S.features(*train[k]) for k in tr]))
+    train_err = []
+    for j, k in enumerate(tr):
+        ut = S.fields(Y[j], *train[k], alpha=alpha)[1]
+        train_err.append(float(np.linalg.norm(S.fields(Yt[j], *train[k], alpha=alpha)[1] - ut) / np.linalg.norm(ut)))
+    secs_l, steps_l, st_l, _, _, fallbacks_l = S.warm_start(None, held, tol, K, max_steps)
     secs_w, steps_w, st_w, warm, t_inf, fallbacks = S.warm_start(sur, held, tol, K, max_steps)
     diff = [float(np.linalg.norm(warm[k][1] - cold[k][1]) / np.linalg.norm(cold[k][1])) for k in range(len(held))]
     # plain sequential cold start on a subset
@@ -545,11 +561,18 @@ def run_surrogate(args, ws, rank, local):
             "data": "synthetic",
             "config": {"workload": "obstacle_channels_d2q9_smrt_f32_256x128_unet_bf16", "H": H, "W": Wd,
                        "train_cases": int(len(ok)), "held_out": len(held), "tol": tol, "tol_train": args.tol_train,
-                       "K": K, "seeds": [2212074942, 2212074943], "unet": "4 levels, widths 32/64/128/256"},
-            "cold": {"seconds": secs_c, "steps_mean": float(np.mean(steps_c)), "converged": int((st_c == 0).sum())},
+                       "K": K, "seeds": [2212074942, 2212074943],
+                       "unet": "4 levels, widths 32/64/128/256, periodic in x, 5 inputs incl. a lubrication estimate",
+                       "augmentation": "mirror y -> H - 1 - y", "lubrication_scale": list(alpha)},
+            "cold": {"seconds": secs_c, "steps_mean": float(np.mean(steps_c)), "steps_max": int(np.max(steps_c)),
+                     "converged": int((st_c == 0).sum())},
             "warm": {"seconds_incl_inference": secs_w, "inference_seconds": t_inf,
-                     "steps_mean": float(np.mean(steps_w)), "converged": int((st_w == 0).sum()),
+                     "steps_mean": float(np.mean(steps_w)), "steps_max": int(np.max(steps_w)),
+                     "converged": int((st_w == 0).sum()),
                      "fallbacks_to_cold": int(fallbacks)},
+            "lubrication_only": {"seconds": secs_l, "steps_mean": float(np.mean(steps_l)),
+                                 "converged": int((st_l == 0).sum()), "fallbacks_to_cold": int(fallbacks_l),
+                                 "what": "warm start from the lubrication estimate the network corrects"},
             "speedup_vs_cold_batched": secs_c / secs_w,
             "plain_cold": {"seconds_extrapolated": t_plain_est, "cases_measured": n_plain,
                            "how": "every 10th held-out case alone (lbm_create, lbm_residual every K), time scaled"},
@@ -557,7 +580,11 @@ def run_surrogate(args, ws, rank, local):
             "steps_saved_frac_mean": float(1.0 - np.mean(steps_w) / np.mean(steps_c)),
             "steps_saved_frac_median_per_case": float(np.median(1.0 - steps_w / steps_c)),
             "equal_error": {"rel_l2_warm_vs_cold_median": float(np.median(diff)), "rel_l2_warm_vs_cold_max": max(diff),
-                            "prediction_rel_l2_u_median": float(np.median(pred_err))},
+                            "prediction_rel_l2_u_median": float(np.median(pred_err)),
+                            "lubrication_rel_l2_u_median": float(np.median(lub_err)),
+                            "train_fit_rel_l2_u_median": float(np.median(train_err)),
+                            "steps_ratio_warm_over_cold_quantiles": [float(q) for q in
+                                                                     np.quantile(steps_w / steps_c, [0.1, 0.5, 0.9])]},
             "training": {"data_seconds": t_data, "train_seconds": t_train, "steps": nsteps, "batch": 8,
                          "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "epochs": len(losses),
                          "tflops": flops / t_train / 1e12, "frac_of_bf16_sustained": flops / t_train / 1e12 / peak_tf,

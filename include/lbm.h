@@ -197,7 +197,14 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out);
  * after the check that met tol), status, last residual.  Returns
  * LBM_ERR_TIMEOUT if the kernel's bounded scan for work saw no progress
  * anywhere for the scan limit (see lbm_batch_set_spin_limit); the channels
- * then hold the state they had reached.  Synchronises. */
+ * then hold the state they had reached.  Synchronises.
+ * The tail of a run: once at most lbm_batch_set_handoff's number of channels
+ * still run, each of them leaves the kernel at its next step boundary and
+ * the library continues it as a plain lattice (lbm_create / lbm_step /
+ * lbm_check_device on a stream of its own, all such channels concurrently),
+ * with the same check cadence, residual and stopping rules; the final state
+ * returns to the batch, so the outputs and lbm_batch_moments read the same
+ * as without the handoff. */
 lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_steps, int64_t *steps_out,
                                    int *st_out, double *r_out);
 
@@ -219,6 +226,12 @@ lbm_status lbm_batch_get_populations(lbm_batch *b, int i, double *f);
 lbm_status lbm_batch_set_tiles(lbm_batch *b, int block, int tile_nodes);
 lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nodes, double *ms_per_step);
 
+/* Channels left running when the tail moves to plain lattices (default 8;
+ * 0: the kernel runs every channel to the end).  A lone small channel costs
+ * a whole scheduling round of the persistent kernel per step, a plain
+ * lattice one graph-launched kernel. */
+lbm_status lbm_batch_set_handoff(lbm_batch *b, int channels);
+
 /* Scans for work without progress anywhere before the kernel stops with
  * LBM_ERR_TIMEOUT (default 2^26). */
 lbm_status lbm_batch_set_spin_limit(lbm_batch *b, int64_t scans);
@@ -229,8 +242,10 @@ void lbm_batch_destroy(lbm_batch *b);
 
 /* ---------------------------------------------------------------- surrogate
  * The steady-flow surrogate of the warm start: a U-Net on an H x W grid
- * (H, W multiples of 8) mapping per-node inputs x[n][y][x][3] (FP32) to
- * outputs y[n][y][x][3] (FP32).  Architecture: 4 levels of widths
+ * (H, W multiples of 8) mapping per-node inputs x[n][y][x][cin] (FP32,
+ * 1 <= cin <= 16) to outputs y[n][y][x][3] (FP32).  Every 3x3 convolution
+ * pads with zeros along y and, when periodic_x = 1, wraps around along x
+ * (a channel periodic in x), else pads with zeros.  Architecture: 4 levels of widths
  * 32/64/128/256, two 3x3 convolutions + ReLU per level, 2x2 average pooling
  * down, nearest 2x upsampling + 3x3 conv + ReLU up, concatenation
  * [up path, skip], linear 3x3 head.  BF16 weights and activations, FP32
@@ -242,7 +257,7 @@ void lbm_batch_destroy(lbm_batch *b);
  * All *_dev pointers are device arrays of n * H * W pixels. */
 typedef struct lbm_unet lbm_unet;
 
-lbm_status lbm_unet_create(int H, int W, int max_batch, void *stream, lbm_unet **out);
+lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch, void *stream, lbm_unet **out);
 int64_t lbm_unet_num_params(const lbm_unet *u);
 lbm_status lbm_unet_set_params(lbm_unet *u, const float *host);  /* resets Adam */
 lbm_status lbm_unet_get_params(lbm_unet *u, float *host);

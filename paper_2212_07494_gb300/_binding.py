@@ -90,6 +90,7 @@ def library():
     L.lbm_batch_set_tiles.argtypes = [B, C.c_int, C.c_int]
     L.lbm_batch_autotune.argtypes = [B, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.lbm_batch_set_spin_limit.argtypes = [B, C.c_int64]
+    L.lbm_batch_set_handoff.argtypes = [B, C.c_int]
     L.lbm_batch_info.argtypes = [B, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_batch_last_error.argtypes = [B]
     L.lbm_batch_last_error.restype = C.c_char_p
@@ -105,7 +106,7 @@ def library():
               "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc",
               "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
               "lbm_batch_moments", "lbm_batch_get_populations", "lbm_batch_set_tiles", "lbm_batch_autotune",
-              "lbm_batch_set_spin_limit", "lbm_batch_info"):
+              "lbm_batch_set_spin_limit", "lbm_batch_set_handoff", "lbm_batch_info"):
         getattr(L, n).restype = C.c_int
     _lib = L
     return L
@@ -441,6 +442,10 @@ def lbm_batch_set_spin_limit(b, scans):
     _bcheck(library().lbm_batch_set_spin_limit(b, int(scans)), b)
 
 
+def lbm_batch_set_handoff(b, channels):
+    _bcheck(library().lbm_batch_set_handoff(b, int(channels)), b)
+
+
 def lbm_batch_info(b, i):
     s, t, r = C.c_int64(), C.c_int(), C.c_int()
     _bcheck(library().lbm_batch_info(b, int(i), C.byref(s), C.byref(t), C.byref(r)), b)
@@ -504,6 +509,9 @@ class Batch:
     def set_spin_limit(self, scans):
         lbm_batch_set_spin_limit(self.b, scans)
 
+    def set_handoff(self, channels):
+        lbm_batch_set_handoff(self.b, channels)
+
     def info(self, i):
         return lbm_batch_info(self.b, i)
 
@@ -525,7 +533,7 @@ def _unet_lib():
     if not getattr(L, "_unet_ready", False):
         U = C.c_void_p
         fp = C.c_void_p
-        L.lbm_unet_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(U)]
+        L.lbm_unet_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(U)]
         L.lbm_unet_num_params.argtypes = [U]
         L.lbm_unet_num_params.restype = C.c_int64
         L.lbm_unet_set_params.argtypes = [U, C.POINTER(C.c_float)]
@@ -551,9 +559,10 @@ def _ucheck(status, u=None):
         raise LbmError(status, m.decode() if m else "")
 
 
-def lbm_unet_create(H, W, max_batch, stream=None):
+def lbm_unet_create(H, W, cin, periodic_x, max_batch, stream=None):
     u = C.c_void_p()
-    _ucheck(_unet_lib().lbm_unet_create(int(H), int(W), int(max_batch), stream, C.byref(u)))
+    _ucheck(_unet_lib().lbm_unet_create(int(H), int(W), int(cin), int(bool(periodic_x)), int(max_batch), stream,
+                                        C.byref(u)))
     return u
 
 
@@ -596,11 +605,13 @@ def lbm_unet_destroy(u):
 
 class UNet:
     """The surrogate network (see lbm.h).  Device tensors are passed as raw
-    pointers (e.g. torch ``data_ptr()``), float32, layout [n][H][W][3]."""
+    pointers (e.g. torch ``data_ptr()``), float32, inputs [n][H][W][cin],
+    outputs and targets [n][H][W][3]; periodic_x wraps the convolutions
+    around along x."""
 
-    def __init__(self, H, W, max_batch, stream=None):
-        self.H, self.W, self.B = H, W, max_batch
-        self.u = lbm_unet_create(H, W, max_batch, stream)
+    def __init__(self, H, W, max_batch, stream=None, cin=3, periodic_x=False):
+        self.H, self.W, self.B, self.cin, self.periodic_x = H, W, max_batch, cin, bool(periodic_x)
+        self.u = lbm_unet_create(H, W, cin, periodic_x, max_batch, stream)
         self.n = lbm_unet_num_params(self.u)
 
     def set_params(self, p):

@@ -31,6 +31,11 @@ using namespace lbm;
 
 namespace lbm {
 
+// the handoff of the tail to plain lattices (lbm_runtime.cu)
+lbm_status handle_adopt(lbm_handle *h, const void *state_dev, const void *snap_dev, int64_t step, int64_t snap_step);
+lbm_status handle_export_state(lbm_handle *h, void *state_dev);
+cudaStream_t handle_stream(const lbm_handle *h);
+
 struct BatchChan {
     long long off;       // element offset of the channel's Q planes in each population arena
     long long plane;     // nxp * ny
@@ -61,6 +66,7 @@ struct BatchCtl {
     long long start;           // steps completed when the run began
     int status;
     double r;                  // last residual
+    int parked;                // 1: left the kernel at a step boundary for the handoff
 };
 
 struct BatchRun {
@@ -79,6 +85,7 @@ struct BatchRun {
     unsigned long long *progress;
     int *error;
     double tol;     // < 0: never converge (fixed number of steps)
+    int park_below; // > 0: once at most this many channels run, each parks at its next step boundary
     int K;
     long long max_steps;   // per channel, counted from the run's start
     long long spin_limit;  // scans without any progress anywhere before giving up
@@ -344,8 +351,13 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                     }
                     r.ctl[c].steps = done_steps;
                     atomicExch(&r.ctl[c].done, 0u);
-                    if (retire) {
-                        r.ctl[c].status = status;
+                    // the tail: few channels left, each would take a whole
+                    // scheduling round per step here; they leave at this step
+                    // boundary and the host continues them as plain lattices
+                    const bool park = !retire && r.park_below > 0 && vload(r.active_count) <= r.park_below;
+                    if (retire || park) {
+                        if (retire) r.ctl[c].status = status;
+                        else r.ctl[c].parked = 1;
                         __threadfence();
                         atomicExch(&r.ctl[c].active, 0);
                         atomicAnd(r.active_bits + (c >> 5), ~(1u << (c & 31)));
@@ -376,6 +388,7 @@ __global__ void k_batch_reset(BatchRun r, long long total_nodes) {
         ctl[c].start = s;
         ctl[c].status = 1;
         ctl[c].r = -1.0;
+        ctl[c].parked = 0;
         atomicOr(r.active_bits + (c >> 5), 1u << (c & 31));
     }
     if (c == 0) {
@@ -418,6 +431,7 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int block = 128, tile_nodes = 2048;
+    int handoff = 8;           // channels left when the tail moves to plain lattices (0: never)
     long long spin_limit = 1ll << 26;
     size_t arena_elems = 0;
     std::string err;
@@ -503,6 +517,7 @@ lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
     r.progress = b->progress;
     r.error = b->error;
     r.tol = tol;
+    r.park_below = tol >= 0.0 ? b->handoff : 0;
     r.K = K;
     r.max_steps = max_steps;
     r.spin_limit = b->spin_limit;
@@ -559,6 +574,152 @@ lbm_status init_channels(lbm_batch *b) {
 const void *channel_state(const lbm_batch *b, int c) {
     const size_t eb = elem_bytes(b->storage);
     return (const char *)((b->steps[c] & 1) ? b->fb : b->fa) + b->ch[c].off * eb;
+}
+
+// Continue the channels that parked in the tail of a run, each as a plain
+// lattice (its own handle and stream, graph-launched steps), all of them
+// concurrently, with the batch's residual cadence and rules:
+//  - a check at every step s with (s - start) % K == 0 and s - start below
+//    max_steps, r = |u(s) - u(s - K)| / (K |u(s)|) over the fluid nodes;
+//  - r <= tol: converged, and (as in the kernel, which finishes the step it
+//    checked) one more step; non-finite: unstable, likewise;
+//  - s - start reaching max_steps: not converged.
+// The final state goes back into the batch's arena, so the channel reads
+// as if the kernel had run it to the end.
+lbm_status run_parked(lbm_batch *b, double tol, int K, int64_t max_steps) {
+    std::vector<BatchCtl> ctl(b->n);
+    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    struct Run {
+        int p;
+        lbm_handle *h;
+        int64_t s0;      // step of the velocity snapshot (the last check)
+        bool running;
+        bool check;      // a check was issued this round
+    };
+    std::vector<Run> runs;
+    for (int p = 0; p < b->n; ++p)
+        if (ctl[p].parked) runs.push_back({p, nullptr, 0, true, false});
+    if (runs.empty()) return LBM_OK;
+    const size_t eb = elem_bytes(b->storage);
+    double *red = nullptr;
+    lbm_status st = balloc(b, &red, runs.size() * 8 * sizeof(double));
+    auto cleanup = [&]() {
+        for (Run &q : runs)
+            if (q.h) lbm_destroy(q.h);
+        if (red) cudaFree(red);
+    };
+    if (st != LBM_OK) return st;
+    for (Run &q : runs) {
+        const int p = q.p;
+        const BatchChan &C = b->ch[p];
+        lbm_desc d = b->desc[p];
+        double g[3] = {C.gx, C.gy, 0.0};
+        d.g = d.force_kind == LBM_G_UNIFORM ? g : nullptr;
+        std::vector<unsigned char> mask;
+        if (C.solid_off >= 0) {
+            std::vector<unsigned char> pad((size_t)C.plane);
+            cudaError_t e = cudaMemcpy(pad.data(), b->solid + C.solid_off, (size_t)C.plane, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                cleanup();
+                return bfail(b, LBM_ERR_CUDA, std::string("handoff mask: ") + cudaGetErrorString(e));
+            }
+            mask.resize((size_t)C.nx * C.ny);
+            for (int y = 0; y < C.ny; ++y)
+                for (int x = 0; x < C.nx; ++x) mask[(size_t)y * C.nx + x] = pad[(size_t)y * C.nxp + x];
+            d.solid = mask.data();
+        } else {
+            d.solid = nullptr;
+        }
+        d.rho0 = d.u0 = nullptr;
+        d.stream = nullptr;
+        d.alloc = nullptr;
+        d.free_ = nullptr;
+        d.alloc_ctx = nullptr;
+        if ((st = lbm_create(&d, &q.h)) != LBM_OK) {
+            q.h = nullptr;
+            cleanup();
+            return bfail(b, st, std::string("handoff: ") + lbm_last_error(nullptr));
+        }
+        const long long steps = ctl[p].steps, start = ctl[p].start;
+        q.s0 = start + (long long)K * ((steps - 1 - start) / K);
+        st = handle_adopt(q.h, channel_state(b, p), (const char *)b->snap + C.snap_off * eb, steps, q.s0);
+        if (st != LBM_OK) {
+            cleanup();
+            return bfail(b, st, "handoff: state copy failed");
+        }
+    }
+    int left = (int)runs.size();
+    while (left > 0) {
+        for (size_t k = 0; k < runs.size(); ++k) {
+            Run &q = runs[k];
+            if (!q.running) continue;
+            const long long start = ctl[q.p].start, steps = b->steps[q.p] = ctl[q.p].steps;
+            const long long next = q.s0 + K, end = start + max_steps;
+            const long long target = std::min(next, end);
+            q.check = target == next && next - start < max_steps;
+            st = lbm_step(q.h, target - steps);
+            if (st == LBM_OK && q.check) st = lbm_check_device(q.h, red + 8 * k);
+            if (st != LBM_OK) {
+                cleanup();
+                return bfail(b, st, "handoff: step failed");
+            }
+            ctl[q.p].steps = target;
+        }
+        for (size_t k = 0; k < runs.size(); ++k) {
+            Run &q = runs[k];
+            if (!q.running) continue;
+            double v[8] = {0};
+            cudaError_t e = cudaStreamSynchronize(handle_stream(q.h));
+            if (e == cudaSuccess && q.check) e = cudaMemcpy(v, red + 8 * k, 7 * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                cleanup();
+                return bfail(b, LBM_ERR_CUDA, std::string("handoff: ") + cudaGetErrorString(e));
+            }
+            BatchCtl &c = ctl[q.p];
+            bool finish = false, extra = false;
+            if (q.check) {
+                q.s0 = c.steps;
+                const double rr = v[5] > 0.0 ? sqrt(v[4]) / ((double)K * sqrt(v[5])) : (v[4] > 0.0 ? INFINITY : 0.0);
+                c.r = rr;
+                if (v[6] > 0.0 || !std::isfinite(v[4]) || !std::isfinite(v[5])) {
+                    c.status = (int)LBM_ERR_UNSTABLE;
+                    finish = extra = true;
+                } else if (rr <= tol) {
+                    c.status = (int)LBM_OK;
+                    finish = extra = true;
+                }
+            }
+            if (!finish && c.steps - c.start >= max_steps) {
+                c.status = (int)LBM_NOT_CONVERGED;
+                finish = true;
+            }
+            if (!finish) continue;
+            if (extra) {
+                if ((st = lbm_step(q.h, 1)) != LBM_OK) {
+                    cleanup();
+                    return bfail(b, st, "handoff: step failed");
+                }
+                c.steps += 1;
+            }
+            void *dst = (char *)((c.steps & 1) ? b->fb : b->fa) + b->ch[q.p].off * eb;
+            st = handle_export_state(q.h, dst);
+            e = st == LBM_OK ? cudaStreamSynchronize(handle_stream(q.h)) : cudaErrorUnknown;
+            if (e != cudaSuccess) {
+                cleanup();
+                return bfail(b, LBM_ERR_CUDA, "handoff: state copy back failed");
+            }
+            b->steps[q.p] = c.steps;
+            c.parked = 0;
+            c.active = 0;
+            lbm_destroy(q.h);
+            q.h = nullptr;
+            q.running = false;
+            --left;
+        }
+    }
+    cleanup();
+    B_CUDA(b, cudaMemcpy(b->ctl_dev, ctl.data(), sizeof(BatchCtl) * b->n, cudaMemcpyHostToDevice));
+    return LBM_OK;
 }
 
 lbm_status ensure_tmp(lbm_batch *b, size_t bytes) {
@@ -791,6 +952,7 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_
     if (!(tol >= 0.0) || K < 1 || max_steps < 1) return bfail(b, LBM_ERR_ARG, "need tol >= 0, K >= 1, max_steps >= 1");
     lbm_status st = batch_run(b, tol, K, max_steps);
     if (st != LBM_OK && st != LBM_ERR_TIMEOUT) return st;
+    if (st == LBM_OK && (st = run_parked(b, tol, K, max_steps)) != LBM_OK) return st;
     std::vector<BatchCtl> ctl(b->n);
     B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
     for (int p = 0; p < b->n; ++p) {
@@ -800,6 +962,12 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_
         if (r_out) r_out[c] = ctl[p].r;
     }
     return st;
+}
+
+lbm_status lbm_batch_set_handoff(lbm_batch *b, int channels) {
+    if (!b || channels < 0) return bfail(b, LBM_ERR_ARG, "need a batch and channels >= 0");
+    b->handoff = channels;
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *block, int *tile_nodes, double *ms) {

@@ -21,7 +21,7 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-enum { BGK = 0, SMRT = 1 };
+enum { BGK = 0, SMRT = 1, SMRT_TRIM = 2 };  // SMRT_TRIM: SMRT with tau_3 = tau_4 = 1 (kernel choice only)
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 enum { G_NONE = 0, G_UNIFORM = 1, G_ROWS = 2, G_FIELD = 3 };
 
@@ -191,7 +191,7 @@ template <int L> inline void fill_offsets(KParams &p) {
 template <int D> struct Grid { static constexpr int N = D == 2 ? 9 : 27; };
 
 template <int D, int AX, typename R, typename F>
-__device__ __forceinline__ void for_lines(R *a, F f) {
+__host__ __device__ __forceinline__ void for_lines(R *a, F f) {
     constexpr int S = AX == 0 ? 1 : (AX == 1 ? 3 : 9);
 #pragma unroll
     for (int g = 0; g < Grid<D>::N; ++g) {
@@ -200,7 +200,7 @@ __device__ __forceinline__ void for_lines(R *a, F f) {
 }
 
 // populations (c = -1, 0, +1) -> moments (h0, h1, h2) on one line
-template <typename R> __device__ __forceinline__ void proj_line(R &m, R &z, R &p) {
+template <typename R> __host__ __device__ __forceinline__ void proj_line(R &m, R &z, R &p) {
     const R s = p + m, d = p - m;
     const R m0 = s + z;
     const R m2 = (R(2) * s - z) * R(1.0 / 3.0);
@@ -209,19 +209,19 @@ template <typename R> __device__ __forceinline__ void proj_line(R &m, R &z, R &p
     p = m2;
 }
 // shift a line of moments (h0, h1, h2) by velocity v: Hermite addition theorem
-template <typename R> __device__ __forceinline__ void shift_line(R &a0, R &a1, R &a2, R v) {
+template <typename R> __host__ __device__ __forceinline__ void shift_line(R &a0, R &a1, R &a2, R v) {
     a2 = a2 + v * (R(2) * a1 + v * a0);
     a1 = a1 + v * a0;
 }
 // moments (t0, t1, t2) -> populations with the D1Q3 weight folded in
-template <typename R> __device__ __forceinline__ void recon_line_w(R &t0, R &t1, R &t2) {
+template <typename R> __host__ __device__ __forceinline__ void recon_line_w(R &t0, R &t1, R &t2) {
     const R a = t0 + R(3) * t2, b = R(3) * t1;
     const R fz = R(2.0 / 3.0) * (t0 - R(1.5) * t2);
     t0 = R(1.0 / 6.0) * (a - b);
     t2 = R(1.0 / 6.0) * (a + b);
     t1 = fz;
 }
-template <typename R> __device__ __forceinline__ void recon_line(R &t0, R &t1, R &t2) {
+template <typename R> __host__ __device__ __forceinline__ void recon_line(R &t0, R &t1, R &t2) {
     const R a = t0 + R(3) * t2, b = R(3) * t1;
     const R fz = t0 - R(1.5) * t2;
     t0 = a - b;
@@ -229,17 +229,17 @@ template <typename R> __device__ __forceinline__ void recon_line(R &t0, R &t1, R
     t1 = fz;
 }
 
-template <int D, typename R> __device__ __forceinline__ void project(R *a) {
+template <int D, typename R> __host__ __device__ __forceinline__ void project(R *a) {
     for_lines<D, 0>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
     for_lines<D, 1>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
     if (D == 3) for_lines<D, 2>(a, [](R &x, R &y, R &z) { proj_line(x, y, z); });
 }
-template <int D, typename R> __device__ __forceinline__ void shift(R *a, R ux, R uy, R uz) {
+template <int D, typename R> __host__ __device__ __forceinline__ void shift(R *a, R ux, R uy, R uz) {
     for_lines<D, 0>(a, [ux](R &x, R &y, R &z) { shift_line(x, y, z, ux); });
     for_lines<D, 1>(a, [uy](R &x, R &y, R &z) { shift_line(x, y, z, uy); });
     if (D == 3) for_lines<D, 2>(a, [uz](R &x, R &y, R &z) { shift_line(x, y, z, uz); });
 }
-template <int L, typename R> __device__ __forceinline__ void reconstruct(R *a) {
+template <int L, typename R> __host__ __device__ __forceinline__ void reconstruct(R *a) {
     constexpr int D = Lat<L>::D;
     if (L == D3Q19) {
         for_lines<D, 0>(a, [](R &x, R &y, R &z) { recon_line(x, y, z); });
@@ -257,7 +257,7 @@ template <int L, typename R> __device__ __forceinline__ void reconstruct(R *a) {
 // overwritten with the post-collision deviations.  g: acceleration (lattice
 // units).  Returns nothing; rho/u are recomputed by the moments kernel.
 template <int L, typename R>
-__device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+__host__ __device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
     constexpr int D = Lat<L>::D;
     constexpr int N = Grid<D>::N;
     constexpr int EX = 1, EY = 3, EZ = 9;
@@ -296,9 +296,182 @@ __device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om
     }
 }
 
+// ------------------------------------------------- sparse passes (trimmed SMRT)
+// With tau_3 = tau_4 = 1 the factors (1 - 1/tau_n) of orders 3 and 4 vanish:
+// after relaxation only the central moments of orders <= 2 are non-zero, so
+// only the raw moments of orders <= 2 need projecting and shifting.  The
+// passes below are the same per-axis line operations as above, restricted
+// at compile time by masks over the 3^D grid (bit g): NEED, the entries a
+// later step reads (an unneeded output is not computed), and NZ, the entries
+// that may be non-zero (a known zero is not read).
+template <int D> __host__ __device__ constexpr unsigned grid_mask() { return D == 2 ? 0x1FFu : 0x7FFFFFFu; }
+__host__ __device__ constexpr int ax_stride(int ax) { return ax == 0 ? 1 : (ax == 1 ? 3 : 9); }
+__host__ __device__ constexpr int line_pos(int g, int ax) { return (g / ax_stride(ax)) % 3; }
+template <int D> __host__ __device__ constexpr unsigned orders_upto(int n) {
+    unsigned m = 0;
+    for (int g = 0; g < Grid<D>::N; ++g)
+        if (morder<D>(g) <= n) m |= 1u << g;
+    return m;
+}
+template <int L> __host__ __device__ constexpr unsigned retained_mask() {
+    unsigned m = 0;
+    for (int g = 0; g < Grid<Lat<L>::D>::N; ++g)
+        if (retained<L>(g)) m |= 1u << g;
+    return m;
+}
+// inputs read by a projection pass along ax for the outputs `need`: whole lines
+template <int D> __host__ __device__ constexpr unsigned need_proj(unsigned need, int ax) {
+    unsigned m = 0;
+    const int S = ax_stride(ax);
+    for (int g = 0; g < Grid<D>::N; ++g)
+        if ((need >> g) & 1u) {
+            const int b = g - line_pos(g, ax) * S;
+            m |= (1u << b) | (1u << (b + S)) | (1u << (b + 2 * S));
+        }
+    return m;
+}
+// inputs read by a shift pass along ax for the outputs `need`: output k of a
+// line reads entries 0..k of it
+template <int D> __host__ __device__ constexpr unsigned need_shift(unsigned need, int ax) {
+    unsigned m = 0;
+    const int S = ax_stride(ax);
+    for (int g = 0; g < Grid<D>::N; ++g)
+        if ((need >> g) & 1u) {
+            const int b = g - line_pos(g, ax) * S;
+            for (int j = 0; j <= line_pos(g, ax); ++j) m |= 1u << (b + j * S);
+        }
+    return m;
+}
+// entries that may be non-zero after a shift pass along ax
+template <int D> __host__ __device__ constexpr unsigned nz_shift(unsigned nz, int ax) {
+    unsigned m = 0;
+    const int S = ax_stride(ax);
+    for (int g = 0; g < Grid<D>::N; ++g) {
+        const int b = g - line_pos(g, ax) * S;
+        for (int j = 0; j <= line_pos(g, ax); ++j)
+            if ((nz >> (b + j * S)) & 1u) m |= 1u << g;
+    }
+    return m;
+}
+
+template <int I> struct Idx { static constexpr int value = I; };
+template <int N, typename F, int I = 0> __host__ __device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (I < N) {
+        f(Idx<I>{});
+        static_for<N, F, I + 1>(static_cast<F &&>(f));
+    }
+}
+
+// projection pass (proj_line) computing only the outputs in NEED
+template <int D, int AX, unsigned NEED, typename R> __host__ __device__ __forceinline__ void proj_pass(R *a) {
+    constexpr int S = ax_stride(AX);
+    static_for<Grid<D>::N>([&](auto I) {
+        constexpr int g = decltype(I)::value;
+        if constexpr (line_pos(g, AX) == 0) {
+            constexpr bool n0 = (NEED >> g) & 1u, n1 = (NEED >> (g + S)) & 1u, n2 = (NEED >> (g + 2 * S)) & 1u;
+            if constexpr (n0 || n1 || n2) {
+                const R m = a[g], z = a[g + S], p = a[g + 2 * S];
+                const R s = p + m;
+                if constexpr (n0) a[g] = s + z;
+                if constexpr (n1) a[g + S] = p - m;
+                if constexpr (n2) a[g + 2 * S] = (R(2) * s - z) * R(1.0 / 3.0);
+            }
+        }
+    });
+}
+
+// shift pass (shift_line) computing only the outputs in NEED from inputs of
+// which only those in NZ may be non-zero
+template <int D, int AX, unsigned NZ, unsigned NEED, typename R>
+__host__ __device__ __forceinline__ void shift_pass(R *a, R v) {
+    constexpr int S = ax_stride(AX);
+    static_for<Grid<D>::N>([&](auto I) {
+        constexpr int g = decltype(I)::value;
+        if constexpr (line_pos(g, AX) == 0) {
+            constexpr bool z0 = (NZ >> g) & 1u, z1 = (NZ >> (g + S)) & 1u, z2 = (NZ >> (g + 2 * S)) & 1u;
+            constexpr bool n0 = (NEED >> g) & 1u, n1 = (NEED >> (g + S)) & 1u, n2 = (NEED >> (g + 2 * S)) & 1u;
+            const R a0 = z0 ? a[g] : R(0);
+            const R a1 = z1 ? a[g + S] : R(0);
+            if constexpr (n2) {
+                if constexpr (z0 && z1 && z2) a[g + 2 * S] = a[g + 2 * S] + v * (R(2) * a1 + v * a0);
+                else if constexpr (z0 && z1) a[g + 2 * S] = v * (R(2) * a1 + v * a0);
+                else if constexpr (z0 && z2) a[g + 2 * S] = a[g + 2 * S] + v * (v * a0);
+                else if constexpr (z1 && z2) a[g + 2 * S] = a[g + 2 * S] + v * (R(2) * a1);
+                else if constexpr (z0) a[g + 2 * S] = v * (v * a0);
+                else if constexpr (z1) a[g + 2 * S] = v * (R(2) * a1);
+                else if constexpr (!z2) a[g + 2 * S] = R(0);
+            }
+            if constexpr (n1) {
+                if constexpr (z0 && z1) a[g + S] = a1 + v * a0;
+                else if constexpr (z0) a[g + S] = v * a0;
+                else if constexpr (!z1) a[g + S] = R(0);
+            }
+            if constexpr (n0 && !z0) a[g] = R(0);
+        }
+    });
+}
+
+// SMRT with tau_3 = tau_4 = 1 (om3 = om4 = 1): the same collision as
+// collide_smrt, whose orders-3/4 factors (1 - om) are then exactly zero,
+// with the passes restricted to what is non-zero or read.
+template <int L, typename R>
+__host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R gz, R om2) {
+    constexpr int D = Lat<L>::D;
+    constexpr int N = Grid<D>::N;
+    constexpr int EX = 1, EY = 3, EZ = 9;
+    constexpr unsigned LOW = orders_upto<D>(2);
+    constexpr unsigned RET = retained_mask<L>();
+    // projection: raw moments of orders <= 2 (a downward-closed set, so the
+    // central shift below reads nothing else)
+    constexpr unsigned P3 = LOW;
+    constexpr unsigned P2 = D == 3 ? need_proj<D>(P3, 2) : LOW;
+    constexpr unsigned P1 = need_proj<D>(P2, 1);
+    proj_pass<D, 0, P1>(G);
+    proj_pass<D, 1, P2>(G);
+    if constexpr (D == 3) proj_pass<D, 2, P3>(G);
+    const R drho = G[0];
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = G[EX] * inv + R(0.5) * gx;   // Eq. (half_F)
+    const R uy = G[EY] * inv + R(0.5) * gy;
+    const R uz = D == 3 ? G[EZ] * inv + R(0.5) * gz : R(0);
+    G[0] = rho;
+    constexpr unsigned ALL = grid_mask<D>();
+    shift_pass<D, 0, ALL, LOW>(G, -ux);
+    shift_pass<D, 1, ALL, LOW>(G, -uy);
+    if constexpr (D == 3) shift_pass<D, 2, ALL, LOW>(G, -uz);
+    static_for<N>([&](auto I) {
+        constexpr int g = decltype(I)::value;
+        if constexpr (((LOW >> g) & 1u) && morder<D>(g) == 2) G[g] *= (R(1) - om2);
+    });
+    G[0] = rho;
+    G[EX] = R(0.5) * rho * gx;
+    G[EY] = R(0.5) * rho * gy;
+    if constexpr (D == 3) G[EZ] = R(0.5) * rho * gz;
+    // back to raw moments on the retained set: only orders <= 2 are non-zero
+    constexpr unsigned S3 = RET;
+    constexpr unsigned S2 = D == 3 ? need_shift<D>(S3, 2) : RET;
+    constexpr unsigned S1 = need_shift<D>(S2, 1);
+    constexpr unsigned Z1 = nz_shift<D>(LOW, 0) & S1;
+    constexpr unsigned Z2 = nz_shift<D>(Z1, 1) & S2;
+    shift_pass<D, 0, LOW, S1>(G, ux);
+    shift_pass<D, 1, Z1, S2>(G, uy);
+    if constexpr (D == 3) shift_pass<D, 2, Z2, S3>(G, uz);
+    static_for<N>([&](auto I) {
+        constexpr int g = decltype(I)::value;
+        if constexpr (!((RET >> g) & 1u)) G[g] = R(0);
+    });
+    G[0] = drho;                          // deviation from the weights
+    reconstruct<L>(G);
+    if (L == D3Q19) {
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) G[gpos<L>(i)] *= R(weight<L>(i));
+    }
+}
+
 // BGK with the second-order equilibrium and Guo-form force, Eq. (explict_eq)
 template <int L, typename R>
-__device__ __forceinline__ void collide_bgk(R *G, R gx, R gy, R gz, R om) {
+__host__ __device__ __forceinline__ void collide_bgk(R *G, R gx, R gy, R gz, R om) {
     constexpr int Q = Lat<L>::Q;
     constexpr int D = Lat<L>::D;
     R drho = 0, jx = 0, jy = 0, jz = 0;

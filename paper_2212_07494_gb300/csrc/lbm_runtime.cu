@@ -88,7 +88,7 @@ struct lbm_handle {
     double *fields = nullptr;    // (1 + D) * N doubles for lbm_moments
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // graph_steps steps starting from buf[0] / buf[1]
     int graph_steps = 0;
     int64_t step = 0;
     void *(*alloc)(size_t, void *) = nullptr;
@@ -192,8 +192,11 @@ lbm_status launch_steps(lbm_handle *h, int64_t n) {
     return LBM_OK;
 }
 
+// the graph of graph_steps steps that starts from the buffer holding the
+// state now (a graph has its buffers baked in; after an odd number of single
+// steps the state lives in the other buffer, so each parity has its graph)
 lbm_status ensure_graph(lbm_handle *h) {
-    if (h->graph) return LBM_OK;
+    if (h->graph[h->cur]) return LBM_OK;
     const int steps = h->graph_steps;
     const int saved = h->cur;
     cudaGraph_t g = nullptr;
@@ -206,10 +209,10 @@ lbm_status ensure_graph(lbm_handle *h) {
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(&h->graph[saved], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph = nullptr;
+        h->graph[saved] = nullptr;
         return cuda_fail(h, e, "cudaGraphInstantiate");
     }
     return LBM_OK;
@@ -231,6 +234,38 @@ lbm_status run_moments(lbm_handle *h, double *rho, double *u, void *uprev, doubl
 
 }  // namespace
 
+// Library-internal entry points of the batch handoff: a handle created for
+// one channel of a batched run takes over that channel's state and residual
+// snapshot at a step boundary, and gives its state back at the end.  The
+// batch stores a D2Q9 channel exactly as a handle does ([Q][ny][nxp],
+// nxp = 32 ceil(nx / 32), deviations; snapshot [D][nx * ny] of the arithmetic
+// type), so both copies are plain device-to-device copies on the handle's
+// stream.
+namespace lbm {
+
+lbm_status handle_adopt(lbm_handle *h, const void *state_dev, const void *snap_dev, int64_t step,
+                        int64_t snap_step) {
+    const size_t sb = (size_t)h->D * h->N() * arith_bytes(h->storage);
+    if (!h->uprev) {
+        lbm_status st = alloc_into(h, &h->uprev, sb, "residual velocity");
+        if (st != LBM_OK) return st;
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], state_dev, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->uprev, snap_dev, sb, cudaMemcpyDeviceToDevice, h->stream));
+    h->step = step;
+    h->uprev_step = snap_step;
+    return LBM_OK;
+}
+
+lbm_status handle_export_state(lbm_handle *h, void *state_dev) {
+    LBM_CUDA(h, cudaMemcpyAsync(state_dev, h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return LBM_OK;
+}
+
+cudaStream_t handle_stream(const lbm_handle *h) { return h->stream; }
+
+}  // namespace lbm
+
 extern "C" {
 
 const char *lbm_last_error(const lbm_handle *h) { return h ? h->err.c_str() : g_thread_err.c_str(); }
@@ -238,7 +273,8 @@ const char *lbm_last_error(const lbm_handle *h) { return h ? h->err.c_str() : g_
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaGraphExec_t &ge : h->graph)
+        if (ge) cudaGraphExecDestroy(ge);
     dev_free(h, h->buf[0]);
     dev_free(h, h->buf[1]);
     dev_free(h, h->g_dev);
@@ -429,7 +465,7 @@ lbm_status lbm_step(lbm_handle *h, int64_t nsteps) {
         lbm_status st = ensure_graph(h);
         if (st != LBM_OK) return st;
         while (left >= h->graph_steps) {
-            LBM_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+            LBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
             left -= h->graph_steps;
         }
     }
@@ -586,10 +622,11 @@ lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread) {
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->cfg.bdx = block_x;
     h->cfg.npt = nodes_per_thread;
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
+    for (cudaGraphExec_t &ge : h->graph)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
     return LBM_OK;
 }
 

@@ -115,6 +115,40 @@ def test_run_to_steady_agrees_with_plain_loop():
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["F32", "F64"])
+def test_tail_handoff_matches_the_kernel_alone(storage):
+    """The tail handed to plain lattices ends where the persistent kernel
+    alone ends: the same status for every channel, the same step count and
+    final fields in FP64 (only the residual's summation order differs); in
+    FP32 the plain and batched kernels round differently (see
+    test_batch_channels_with_obstacles), so a residual near tol may stop a
+    check interval apart, with fields equal to FP32 noise.  Handoff 1000
+    hands every channel over after its first step, 8 only the last eight, 0
+    never."""
+    import paper_2212_07494_gb300 as P
+    chans = _channels(24, 13, nx=(24, 96), ny=(8, 40))
+    chans[5]["solid"] = W.random_solid((chans[5]["shape"][0], chans[5]["shape"][1], 1), 3, frac=0.05)
+    tol, K = 1e-7, 200
+    res = {}
+    for ho in (0, 8, 1000):
+        b = P.Batch(chans, "SMRT", storage)
+        b.set_handoff(ho)
+        status, steps, st, r = b.run_to_steady(tol, K, max_steps=400000)
+        assert status == 0
+        res[ho] = (steps.copy(), st.copy(), r.copy(), [b.moments(i)[1] for i in range(len(chans))])
+        b.close()
+    assert np.all(res[0][1] == 0), res[0][1]
+    for ho in (8, 1000):
+        assert np.array_equal(res[ho][1], res[0][1]), (ho, res[ho][1])
+        if storage == "F64":
+            assert np.array_equal(res[ho][0], res[0][0]), (ho, res[ho][0] - res[0][0])
+            assert np.allclose(res[ho][2], res[0][2], rtol=1e-6), ho
+        else:
+            assert np.abs(res[ho][0] - res[0][0]).max() <= K, (ho, res[ho][0] - res[0][0])
+        for i in range(len(chans)):
+            assert rel_l2(res[ho][3][i], res[0][3][i]) < (1e-10 if storage == "F64" else 1e-5), (ho, i)
+
+
 def test_run_to_steady_reports_not_converged():
     import paper_2212_07494_gb300 as P
     chans = _channels(5, 3)
@@ -132,6 +166,7 @@ def test_bounded_scan_times_out_cleanly():
     import paper_2212_07494_gb300 as P
     chans = _channels(2, 5, nx=(40, 60), ny=(8, 12))
     b = P.Batch(chans, "SMRT", "F32")
+    b.set_handoff(0)   # the kernel alone: the test is about its bounded scan
     b.set_spin_limit(1)
     status, steps, st, r = b.run_to_steady(0.0, 10, max_steps=100000)
     assert status == -5, status

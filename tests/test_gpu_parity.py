@@ -19,7 +19,14 @@ pytestmark = pytest.mark.gpu
 LATTICES = ["D2Q9", "D3Q19", "D3Q27"]
 SHAPES = {"D2Q9": [(150, 37, 1), (530, 9, 1)], "D3Q19": [(70, 9, 7), (130, 5, 4)],
           "D3Q27": [(70, 9, 7), (130, 5, 4)]}
-TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1)}
+# SMRT_TRIM: tau_3 = tau_4 = 1, the kernels' trimmed collision (orders 3 and 4
+# relax to zero exactly); the oracle runs its one general collision for both
+TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1), "SMRT_TRIM": (1.0, 1.3, 0.63, 1.0, 1.0)}
+COLLS = ["BGK", "SMRT", "SMRT_TRIM"]
+
+
+def _model(coll):
+    return "BGK" if coll == "BGK" else "SMRT"
 
 
 def _D(lat):
@@ -48,7 +55,7 @@ def test_initial_populations(lat, coll):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", ["BGK", "SMRT"])
+@pytest.mark.parametrize("coll", COLLS)
 @pytest.mark.parametrize("which", [0, 1])
 def test_one_step_populations_f64(lat, coll, which):
     """Arbitrary non-equilibrium state, periodic x, walls in y (and z), solid
@@ -57,7 +64,7 @@ def test_one_step_populations_f64(lat, coll, which):
     periodic = (1, 0, 0) if _D(lat) == 3 else (1, 0, 1)
     solid = W.random_solid(shape, seed=31 + which, frac=0.08)
     f0 = _random_state(lat, shape, 41 + which, solid)
-    gl, orc = make_pair(lat, coll, shape, TAU[coll], "F64", periodic, g=_gvec(lat), solid=solid)
+    gl, orc = make_pair(lat, _model(coll), shape, TAU[coll], "F64", periodic, g=_gvec(lat), solid=solid)
     gl.set_populations(f0)
     orc.set_populations(f0)
     assert np.abs(gl.populations() - f0).max() < 1e-16
@@ -69,12 +76,12 @@ def test_one_step_populations_f64(lat, coll, which):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", ["BGK", "SMRT"])
+@pytest.mark.parametrize("coll", COLLS)
 def test_velocity_after_many_steps_f64(lat, coll):
     shape = SHAPES[lat][1]
     steps = 300 if lat == "D2Q9" else 60
     rho0, u0 = W.random_near_equilibrium(lat, shape, seed=51, du=0.02)
-    gl, orc = make_pair(lat, coll, shape, TAU[coll], "F64", (1, 1, 1), g=_gvec(lat), rho0=rho0, u0=u0)
+    gl, orc = make_pair(lat, _model(coll), shape, TAU[coll], "F64", (1, 1, 1), g=_gvec(lat), rho0=rho0, u0=u0)
     gl.step(steps)
     orc.step(steps)
     rg, ug, tg = gl.moments()
@@ -132,14 +139,14 @@ def test_force_kinds(kind, lat):
 
 @pytest.mark.parametrize("lat", LATTICES)
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16"])
-def test_one_step_reduced_storage(lat, storage):
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_TRIM"])
+def test_one_step_reduced_storage(lat, storage, coll):
     """One step from the same stored (rounded) state: GPU (FP32 arithmetic,
     rounding on store) vs the oracle (FP64 arithmetic, same rounding)."""
     shape = SHAPES[lat][0]
-    coll = "SMRT"
     solid = W.random_solid(shape, seed=61, frac=0.05)
     f0 = _random_state(lat, shape, 71, solid, amp=0.05)
-    gl, orc = make_pair(lat, coll, shape, TAU[coll], storage, (1, 0, 1), g=_gvec(lat), solid=solid,
+    gl, orc = make_pair(lat, _model(coll), shape, TAU[coll], storage, (1, 0, 1), g=_gvec(lat), solid=solid,
                         emulate_storage=True)
     # start both from deviations already representable in the storage format
     orc.set_populations(f0)                     # rounds to the storage format
@@ -177,6 +184,29 @@ def test_state_checkpoint_restart_is_bit_exact():
     b.step(41)
     assert np.array_equal(a.state()[0], b.state()[0])
     assert a.info()[2] == b.info()[2] == 78
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q27"])
+def test_step_splits_are_bit_identical(lat):
+    """lbm_step replays a captured graph of 64 steps and launches the rest one
+    by one; after an odd number of single steps the state lives in the other
+    population buffer.  Any split of the same steps gives the same state,
+    bit for bit."""
+    from paper_2212_07494_gb300 import Lattice
+    shape = SHAPES[lat][0]
+    rho0, u0 = W.random_near_equilibrium(lat, shape, seed=91)
+    mk = lambda: Lattice(lat, "SMRT", shape, TAU["SMRT_TRIM"], "F32", (1, 0, 1), g=_gvec(lat), rho0=rho0, u0=u0)
+    a, b, c = mk(), mk(), mk()
+    for n in (1, 64, 3, 100, 65, 7):
+        a.step(n)
+    for _ in range(240):
+        b.step(1)
+    c.step(240)
+    sa, sb, sc = a.state()[0], b.state()[0], c.state()[0]
+    assert np.array_equal(sa, sb) and np.array_equal(sa, sc)
+    assert a.info()[2] == b.info()[2] == c.info()[2] == 240
+    for x in (a, b, c):
+        x.close()
 
 
 def test_mass_conservation_long_f64():
