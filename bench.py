@@ -94,12 +94,15 @@ def job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
     return ws * units_per_rank / seconds
 
 
+# the sources that define the D2Q9 stream-collide kernel and its launch
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h", "lbm_inst_d2q9.cu")
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2212_07494_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
