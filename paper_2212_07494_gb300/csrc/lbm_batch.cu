@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
             const unsigned char *solid = C.solid_off >= 0 ? r.solid + C.solid_off : nullptr;
             const int N = C.nx * C.ny;
             const R om2 = R(C.om2), om3 = R(C.om3), om4 = R(C.om4), gx = R(C.gx), gy = R(C.gy);
+            const bool trim = C.om3 == 1.0 && C.om4 == 1.0;
             double v[2] = {0.0, 0.0};
             // two nodes per thread per pass, all loads issued first
             for (int base = threadIdx.x; base < nn; base += 2 * blockDim.x) {
@@ -302,7 +303,10 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                         snap[n] = ux;
                         snap[N + n] = uy;
                     }
-                    if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4);
+                    // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it, so
+                    // that a channel evolves with the same arithmetic here and alone
+                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
+                    else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4);
                     else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
                     T *dst = fout + (y * C.nxp + x);
 #pragma unroll
