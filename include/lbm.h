@@ -249,7 +249,12 @@ void lbm_batch_destroy(lbm_batch *b);
  * 32/64/128/256, two 3x3 convolutions + ReLU per level, 2x2 average pooling
  * down, nearest 2x upsampling + 3x3 conv + ReLU up, concatenation
  * [up path, skip], linear 3x3 head.  BF16 weights and activations, FP32
- * accumulation on the tensor cores, FP32 master weights and Adam moments.
+ * accumulation on the tensor cores (every convolution and input-gradient
+ * convolution but the 3-output head as an implicit GEMM on tcgen05 with TMEM
+ * accumulators; the head and the weight gradients on mma.sync), FP32 master
+ * weights and Adam moments.  A tcgen05 convolution whose bounded wait
+ * expires is reported as LBM_ERR_TIMEOUT by the next lbm_unet_grad or
+ * lbm_unet_get_params (the calls that synchronise).
  * Loss: sum_p m[p] sum_c (y - t)^2 * scale (scale = 1 / (3 sum m) gives the
  * weighted mean).  Parameters (host, FP32) in the canonical layout: per layer
  * W[co][ky][kx][ci] then b[co], layers in the order enc1a enc1b enc2a enc2b

@@ -195,6 +195,202 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
             }
 }
 
+// ------------------------------------------- convolution on tcgen05 (TMEM)
+// The same implicit GEMM as k_conv on the 5th-generation tensor cores: a CTA
+// of 4 warps computes 128 pixels x NT output channels, accumulating in TMEM
+// (128 lanes x NT FP32 columns).  Operand tiles are staged by cp.async into
+// shared memory in the K-major layout without swizzle that the MMA reads
+// through matrix descriptors: 8-row x 16-byte core matrices, adjacent along
+// K at TC_KSTEP bytes, adjacent 8-row groups at (BK / 8) * TC_KSTEP bytes.
+// One thread issues the MMAs of a K block (BK / 16 instructions of K = 16)
+// and commits them to the stage's mbarrier; a stage is refilled once that
+// barrier shows its MMAs done.  Every wait is bounded: on expiry the CTA sets
+// *err, skips the rest (uniformly across the CTA), frees its TMEM and
+// returns.
+constexpr int TC_KSTEP = 128;
+constexpr long TC_SPIN = 1L << 22;
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family; no swizzle, base offset 0
+    return d;
+}
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ bool tc_wait(unsigned long long *mbar, unsigned parity) {
+    for (long it = 0; it < TC_SPIN; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t"
+            "}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(mbar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+template <int BK, int NT>
+__global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a, int *err) {
+    constexpr int ABYTES = 128 * BK * 2, BBYTES = NT * BK * 2, STAGE = ABYTES + BBYTES;
+    constexpr int RGRP = (BK / 8) * TC_KSTEP;
+    constexpr int NCOL = NT < 32 ? 32 : NT;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *sm = (unsigned char *)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+    const long long M = (long long)a.N * a.H * a.W;
+    const long long m0 = (long long)blockIdx.x * 128;
+    const int co0 = blockIdx.y * NT;
+    // this thread's A row (one pixel)
+    const long long mrow = m0 + tid;
+    int an = -1, ay = 0, ax = 0;
+    if (mrow < M) {
+        const int hw = a.H * a.W;
+        an = (int)(mrow / hw);
+        const int r = (int)(mrow - (long long)an * hw);
+        ay = r / a.W;
+        ax = r - ay * a.W;
+    }
+    const int cblocks = a.cin / BK;
+    const int KB = 9 * cblocks;
+    auto load = [&](int kb, int buf) {
+        const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        unsigned char *sa = sm + buf * STAGE, *sb = sa + ABYTES;
+        {
+            const int yy = ay + dy;
+            int xx = ax + dx;
+            if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+            const bool ok = an >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = ok ? a.x + ((long long)(an * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 : a.x;
+#pragma unroll
+            for (int cc = 0; cc < BK / 8; ++cc)
+                cp_async16(sa + (tid >> 3) * RGRP + cc * TC_KSTEP + (tid & 7) * 16, ok ? src + cc * 8 : a.x, ok);
+        }
+#pragma unroll
+        for (int q = tid; q < NT * (BK / 8); q += 128) {
+            const int r = q / (BK / 8), cc = q % (BK / 8);
+            const int co = co0 + r;
+            const bool ok = co < a.wrows;
+            const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + cc * 8 : a.w;
+            cp_async16(sb + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, src, ok);
+        }
+        cp_async_commit();
+    };
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[s])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    constexpr uint32_t IDESC = tc_idesc(128, NT);
+    bool fail = false;
+    load(0, 0);
+    for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb & 1;
+        if (kb + 1 < KB) {
+            // the MMAs of kb - 1 read stage s ^ 1: wait for them before refilling it
+            if (kb >= 1 && !tc_wait(&mbar[s ^ 1], ((kb - 1) >> 1) & 1)) fail = true;
+            if (!fail) load(kb + 1, s ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (fail) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned sa = smem_addr(sm + s * STAGE), sb = sa + ABYTES;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint64_t da = tc_desc(sa + ks * 2 * TC_KSTEP, TC_KSTEP, RGRP);
+                const uint64_t db = tc_desc(sb + ks * 2 * TC_KSTEP, TC_KSTEP, RGRP);
+                const unsigned acc = (kb > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                    "}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&mbar[s])));
+        }
+    }
+    cp_async_wait<0>();
+    // the last commit covers every MMA of this CTA
+    if (!s_fail && !tc_wait(&mbar[(KB - 1) & 1], ((KB - 1) >> 1) & 1)) fail = true;
+    if (fail) s_fail = 1;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!s_fail) {
+        // warp w holds TMEM lanes 32w .. 32w + 31: one pixel per thread
+        const long long m = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < NT; c += 16) {
+            unsigned r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int cb = co0 + c;
+            if (m >= M || cb >= a.cout) continue;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                v[j] = __uint_as_float(r[j]);
+                if (a.bias && cb + j < a.cout) v[j] += a.bias[cb + j];
+                if (a.relu) v[j] = fmaxf(v[j], 0.f);
+            }
+            if (a.gate) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (cb + j < a.cout && !(__bfloat162float(a.gate[m * a.gc + a.go + cb + j]) > 0.f)) v[j] = 0.f;
+            }
+            bf16 *dst = a.y + m * a.yc + a.yo + cb;
+            if (cb + 16 <= a.cout) {
+                __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) o[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+            } else {
+                for (int j = 0; j < 16 && cb + j < a.cout; ++j) dst[j] = __float2bfloat16_rn(v[j]);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
 // ------------------------------------------------------------ weight gradient
 struct WgradArgs {
     const bf16 *dz;
@@ -479,6 +675,7 @@ struct lbm_unet {
         *g_ba, *g_p3, *g_e3a, *g_p2, *g_e2a, *g_p1, *g_e1a;
     float *yf = nullptr;
     double *loss = nullptr;
+    int *tc_err = nullptr;     // set by a tcgen05 convolution whose bounded wait expired
     std::vector<void *> allocs;
     std::string err;
 };
@@ -512,6 +709,43 @@ lbm_status ualloc(lbm_unet *u, T **p, size_t count) {
 }
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// dynamic shared memory of k_conv_tc<BK, NT>: two stages plus alignment
+// slack, and at least enough that no more CTAs fit on an SM than its 512
+// TMEM columns serve (tcgen05.alloc of a CTA beyond them would wait)
+template <int BK, int NT> size_t tc_smem_bytes() {
+    const size_t need = 2 * (size_t)(128 * BK + NT * BK) * 2 + 1024;
+    const int ncol = NT < 32 ? 32 : NT;
+    const size_t floor_ = 233472 / (512 / ncol + 1) - 1024 + 1;
+    return need > floor_ ? need : floor_;
+}
+
+template <int BK, int NT> lbm_status launch_tc(lbm_unet *u, const ConvArgs &a, long long M) {
+    static bool attr = false;
+    const size_t smem = tc_smem_bytes<BK, NT>();
+    if (!attr) {
+        U_CUDA(u, cudaFuncSetAttribute(k_conv_tc<BK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    dim3 grid(nblk(M, 128), nblk(a.cout, NT));
+    k_conv_tc<BK, NT><<<grid, 128, smem, u->stream>>>(a, u->tc_err);
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <int BK> lbm_status launch_tc_n(lbm_unet *u, const ConvArgs &a, long long M) {
+    if (a.cout <= 16) return launch_tc<BK, 16>(u, a, M);
+    if (a.cout <= 32) return launch_tc<BK, 32>(u, a, M);
+    if (a.cout <= 64) return launch_tc<BK, 64>(u, a, M);
+    return launch_tc<BK, 128>(u, a, M);
+}
+
+// convolutions with N = cout a multiple of 16 (every layer but the head)
+lbm_status conv_tc(lbm_unet *u, const ConvArgs &a, long long M) {
+    if (a.cin % 64 == 0) return launch_tc_n<64>(u, a, M);
+    if (a.cin % 32 == 0) return launch_tc_n<32>(u, a, M);
+    return launch_tc_n<16>(u, a, M);
+}
 
 lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H, int W, bf16 *y, int yc, int yo,
                 bool forward, const bf16 *gate = nullptr, int gc = 0, int go = 0, float *yf = nullptr, int yfc = 0) {
@@ -549,6 +783,7 @@ lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H
         a.relu = 0;
     }
     const long long M = (long long)n * H * W;
+    if (!yf && a.cout % 16 == 0 && a.cin % 16 == 0) return conv_tc(u, a, M);
     dim3 grid(nblk(M, CBM), nblk(a.cout, CBN));
     if (a.cin % 32 == 0) k_conv<32><<<grid, 256, 0, u->stream>>>(a);
     else k_conv<16><<<grid, 256, 0, u->stream>>>(a);
@@ -763,7 +998,8 @@ lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch,
         if (st == LBM_OK) st = ualloc(u, p, n);
     };
     if ((st = ualloc(u, &u->p, off)) || (st = ualloc(u, &u->m, off)) || (st = ualloc(u, &u->v, off)) ||
-        (st = ualloc(u, &u->g, off)) || (st = ualloc(u, &u->yf, P1 * 3)) || (st = ualloc(u, &u->loss, 1))) {
+        (st = ualloc(u, &u->g, off)) || (st = ualloc(u, &u->yf, P1 * 3)) || (st = ualloc(u, &u->loss, 1)) ||
+        (st = ualloc(u, &u->tc_err, 1))) {
         lbm_unet_destroy(u);
         return ufail(nullptr, st, "device allocation failed");
     }
@@ -788,6 +1024,7 @@ lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch,
     cudaError_t e = cudaMemsetAsync(u->p, 0, off * 4, u->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, off * 4, u->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, off * 4, u->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->tc_err, 0, sizeof(int), u->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
     if (e != cudaSuccess) {
         lbm_unet_destroy(u);
@@ -822,6 +1059,16 @@ lbm_status lbm_unet_set_params(lbm_unet *u, const float *host) {
     return LBM_OK;
 }
 
+// a tcgen05 convolution whose bounded wait expired (reported at the next
+// synchronising call)
+static lbm_status check_tc(lbm_unet *u) {
+    int flag = 0;
+    U_CUDA(u, cudaMemcpyAsync(&flag, u->tc_err, sizeof(int), cudaMemcpyDeviceToHost, u->stream));
+    U_CUDA(u, cudaStreamSynchronize(u->stream));
+    if (flag) return ufail(u, LBM_ERR_TIMEOUT, "tensor-core convolution: a bounded wait expired");
+    return LBM_OK;
+}
+
 static lbm_status copy_out(lbm_unet *u, const float *dev, float *host) {
     std::vector<float> pad(u->nparam);
     U_CUDA(u, cudaMemcpyAsync(pad.data(), dev, pad.size() * 4, cudaMemcpyDeviceToHost, u->stream));
@@ -840,6 +1087,8 @@ static lbm_status copy_out(lbm_unet *u, const float *dev, float *host) {
 
 lbm_status lbm_unet_get_params(lbm_unet *u, float *host) {
     if (!u || !host) return ufail(u, LBM_ERR_ARG, "NULL argument");
+    lbm_status st = check_tc(u);
+    if (st != LBM_OK) return st;
     return copy_out(u, u->p, host);
 }
 
@@ -859,6 +1108,7 @@ lbm_status lbm_unet_grad(lbm_unet *u, const float *x_dev, const float *t_dev, co
     lbm_status st = forward(u, x_dev, n);
     if (st == LBM_OK) st = backward(u, t_dev, m_dev, n, scale);
     if (st != LBM_OK) return st;
+    if ((st = check_tc(u)) != LBM_OK) return st;
     if (loss_host) {
         U_CUDA(u, cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->stream));
         U_CUDA(u, cudaStreamSynchronize(u->stream));
