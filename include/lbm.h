@@ -262,6 +262,8 @@ void lbm_batch_destroy(lbm_batch *b);
  * All *_dev pointers are device arrays of n * H * W pixels. */
 typedef struct lbm_unet lbm_unet;
 
+/* H, W multiples of 8; 1 <= cin <= 16; max_batch * H <= 65535.  stream: the
+ * cudaStream_t every call runs on (NULL: the library makes one). */
 lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch, void *stream, lbm_unet **out);
 int64_t lbm_unet_num_params(const lbm_unet *u);
 lbm_status lbm_unet_set_params(lbm_unet *u, const float *host);  /* resets Adam */

@@ -494,18 +494,34 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
 }
 
 // ------------------------------------------------------------- small kernels
-// bias gradient: db[c] += sum_p dz[p][c]; block = 256 pixels x all channels
-__global__ void k_bias_grad(const bf16 *dz, int dzc, int dzo, int C, long long P, float *db) {
-    const int c = threadIdx.x;
-    if (c >= C) return;
-    const long long p0 = (long long)blockIdx.x * 256;
-    float s = 0.f;
-    for (int i = 0; i < 256; ++i) {
-        const long long p = p0 + i;
-        if (p >= P) break;
-        s += __bfloat162float(dz[p * dzc + dzo + c]);
+// bias gradient: db[c] += sum_p dz[p][c].  A block of 8 x 32 threads takes
+// 32 channels of a chunk of kBiasChunk pixels: a warp reads 32 adjacent
+// channels of one pixel, each thread keeps four independent sums over every
+// 8th pixel, the 8 rows meet in shared memory, one atomic per channel.
+constexpr int kBiasChunk = 512;
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16 *dz, int dzc, int dzo, int C, long long P, float *db) {
+    const int cl = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int c = blockIdx.y * 32 + cl;
+    const long long p0 = (long long)blockIdx.x * kBiasChunk;
+    const long long p1 = p0 + kBiasChunk < P ? p0 + kBiasChunk : P;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c < C) {
+        long long p = p0 + row;
+        for (; p + 24 < p1; p += 32) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += __bfloat162float(dz[(p + 8 * k) * dzc + dzo + c]);
+        }
+        for (; p < p1; p += 8) s[0] += __bfloat162float(dz[p * dzc + dzo + c]);
     }
-    atomicAdd(db + c, s);
+    __shared__ float sh[8][32];
+    sh[row][cl] = (s[0] + s[1]) + (s[2] + s[3]);
+    __syncthreads();
+    if (row == 0 && c < C) {
+        float t = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) t += sh[r][cl];
+        atomicAdd(db + c, t);
+    }
 }
 
 // 2x2 average pooling: y[n][i][j] = mean of x[n][2i..2i+1][2j..2j+1]
@@ -543,15 +559,18 @@ __global__ void k_pool_back(const bf16 *dy, int dyc, int dyo, const bf16 *gate, 
 }
 
 // nearest 2x upsampling: y[n][i][j] = x[n][i/2][j/2]
+// grid (ceil(W * C / 8 / 256), N * H): blockIdx.y is an output row, a thread
+// moves 8 channels (16 bytes; C, xc, yc, xo, yo multiples of 8)
 __global__ void k_up(const bf16 *x, int xc, int xo, bf16 *y, int yc, int yo, int N, int H, int W, int C) {
     // H, W: fine (output) sizes
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)N * H * W * C;
-    if (idx >= total) return;
-    const int c = (int)(idx % C);
-    const long long p = idx / C;
-    const int j = (int)(p % W), i = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
-    y[p * yc + yo + c] = x[((long long)(n * (H / 2) + i / 2) * (W / 2) + j / 2) * xc + xo + c];
+    const int C8 = C >> 3;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= W * C8) return;
+    const int row = blockIdx.y, n = row / H, i = row - n * H;
+    const int j = t / C8, c = (t - j * C8) * 8;
+    const long long p = (long long)row * W + j;
+    const long long q = ((long long)(n * (H / 2) + i / 2) * (W / 2) + j / 2);
+    *reinterpret_cast<uint4 *>(y + p * yc + yo + c) = *reinterpret_cast<const uint4 *>(x + q * xc + xo + c);
 }
 
 // upsampling backward at the coarse resolution, gated by the coarse activation
@@ -812,7 +831,8 @@ lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, in
     dim3 grid(nblk(P, a.pix), nblk(l.coutp, WBM), 9 * ((l.cinp + WBN - 1) / WBN));
     k_wgrad<<<grid, 128, 0, u->stream>>>(a);
     U_CUDA(u, cudaGetLastError());
-    k_bias_grad<<<nblk(P, 256), ((l.coutp + 31) / 32) * 32, 0, u->stream>>>(dz, dzc, 0, l.cout, P, u->g + l.boff);
+    k_bias_grad<<<dim3(nblk(P, kBiasChunk), (l.cout + 31) / 32), 256, 0, u->stream>>>(dz, dzc, 0, l.cout, P,
+                                                                                     u->g + l.boff);
     U_CUDA(u, cudaGetLastError());
     return LBM_OK;
 }
@@ -847,15 +867,15 @@ lbm_status forward(lbm_unet *u, const float *xin, int n) {
     k_pool<<<nblk((long long)n * H8 * W8 * 128, 256), 256, 0, u->stream>>>(u->cat3, 256, 128, u->p3, 128, 0, n, H4, W4, 128);
     FW(BA, u->p3, 128, 0, H8, W8, u->ba, 256, 0);
     FW(BB, u->ba, 256, 0, H8, W8, u->bb, 256, 0);
-    k_up<<<nblk((long long)n * H4 * W4 * 256, 256), 256, 0, u->stream>>>(u->bb, 256, 0, u->u3in, 256, 0, n, H4, W4, 256);
+    k_up<<<dim3(nblk((long long)W4 * 256 / 8, 256), n * H4), 256, 0, u->stream>>>(u->bb, 256, 0, u->u3in, 256, 0, n, H4, W4, 256);
     FW(U3, u->u3in, 256, 0, H4, W4, u->cat3, 256, 0);
     FW(D3A, u->cat3, 256, 0, H4, W4, u->d3a, 128, 0);
     FW(D3B, u->d3a, 128, 0, H4, W4, u->d3, 128, 0);
-    k_up<<<nblk((long long)n * H2 * W2 * 128, 256), 256, 0, u->stream>>>(u->d3, 128, 0, u->u2in, 128, 0, n, H2, W2, 128);
+    k_up<<<dim3(nblk((long long)W2 * 128 / 8, 256), n * H2), 256, 0, u->stream>>>(u->d3, 128, 0, u->u2in, 128, 0, n, H2, W2, 128);
     FW(U2, u->u2in, 128, 0, H2, W2, u->cat2, 128, 0);
     FW(D2A, u->cat2, 128, 0, H2, W2, u->d2a, 64, 0);
     FW(D2B, u->d2a, 64, 0, H2, W2, u->d2, 64, 0);
-    k_up<<<nblk((long long)n * H * W * 64, 256), 256, 0, u->stream>>>(u->d2, 64, 0, u->u1in, 64, 0, n, H, W, 64);
+    k_up<<<dim3(nblk((long long)W * 64 / 8, 256), n * H), 256, 0, u->stream>>>(u->d2, 64, 0, u->u1in, 64, 0, n, H, W, 64);
     FW(U1, u->u1in, 64, 0, H, W, u->cat1, 64, 0);
     FW(D1A, u->cat1, 64, 0, H, W, u->d1a, 32, 0);
     FW(D1B, u->d1a, 32, 0, H, W, u->d1, 32, 0);
@@ -955,6 +975,7 @@ lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch,
     if (H < 8 || W < 8 || H % 8 || W % 8 || max_batch < 1)
         return ufail(nullptr, LBM_ERR_ARG, "H and W must be multiples of 8 (>= 8), max_batch >= 1");
     if (cin < 1 || cin > 16) return ufail(nullptr, LBM_ERR_ARG, "cin must be in [1, 16]");
+    if ((long long)max_batch * H > 65535) return ufail(nullptr, LBM_ERR_ARG, "max_batch * H must be <= 65535");
     if (periodic_x != 0 && periodic_x != 1) return ufail(nullptr, LBM_ERR_ARG, "periodic_x must be 0 or 1");
     lbm_unet *u = new lbm_unet();
     u->H = H;
