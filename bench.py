@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch", "surrogate", "precision"],
+    ap.add_argument("--workload", default="kolmogorov", choices=["kolmogorov", "batch", "surrogate", "precision", "unet"],
                     help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady "
                          "state; surrogate: learned warm start of obstacle channels vs cold start; "
                          "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
@@ -596,6 +596,58 @@ def run_surrogate(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_unet(args, ws, rank, local):
+    """Training steps of the surrogate network alone (the warm start's 128 x 256
+    channels, batch 8, eight input channels, periodic along x): forward, loss,
+    backward and Adam, all in the library's kernels, on seeded synthetic
+    tensors; TFLOP/s against the measured sustained BF16 peak."""
+    import torch
+
+    import paper_2212_07494_gb300 as P
+    import paper_2212_07494_gb300.surrogate as S
+
+    torch.cuda.set_device(local)
+    H, Wd, B = 128, 256, 8
+    stream = torch.cuda.Stream(device=local)
+    g = torch.Generator(device=f"cuda:{local}")
+    g.manual_seed(2212074945)
+    with torch.cuda.stream(stream):
+        net = P.UNet(H, Wd, B, stream.cuda_stream, cin=S.NF, periodic_x=True)
+        net.set_params(S.init_params(S.ARCH, 2212074946))
+        x = torch.randn(B, H, Wd, S.NF, device=f"cuda:{local}", generator=g)
+        t = torch.randn(B, H, Wd, 3, device=f"cuda:{local}", generator=g)
+        m = torch.ones(B, H, Wd, device=f"cuda:{local}")
+        ld = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
+        scale = 1.0 / (3 * B * H * Wd)
+        for _ in range(max(args.warmup, 3)):
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, scale, 1e-4, ld.data_ptr())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, scale, 1e-4, ld.data_ptr())
+        e1.record(stream)
+    torch.cuda.synchronize()
+    net.params()   # a synchronising call: reports a tensor-core wait that expired
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = S.train_flops_per_sample(H, Wd) * B
+    tf = flops / (ms * 1e-3) / 1e12
+    peak = 1695.8
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"])
+    except Exception:
+        pass
+    net.close()
+    line = {"metric": "surrogate training throughput", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "unet_train_step_128x256_batch8", "H": H, "W": Wd, "batch": B, "cin": S.NF,
+                       "flops_per_step": flops},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "traffic": None, "peak_source": "measured bf16_tflops_sustained"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_precision(args, ws, rank, local):
     """Storage precision: the 4096^2 Kolmogorov flow (D2Q9 SMRT, 10000 steps)
     and the 256^3 Taylor-Green vortex (D3Q27 SMRT, Re 1600, 5000 steps) in
@@ -667,6 +719,8 @@ def main():
         run_surrogate(args, ws, rank, local)
     elif args.workload == "precision":
         run_precision(args, ws, rank, local)
+    elif args.workload == "unet":
+        run_unet(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
 
