@@ -58,6 +58,11 @@ def parse():
                     help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady "
                          "state; surrogate: learned warm start of obstacle channels vs cold start; "
                          "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
+    ap.add_argument("--storage", default="F32", choices=["F32", "F16", "BF16"],
+                    help="kolmogorov: storage of the populations (F32 is the benchmark configuration)")
+    ap.add_argument("--channels", type=int, default=512, help="batch: number of channels (512: the benchmark)")
+    ap.add_argument("--tune-only", action="store_true",
+                    help="batch: autotune the tiles, print the chosen shape and stop (a short run for profilers)")
     ap.add_argument("--tgv-n", type=int, default=256)
     ap.add_argument("--tgv-steps", type=int, default=5000)
     ap.add_argument("--kol-steps", type=int, default=10000)
@@ -285,7 +290,8 @@ def run_gpu(args, ws, rank, local):
     wl = W.kolmogorov(n=n)
     stream = torch.cuda.Stream(device=local)
     N = n * n
-    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, "F32", (1, 1, 1), g=wl.g, force_kind="rows",
+    st = args.storage
+    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, st, (1, 1, 1), g=wl.g, force_kind="rows",
                     u0=wl.u0, torch_stream=stream)
     D, Q, _, bytes_per_node = lat.info()
     C = max(1, args.check_every)
@@ -335,24 +341,30 @@ def run_gpu(args, ws, rank, local):
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_node * N
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = traffic_per_launch(N)
+    traffic = traffic_per_launch(N) if st == "F32" else None
     clocks = sampler.summary()
     launches = chunks * (C + 2)
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(P, torch, wl, n, steps, C, local, ws, dist)
+        e2e = run_e2e(P, torch, wl, n, steps, C, local, ws, dist, st)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
             "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "D2Q9", "collision": "SMRT", "storage": "F32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if st == "F32" else f"{st.lower()} storage, f32 arithmetic",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if st == "F32" else WORKLOAD.replace("_f32_", f"_{st.lower()}_"),
+                       "lattice": "D2Q9", "collision": "SMRT", "storage": st,
                        "nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)",
-                       "check_every": C, "l2": "inputs larger than L2 (two 604 MB population buffers)",
+                       "check_every": C,
+                       "l2": (f"inputs larger than L2 (two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers)"
+                              if N * Q * (4 if st == 'F32' else 2) > 129e6 else
+                              f"two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers fit in L2: "
+                              "a small case for profilers, not a bench line"),
                        "replicas": ws},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_step<D2Q9,SMRT,F32>", "bytes_per_launch": algo_bytes,
+                         "kernel": f"k_step<D2Q9,SMRT,{st}>", "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,
             "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res}}
@@ -366,7 +378,7 @@ def run_gpu(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def run_e2e(P, torch, wl, n, steps, C, local, ws, dist):
+def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32"):
     """Whole job through the public API from pinned host memory: create (H2D of
     the initial velocity and force), run with a host-read residual every C
     steps, read rho and u back (D2H)."""
@@ -380,7 +392,7 @@ def run_e2e(P, torch, wl, n, steps, C, local, ws, dist):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, "F32", (1, 1, 1), g=g.numpy(), force_kind="rows",
+    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, storage, (1, 1, 1), g=g.numpy(), force_kind="rows",
                     u0=u0.numpy())
     r = None
     for _ in range(steps // C):
@@ -408,11 +420,18 @@ def run_batch(args, ws, rank, local):
     import paper_2212_07494_gb300 as P
 
     torch.cuda.set_device(local)
-    chans = W.batch_channels()
+    chans = W.batch_channels(n=args.channels)
     spec = [{"shape": (c.nx, c.ny, 1), "tau": (1.0, 1.0, c.tau2, 1.0, 1.0), "periodic": (1, 0, 1),
              "g": [c.gx, 0.0]} for c in chans]
     b = P.Batch(spec, "SMRT", "F32")
     block, tile, ms_tune = b.autotune(200)
+    if args.tune_only:
+        b.close()
+        if rank == 0:
+            print(json.dumps({"metric": "batch tile autotune", "value": ms_tune, "unit": "ms per step",
+                              "higher_is_better": False, "config": {"workload": f"batched_channels_{len(spec)}",
+                                                                     "block": block, "tile_nodes": tile}}))
+        return
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     status, steps, st, r = b.run_to_steady(args.tol, args.K, max_steps=50_000_000)
