@@ -715,6 +715,20 @@ def run_precision(args, ws, rank, local):
                                           rho0=tg.rho0, u0=tg.u0, torch_stream=stream), tg.steps)
     tgv19 = run("tgv19", lambda st: P.Lattice("D3Q19", "SMRT", tg.shape, tg.tau, st, tg.periodic, g=tg.g,
                                               rho0=tg.rho0, u0=tg.u0, torch_stream=stream), tg.steps)
+    # the FP64 oracle on the host cores, as a baseline per 3-D lattice: 3 steps on
+    # a 256 x 256 x 4 periodic slab of the same vortex
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    cpu = {}
+    for name, lat in (("D3Q27", O.D3Q27), ("D3Q19", O.D3Q19)):
+        sl = (slice(0, 4), slice(None), slice(None))
+        orc = O.Sim(lat, O.SMRT, (args.tgv_n, args.tgv_n, 4), (1, 1, 1), tg.tau, g=tg.g,
+                    rho0=np.ascontiguousarray(tg.rho0[sl]), u0=np.ascontiguousarray(tg.u0[(slice(None),) + sl]))
+        t0 = time.perf_counter()
+        orc.step(3)
+        dt = time.perf_counter() - t0
+        cpu[name] = {"value": args.tgv_n * args.tgv_n * 4 * 3 / dt / 1e6, "unit": "MLUPS", "cores": cores,
+                     "kind": "oracle", "sample": f"3 FP64 oracle steps on a {args.tgv_n} x {args.tgv_n} x 4 periodic slab"}
     line = {"metric": "MLUPS and % of HBM roofline per lattice, with velocity error vs FP64 per storage mode",
             "value": tgv["F16"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.tgv_steps, "warmup": 0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 arithmetic",
@@ -722,7 +736,8 @@ def run_precision(args, ws, rank, local):
             "config": {"workload": "precision_modes", "kolmogorov": {"n": args.n, "steps": args.kol_steps},
                        "tgv3d": {"n": args.tgv_n, "steps": args.tgv_steps, "Re": 1600, "U0": 0.05,
                                  "tau2": tg.tau[2], "lattice": "D3Q27"}},
-            "kolmogorov_d2q9_smrt": kol, "tgv_d3q27_smrt": tgv, "tgv_d3q19_smrt": tgv19, "peak_gbs": peak}
+            "kolmogorov_d2q9_smrt": kol, "tgv_d3q27_smrt": tgv, "tgv_d3q19_smrt": tgv19, "peak_gbs": peak,
+            "cpu_baseline_3d": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
