@@ -197,16 +197,11 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
 
 // ------------------------------------------- convolution on tcgen05 (TMEM)
 // The same implicit GEMM as k_conv on the 5th-generation tensor cores: a CTA
-// of 4 warps computes 128 pixels x NT output channels, accumulating in TMEM
-// (128 lanes x NT FP32 columns).  Operand tiles are staged by cp.async into
-// shared memory in the K-major layout without swizzle that the MMA reads
-// through matrix descriptors: 8-row x 16-byte core matrices, adjacent along
-// K at TC_KSTEP bytes, adjacent 8-row groups at (BK / 8) * TC_KSTEP bytes.
-// One thread issues the MMAs of a K block (BK / 16 instructions of K = 16)
-// and commits them to the stage's mbarrier; a stage is refilled once that
-// barrier shows its MMAs done.  Every wait is bounded: on expiry the CTA sets
-// *err, skips the rest (uniformly across the CTA), frees its TMEM and
-// returns.
+// computes 128 pixels x NT output channels, accumulating in TMEM (128 lanes x
+// NT FP32 columns).  Operand tiles are staged by cp.async into shared memory
+// in the K-major layout without swizzle that the MMA reads through matrix
+// descriptors: 8-row x 16-byte core matrices, adjacent along K at TC_KSTEP
+// bytes, adjacent 8-row groups at (BK / 8) * TC_KSTEP bytes.
 constexpr int TC_KSTEP = 128;
 constexpr long TC_SPIN = 1L << 22;
 
@@ -221,7 +216,20 @@ __device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsign
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ bool tc_wait(unsigned long long *mbar, unsigned parity) {
+
+// k_conv_ws: the convolution, warp-specialised, 5 warps.  Warps 0-3
+// are producers, warp w owning stage w (K blocks kb = w, w + 4, ...): it
+// waits until the MMAs that last read its stage are done (empty[w]), fills
+// the stage with cp.async, waits for its own copies only, fences them into
+// the async proxy and arrives on full[w].  Warp 4 issues the MMAs: for each
+// K block it waits full[s], issues BK / 16 MMAs and commits them to empty[s];
+// after the last block it commits to done.  Then warps 0-3 read their TMEM
+// lane quarter for the epilogue.  Four stages are in flight, and no thread
+// waits on copies it did not issue.  Every wait is bounded and gives up when
+// another thread has failed (s_fail).
+constexpr int WS_S = 4;
+
+__device__ __forceinline__ bool ws_wait(unsigned long long *mbar, unsigned parity, volatile int *fail) {
     for (long it = 0; it < TC_SPIN; ++it) {
         unsigned ok;
         asm volatile(
@@ -233,65 +241,52 @@ __device__ __forceinline__ bool tc_wait(unsigned long long *mbar, unsigned parit
             : "r"(smem_addr(mbar)), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (*fail) return false;
         if (it > 64) __nanosleep(32);
     }
+    *fail = 1;
     return false;
 }
 
 template <int BK, int NT>
-__global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a, int *err) {
+__global__ void __launch_bounds__(160) k_conv_ws(const ConvArgs a, int *err) {
     constexpr int ABYTES = 128 * BK * 2, BBYTES = NT * BK * 2, STAGE = ABYTES + BBYTES;
     constexpr int RGRP = (BK / 8) * TC_KSTEP;
     constexpr int NCOL = NT < 32 ? 32 : NT;
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) unsigned long long mbar[2];
+    constexpr int CH = BK / 8;  // 16-byte chunks per tile row
+    extern __shared__ __align__(1024) unsigned char ws_smem[];
+    __shared__ __align__(8) unsigned long long full[WS_S], empty[WS_S], done;
     __shared__ unsigned tmem_base;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
+    __shared__ int s_rows[128][3];  // (image, y, x) of the tile's pixels; image -1 past the end
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char *sm = (unsigned char *)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+    unsigned char *sm = (unsigned char *)(((uintptr_t)ws_smem + 1023) & ~(uintptr_t)1023);
     const long long M = (long long)a.N * a.H * a.W;
     const long long m0 = (long long)blockIdx.x * 128;
     const int co0 = blockIdx.y * NT;
-    // this thread's A row (one pixel)
-    const long long mrow = m0 + tid;
-    int an = -1, ay = 0, ax = 0;
-    if (mrow < M) {
-        const int hw = a.H * a.W;
-        an = (int)(mrow / hw);
-        const int r = (int)(mrow - (long long)an * hw);
-        ay = r / a.W;
-        ax = r - ay * a.W;
-    }
     const int cblocks = a.cin / BK;
     const int KB = 9 * cblocks;
-    auto load = [&](int kb, int buf) {
-        const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        unsigned char *sa = sm + buf * STAGE, *sb = sa + ABYTES;
-        {
-            const int yy = ay + dy;
-            int xx = ax + dx;
-            if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
-            const bool ok = an >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = ok ? a.x + ((long long)(an * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 : a.x;
-#pragma unroll
-            for (int cc = 0; cc < BK / 8; ++cc)
-                cp_async16(sa + (tid >> 3) * RGRP + cc * TC_KSTEP + (tid & 7) * 16, ok ? src + cc * 8 : a.x, ok);
+    if (tid < 128) {
+        const long long m = m0 + tid;
+        int an = -1, ay = 0, ax = 0;
+        if (m < M) {
+            const int hw = a.H * a.W;
+            an = (int)(m / hw);
+            const int r = (int)(m - (long long)an * hw);
+            ay = r / a.W;
+            ax = r - ay * a.W;
         }
-#pragma unroll
-        for (int q = tid; q < NT * (BK / 8); q += 128) {
-            const int r = q / (BK / 8), cc = q % (BK / 8);
-            const int co = co0 + r;
-            const bool ok = co < a.wrows;
-            const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + cc * 8 : a.w;
-            cp_async16(sb + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, src, ok);
-        }
-        cp_async_commit();
-    };
+        s_rows[tid][0] = an;
+        s_rows[tid][1] = ay;
+        s_rows[tid][2] = ax;
+    }
     if (tid == 0) {
         s_fail = 0;
-        for (int s = 0; s < 2; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[s])), "r"(1));
+        for (int s = 0; s < WS_S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[s])), "r"(32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&done)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -303,24 +298,50 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a, int *err) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem = tmem_base;
-    constexpr uint32_t IDESC = tc_idesc(128, NT);
-    bool fail = false;
-    load(0, 0);
-    for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb & 1;
-        if (kb + 1 < KB) {
-            // the MMAs of kb - 1 read stage s ^ 1: wait for them before refilling it
-            if (kb >= 1 && !tc_wait(&mbar[s ^ 1], ((kb - 1) >> 1) & 1)) fail = true;
-            if (!fail) load(kb + 1, s ^ 1);
-            cp_async_wait<1>();
-        } else {
+    if (warp < WS_S) {
+        // ---- producer of stage `warp`: lane l copies tile rows l + 32 i
+        // (pixel coordinates from s_rows) and the weight rows l + 32 i
+        unsigned char *sa = sm + warp * STAGE, *sb = sa + ABYTES;
+        for (int kb = warp, j = 0; kb < KB; kb += WS_S, ++j) {
+            if (j >= 1 && !ws_wait(&empty[warp], (j - 1) & 1, &s_fail)) break;
+            const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = lane + 32 * i;
+                const int an = s_rows[r][0];
+                const int yy = s_rows[r][1] + dy;
+                int xx = s_rows[r][2] + dx;
+                if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+                const bool ok = an >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                const bf16 *src = ok ? a.x + ((long long)(an * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 : a.x;
+#pragma unroll
+                for (int cc = 0; cc < CH; ++cc)
+                    cp_async16(sa + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, ok ? src + cc * 8 : a.x, ok);
+            }
+#pragma unroll 4
+            for (int q = lane; q < NT * CH; q += 32) {
+                const int r = q / CH, cc = q % CH;
+                const int co = co0 + r;
+                const bool ok = co < a.wrows;
+                const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + cc * 8 : a.w;
+                cp_async16(sb + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, src, ok);
+            }
+            cp_async_commit();
             cp_async_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                smem_addr(&full[warp]))
+                         : "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (fail) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        if (tid == 0) {
+        cp_async_wait<0>();
+    } else if (lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t IDESC = tc_idesc(128, NT);
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int s = kb % WS_S;
+            if (!ws_wait(&full[s], (kb / WS_S) & 1, &s_fail)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const unsigned sa = smem_addr(sm + s * STAGE), sb = sa + ABYTES;
 #pragma unroll
@@ -336,56 +357,58 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a, int *err) {
                     "l"(da), "l"(db), "r"(IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&mbar[s])));
+                smem_addr(&empty[s])));
+        }
+        // done completes when every MMA issued above has (after a failure: the
+        // ones issued before it)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&done)));
+    }
+    if (warp < WS_S) {
+        const bool ok = ws_wait(&done, 0, &s_fail) && !s_fail;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            // warp w holds TMEM lanes 32w .. 32w + 31: one pixel per thread
+            const long long m = m0 + warp * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < NT; c += 16) {
+                unsigned r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int cb = co0 + c;
+                if (m >= M || cb >= a.cout) continue;
+                float v[16];
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    v[jj] = __uint_as_float(r[jj]);
+                    if (a.bias && cb + jj < a.cout) v[jj] += a.bias[cb + jj];
+                    if (a.relu) v[jj] = fmaxf(v[jj], 0.f);
+                }
+                if (a.gate) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        if (cb + jj < a.cout && !(__bfloat162float(a.gate[m * a.gc + a.go + cb + jj]) > 0.f)) v[jj] = 0.f;
+                }
+                bf16 *dst = a.y + m * a.yc + a.yo + cb;
+                if (cb + 16 <= a.cout) {
+                    __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) o[jj] = __floats2bfloat162_rn(v[2 * jj], v[2 * jj + 1]);
+                    reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                    reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+                } else {
+                    for (int jj = 0; jj < 16 && cb + jj < a.cout; ++jj) dst[jj] = __float2bfloat16_rn(v[jj]);
+                }
+            }
         }
     }
-    cp_async_wait<0>();
-    // the last commit covers every MMA of this CTA
-    if (!s_fail && !tc_wait(&mbar[(KB - 1) & 1], ((KB - 1) >> 1) & 1)) fail = true;
-    if (fail) s_fail = 1;
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!s_fail) {
-        // warp w holds TMEM lanes 32w .. 32w + 31: one pixel per thread
-        const long long m = m0 + warp * 32 + lane;
-#pragma unroll
-        for (int c = 0; c < NT; c += 16) {
-            unsigned r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int cb = co0 + c;
-            if (m >= M || cb >= a.cout) continue;
-            float v[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                v[j] = __uint_as_float(r[j]);
-                if (a.bias && cb + j < a.cout) v[j] += a.bias[cb + j];
-                if (a.relu) v[j] = fmaxf(v[j], 0.f);
-            }
-            if (a.gate) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (cb + j < a.cout && !(__bfloat162float(a.gate[m * a.gc + a.go + cb + j]) > 0.f)) v[j] = 0.f;
-            }
-            bf16 *dst = a.y + m * a.yc + a.yo + cb;
-            if (cb + 16 <= a.cout) {
-                __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) o[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
-                reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
-            } else {
-                for (int j = 0; j < 16 && cb + j < a.cout; ++j) dst[j] = __float2bfloat16_rn(v[j]);
-            }
-        }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
-    }
+    if (tid == 0 && s_fail) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
@@ -729,11 +752,11 @@ lbm_status ualloc(lbm_unet *u, T **p, size_t count) {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// dynamic shared memory of k_conv_tc<BK, NT>: two stages plus alignment
+// dynamic shared memory of k_conv_ws<BK, NT>: WS_S stages plus alignment
 // slack, and at least enough that no more CTAs fit on an SM than its 512
 // TMEM columns serve (tcgen05.alloc of a CTA beyond them would wait)
 template <int BK, int NT> size_t tc_smem_bytes() {
-    const size_t need = 2 * (size_t)(128 * BK + NT * BK) * 2 + 1024;
+    const size_t need = WS_S * (size_t)(128 * BK + NT * BK) * 2 + 1024;
     const int ncol = NT < 32 ? 32 : NT;
     const size_t floor_ = 233472 / (512 / ncol + 1) - 1024 + 1;
     return need > floor_ ? need : floor_;
@@ -743,11 +766,11 @@ template <int BK, int NT> lbm_status launch_tc(lbm_unet *u, const ConvArgs &a, l
     static bool attr = false;
     const size_t smem = tc_smem_bytes<BK, NT>();
     if (!attr) {
-        U_CUDA(u, cudaFuncSetAttribute(k_conv_tc<BK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        U_CUDA(u, cudaFuncSetAttribute(k_conv_ws<BK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     dim3 grid(nblk(M, 128), nblk(a.cout, NT));
-    k_conv_tc<BK, NT><<<grid, 128, smem, u->stream>>>(a, u->tc_err);
+    k_conv_ws<BK, NT><<<grid, 160, smem, u->stream>>>(a, u->tc_err);
     U_CUDA(u, cudaGetLastError());
     return LBM_OK;
 }
