@@ -20,7 +20,11 @@
  *  - tau values are the tau-hat of Eq. (explict_eq): tau_hat = tau + 1/2.
  *  - SMRT uses one relaxation time per Hermite order (tau_nk = tau_n).
  *  - the force keeps only its equilibrium part in the co-moving frame:
- *    d_F^(1) = rho g, d_F^(n>=2) = 0 (Sec. II.C, after Eq. Frc).
+ *    d_F^(1) = rho g, d_F^(n>=2) = 0 (Sec. II.C, after Eq. Frc).  The third
+ *    collision mode (OR_SMRT_FNEQ) keeps the non-equilibrium parts as well,
+ *    d_F^(n) = n g d^(n-1) for n <= 4 (Eq. Frc, third and fourth terms), with
+ *    d^(n-1) the moments of f itself, recovered from those of fbar by
+ *    inverting Eq. (newf) order by order.
  *  - retained Hermite components per lattice: D2Q9/D3Q27 keep components with
  *    per-axis multiplicity <= 2 and order <= 4; D3Q19 keeps orders <= 2 and
  *    the six (2,1,0) third-order components.  D3Q19 is a degree-5 rule, so a
@@ -50,7 +54,7 @@
 #define OR_PACK 121 /* 1 + 3 + 9 + 27 + 81 for D = 3 */
 
 enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
-enum { OR_BGK = 0, OR_SMRT = 1 };
+enum { OR_BGK = 0, OR_SMRT = 1, OR_SMRT_FNEQ = 2 };
 
 typedef struct {
     int id, D, Q;
@@ -322,12 +326,24 @@ static void collide_bgk(const or_lattice *L, const double *tau, const double *de
     }
 }
 
-static void collide_smrt(const or_lattice *L, const double *tau, const double *dev,
+/* Order-n force coefficients in the co-moving frame, d_F^(n) = n g d^(n-1)
+ * (the definition after Eq. Frc at theta = 1): the symmetric product of g
+ * and d^(n-1) summed over the n positions g can take. */
+static void force_order(const or_lattice *L, int n, const double *g, const double *d, double *dF)
+{
+    for (int k = L->off[n]; k < L->off[n + 1]; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += g[L->dig[k][j]] * d[L->rest[k][1 << j]];
+        dF[k] = acc;
+    }
+}
+
+static void collide_smrt(const or_lattice *L, const double *tau, int fneq, const double *dev,
                          const double *gL, double *dpop, double *dbg)
 {
     double drho, rho, u[3], g[3], mu[3];
     double abar[OR_PACK], a0[OR_PACK], a1[OR_PACK], d1[OR_PACK], dp[OR_PACK], ap[OR_PACK];
-    double tot[OR_PACK];
+    double tot[OR_PACK], dF[OR_PACK], d[OR_PACK];
     const int P = L->off[OR_MAXN + 1];
     macroscopic(L, dev, gL, &drho, &rho, u, g);
     for (int k = 0; k < 3; ++k) mu[k] = -u[k];
@@ -340,16 +356,30 @@ static void collide_smrt(const or_lattice *L, const double *tau, const double *d
     for (int k = 0; k < P; ++k) a1[k] = abar[k] - a0[k];
     a1[0] = 0.0;
     shift(L, mu, a1, d1);                   /* RM -> RCM */
+    /* force coefficients.  d_F^(1) = rho g always.  With the non-equilibrium
+     * contributions, d_F^(n) = n g d^(n-1) needs the central moments d of f
+     * (not fbar): d^(0) = rho, d^(1) = 0 (mass and momentum), and for n >= 2
+     * Eq. (newf) in moment form, d_1bar^(n) = (tau_n/(tau_n - 1/2)) d^(n)
+     * - d_F^(n)/2 with tau_n the tau-hat of the update, inverts to
+     * d^(n) = (1 - 1/(2 tau_n)) (d_1bar^(n) + d_F^(n)/2).  Each order needs
+     * only the one below it. */
+    for (int k = 0; k < P; ++k) { dF[k] = 0.0; d[k] = 0.0; }
+    d[0] = rho;
+    for (int k = 0; k < L->D; ++k) dF[L->off[1] + k] = rho * g[k];
+    if (fneq) {
+        for (int n = 2; n <= OR_MAXN; ++n) {
+            force_order(L, n, g, d, dF);
+            for (int k = L->off[n]; k < L->off[n + 1]; ++k)
+                d[k] = (1.0 - 0.5 / tau[n]) * (d1[k] + 0.5 * dF[k]);
+        }
+    }
     /* relaxation with the force, order by order (Eq. RHS, explicit form):
-     * d_p^(n) = (1 - 1/tau_n) d_1^(n) + (1 - 1/(2 tau_n)) d_F^(n),
-     * d_F^(1) = rho g, d_F^(n>=2) = 0, d_p^(0) = 0 */
+     * d_p^(n) = (1 - 1/tau_n) d_1^(n) + (1 - 1/(2 tau_n)) d_F^(n), d_p^(0) = 0 */
     dp[0] = 0.0;
     for (int n = 1; n <= OR_MAXN; ++n) {
         const double t = tau[n];
-        for (int k = L->off[n]; k < L->off[n + 1]; ++k) {
-            double dF = (n == 1) ? rho * g[k - L->off[1]] : 0.0;
-            dp[k] = (1.0 - 1.0 / t) * d1[k] + (1.0 - 0.5 / t) * dF;
-        }
+        for (int k = L->off[n]; k < L->off[n + 1]; ++k)
+            dp[k] = (1.0 - 1.0 / t) * d1[k] + (1.0 - 0.5 / t) * dF[k];
     }
     shift(L, u, dp, ap);                    /* RCM -> RM (Eq. bbd1) */
     for (int k = 0; k < P; ++k) tot[k] = a0[k] + ap[k];
@@ -401,12 +431,12 @@ typedef struct {
 
 static int check_params(const or_params *p, or_lattice *L)
 {
-    if (p->lattice < 0 || p->lattice > 2 || p->collision < 0 || p->collision > 1) return -1;
+    if (p->lattice < 0 || p->lattice > 2 || p->collision < 0 || p->collision > 2) return -1;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
     lattice_init(p->lattice, L);
     if (L->D == 2 && p->nz != 1) return -1;
     if (p->collision == OR_BGK && !(p->tau[2] > 0.5)) return -1;
-    if (p->collision == OR_SMRT)
+    if (p->collision != OR_BGK)
         for (int n = 2; n <= 4; ++n)
             if (!(p->tau[n] > 0.5)) return -1;
     return 0;
@@ -490,7 +520,7 @@ int or_collide_node(const or_params *p, const double *fbar, const double *gL, do
     if (check_params(p, &L)) return -1;
     for (int i = 0; i < L.Q; ++i) dev[i] = fbar[i] - L.w[i];
     if (p->collision == OR_BGK) collide_bgk(&L, p->tau, dev, gL, dp);
-    else collide_smrt(&L, p->tau, dev, gL, dp, dbg);
+    else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, dev, gL, dp, dbg);
     for (int i = 0; i < L.Q; ++i) fp[i] = L.w[i] + dp[i];
     return 0;
 }
@@ -555,7 +585,7 @@ int or_step(const or_params *p, const unsigned char *solid, const double *g,
         for (int i = 0; i < L.Q; ++i) fb[i] = f_in[(size_t)i * N + x];
         for (int k = 0; k < L.D; ++k) gL[k] = g ? g[(size_t)k * N + x] : 0.0;
         if (p->collision == OR_BGK) collide_bgk(&L, p->tau, fb, gL, fp);
-        else collide_smrt(&L, p->tau, fb, gL, fp, NULL);
+        else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, fb, gL, fp, NULL);
         const int X = (int)(x % nx), Y = (int)((x / nx) % ny), Z = (int)(x / ((size_t)nx * ny));
         for (int i = 0; i < L.Q; ++i) {
             int t[3] = {X + L.c[i][0], Y + L.c[i][1], Z + L.c[i][2]};

@@ -34,7 +34,7 @@ def _shape(lat, n2=(6, 5), n3=(4, 3, 5)):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
 def test_uniform_state_velocity_grows_by_g(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat)
@@ -52,7 +52,7 @@ def test_uniform_state_velocity_grows_by_g(lat, coll):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
 def test_momentum_grows_by_Mg(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat, (8, 7), (5, 4, 6))
@@ -69,7 +69,7 @@ def test_momentum_grows_by_Mg(lat, coll):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
 def test_mass_conserved_with_walls_and_solids(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat, (12, 9), (6, 5, 4))
@@ -110,12 +110,14 @@ def test_poiseuille_closed_form():
     assert err < 1e-8, err
 
 
-def test_poiseuille_smrt_second_difference():
-    """SMRT in the same channel: the interior profile has the exact viscosity
-    nu = (tau_2 - 1/2)/3, i.e. second difference -g/nu (wall slip depends on
-    tau_3 and is left to the GPU-oracle parity)."""
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ])
+def test_poiseuille_smrt_second_difference(coll):
+    """SMRT in the same channel, with and without the force's non-equilibrium
+    terms: the interior profile has the exact viscosity nu = (tau_2 - 1/2)/3,
+    i.e. second difference -g/nu (wall slip depends on tau_3 and is left to
+    the GPU-oracle parity)."""
     ny = 32
-    s = O.Sim(O.D2Q9, O.SMRT, (4, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1.0, 1.0), g=[1e-6, 0])
+    s = O.Sim(O.D2Q9, coll, (4, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1.0, 1.0), g=[1e-6, 0])
     s.step(20000)
     _, u, _ = s.moments()
     ux = u[0, 0, :, 0]
@@ -125,12 +127,15 @@ def test_poiseuille_smrt_second_difference():
 
 
 @pytest.mark.slow
-def test_taylor_green_second_order():
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ])
+def test_taylor_green_second_order(coll):
+    """Sec. III.A; the non-equilibrium force terms (Eq. Frc) must keep the
+    second-order convergence."""
     cfg = GOLD["taylor_green_2d"]
     errs = []
     for L in cfg["L"]:
         tau, T, uinit, force = W.taylor_green_2d(L, cfg["u0"], cfg["Re"])
-        s = O.Sim(O.D2Q9, O.SMRT, (L, L, 1), tau=(1, 1, tau, 1, 1), g=force(0),
+        s = O.Sim(O.D2Q9, coll, (L, L, 1), tau=(1, 1, tau, 1, 1), g=force(0),
                   force_kind="field", u0=uinit)
         for t in range(T):
             s.set_force(force(t), "field")
