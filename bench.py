@@ -40,7 +40,8 @@ import lbm_workloads as W  # noqa: E402
 METRIC = "MLUPS and % of HBM roofline per lattice"
 UNIT = "MLUPS"
 WORKLOAD = "kolmogorov_d2q9_smrt_f32_4096x4096"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_d2q9_smrt_f32_traffic.json")
+PROFILE_TRAFFIC = {c: os.path.join(ROOT, "profiles", f"k_step_d2q9_{c.lower()}_f32_traffic.json")
+                   for c in ("SMRT", "SMRT_FNEQ")}
 
 
 def parse():
@@ -60,6 +61,9 @@ def parse():
                          "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
     ap.add_argument("--storage", default="F32", choices=["F32", "F16", "BF16"],
                     help="kolmogorov: storage of the populations (F32 is the benchmark configuration)")
+    ap.add_argument("--collision", default="SMRT", choices=["SMRT", "SMRT_FNEQ"],
+                    help="kolmogorov: SMRT (the benchmark configuration) or SMRT with the force's "
+                         "non-equilibrium terms (Eq. Frc, third and fourth)")
     ap.add_argument("--channels", type=int, default=512, help="batch: number of channels (512: the benchmark)")
     ap.add_argument("--tune-only", action="store_true",
                     help="batch: autotune the tiles, print the chosen shape and stop (a short run for profilers)")
@@ -188,20 +192,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_per_launch(n_nodes):
+def traffic_per_launch(n_nodes, collision="SMRT"):
     """DRAM bytes per launch of the stream-collide kernel from the committed ncu
     summary, scaled to this launch by node count; None when the summary is
     missing or the kernel sources changed since it was taken."""
-    if not os.path.exists(PROFILE_TRAFFIC):
+    path = PROFILE_TRAFFIC.get(collision)
+    if path is None or not os.path.exists(path):
         return None
-    d = json.load(open(PROFILE_TRAFFIC))
+    d = json.load(open(path))
     if d.get("kernel_sources_sha") != kernel_sources_sha():
         return None
     return float(d["dram_bytes_per_node"]) * n_nodes
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_strip(n, rows, seed=2212074940):
+def oracle_strip(n, rows, seed=2212074940, collision="SMRT"):
     """Rows [0, rows) of the n x n Kolmogorov workload as an n x rows periodic
     strip (same per-node work; the oracle cannot hold the full run)."""
     import oracle as O
@@ -220,15 +225,16 @@ def oracle_strip(n, rows, seed=2212074940):
         u0 = wl.u0[:, :, :rows]
         g = wl.g[:rows]
         tau = wl.tau
-    return O.Sim(O.D2Q9, O.SMRT, (n, rows, 1), (1, 1, 1), tau, g=g, force_kind="rows",
+    coll = O.SMRT_FNEQ if collision == "SMRT_FNEQ" else O.SMRT
+    return O.Sim(O.D2Q9, coll, (n, rows, 1), (1, 1, 1), tau, g=g, force_kind="rows",
                  u0=np.ascontiguousarray(u0))
 
 
-def cpu_baseline(n, seconds):
+def cpu_baseline(n, seconds, collision="SMRT"):
     import oracle as O
     cores = O.set_threads(os.cpu_count() or 1)
     rows = max(8, min(n, 256))
-    sim = oracle_strip(n, rows)
+    sim = oracle_strip(n, rows, collision=collision)
     sim.step(1)
     t0 = time.perf_counter()
     steps = 0
@@ -291,7 +297,8 @@ def run_gpu(args, ws, rank, local):
     stream = torch.cuda.Stream(device=local)
     N = n * n
     st = args.storage
-    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, st, (1, 1, 1), g=wl.g, force_kind="rows",
+    coll = args.collision
+    lat = P.Lattice("D2Q9", coll, (n, n, 1), wl.tau, st, (1, 1, 1), g=wl.g, force_kind="rows",
                     u0=wl.u0, torch_stream=stream)
     D, Q, _, bytes_per_node = lat.info()
     C = max(1, args.check_every)
@@ -341,20 +348,20 @@ def run_gpu(args, ws, rank, local):
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_node * N
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = traffic_per_launch(N) if st == "F32" else None
+    traffic = traffic_per_launch(N, coll) if st == "F32" else None
     clocks = sampler.summary()
     launches = chunks * (C + 2)
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(P, torch, wl, n, steps, C, local, ws, dist, st)
+        e2e = run_e2e(P, torch, wl, n, steps, C, local, ws, dist, st, coll)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
             "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if st == "F32" else f"{st.lower()} storage, f32 arithmetic",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if st == "F32" else WORKLOAD.replace("_f32_", f"_{st.lower()}_"),
-                       "lattice": "D2Q9", "collision": "SMRT", "storage": st,
+            "config": {"workload": WORKLOAD.replace("_smrt_f32_", f"_{coll.lower()}_{st.lower()}_"),
+                       "lattice": "D2Q9", "collision": coll, "storage": st,
                        "nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)",
                        "check_every": C,
                        "l2": (f"inputs larger than L2 (two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers)"
@@ -364,21 +371,21 @@ def run_gpu(args, ws, rank, local):
                        "replicas": ws},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"k_step<D2Q9,SMRT,{st}>", "bytes_per_launch": algo_bytes,
+                         "kernel": f"k_step<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st}>", "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,
             "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res}}
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds, coll)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32"):
+def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32", collision="SMRT"):
     """Whole job through the public API from pinned host memory: create (H2D of
     the initial velocity and force), run with a host-read residual every C
     steps, read rho and u back (D2H)."""
@@ -392,7 +399,7 @@ def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32"):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat = P.Lattice("D2Q9", "SMRT", (n, n, 1), wl.tau, storage, (1, 1, 1), g=g.numpy(), force_kind="rows",
+    lat = P.Lattice("D2Q9", collision, (n, n, 1), wl.tau, storage, (1, 1, 1), g=g.numpy(), force_kind="rows",
                     u0=u0.numpy())
     r = None
     for _ in range(steps // C):

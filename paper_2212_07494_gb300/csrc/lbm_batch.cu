@@ -759,7 +759,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
     const lbm_desc &d0 = descs[0];
     if (d0.lattice != LBM_D2Q9) return bfail(nullptr, LBM_ERR_ARG, "batches are D2Q9");
     if (d0.storage != LBM_F32 && d0.storage != LBM_F64) return bfail(nullptr, LBM_ERR_ARG, "batch storage is F32 or F64");
-    if (d0.collision != LBM_BGK && d0.collision != LBM_SMRT) return bfail(nullptr, LBM_ERR_ARG, "bad collision");
+    if (d0.collision != LBM_BGK && d0.collision != LBM_SMRT)
+        return bfail(nullptr, LBM_ERR_ARG, "batches take BGK or SMRT collisions");
     for (int c = 0; c < n; ++c) {
         const lbm_desc &d = descs[c];
         if (d.lattice != d0.lattice || d.collision != d0.collision || d.storage != d0.storage)

@@ -21,7 +21,9 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-enum { BGK = 0, SMRT = 1, SMRT_TRIM = 2 };  // SMRT_TRIM: SMRT with tau_3 = tau_4 = 1 (kernel choice only)
+// BGK, SMRT and SMRT_FNEQ carry the values of the C ABI's lbm_collision;
+// SMRT_TRIM is SMRT with tau_3 = tau_4 = 1 (a kernel choice only)
+enum { BGK = 0, SMRT = 1, SMRT_FNEQ = 2, SMRT_TRIM = 3 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 enum { G_NONE = 0, G_UNIFORM = 1, G_ROWS = 2, G_FIELD = 3 };
 
@@ -461,6 +463,72 @@ __host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R g
         constexpr int g = decltype(I)::value;
         if constexpr (!((RET >> g) & 1u)) G[g] = R(0);
     });
+    G[0] = drho;                          // deviation from the weights
+    reconstruct<L>(G);
+    if (L == D3Q19) {
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) G[gpos<L>(i)] *= R(weight<L>(i));
+    }
+}
+
+// SMRT with the force's non-equilibrium contributions (Eq. Frc, third and
+// fourth terms): d_F^(n) = n g d^(n-1) in the co-moving frame for n <= 4, the
+// product summed over the n positions of g, which on the grid of per-axis
+// orders reads d_F[m] = sum_a m_a g_a d[m - e_a] (the monic per-axis
+// polynomials satisfy h_k' = k h_(k-1), so this holds in lattice units).  d
+// are the central moments of f itself, not of fbar: d^(1) = 0, and for n >= 2
+// Eq. (newf) inverts to d^(n) = (1 - om_n/2)(dbar_1^(n) + d_F^(n)/2).  Hence
+// d_F^(2) = 0, d_F^(3) = 3 g d^(2) and d_F^(4) = 4 g d^(3), each order needing
+// the one below it.  Relaxation as in collide_smrt with these d_F added.
+template <int L, typename R>
+__host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+    constexpr int D = Lat<L>::D;
+    constexpr int N = Grid<D>::N;
+    constexpr int EX = 1, EY = 3, EZ = 9;
+    project<D>(G);
+    const R drho = G[0];
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = G[EX] * inv + R(0.5) * gx;   // Eq. (half_F)
+    const R uy = G[EY] * inv + R(0.5) * gy;
+    const R uz = D == 3 ? G[EZ] * inv + R(0.5) * gz : R(0);
+    G[0] = rho;
+    shift<D>(G, -ux, -uy, -uz);           // central moments of fbar
+    const R ga[3] = {gx, gy, gz};
+    R d2[N], F3[N], d3[N];                // second- and third-order central moments of f, d_F^(3)
+#pragma unroll
+    for (int g = 0; g < N; ++g) d2[g] = morder<D>(g) == 2 ? (R(1) - R(0.5) * om2) * G[g] : R(0);
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+        F3[g] = R(0);
+        if (morder<D>(g) == 3) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (mdig<D>(g, a) > 0) F3[g] += R(mdig<D>(g, a)) * ga[a] * d2[g - ax_stride(a)];
+        }
+        d3[g] = morder<D>(g) == 3 ? (R(1) - R(0.5) * om3) * (G[g] + R(0.5) * F3[g]) : R(0);
+    }
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+        const int n = morder<D>(g);
+        if (n == 2) G[g] *= (R(1) - om2);
+        else if (n == 3) G[g] = (R(1) - om3) * G[g] + (R(1) - R(0.5) * om3) * F3[g];
+        else if (n == 4) {
+            R F4 = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (mdig<D>(g, a) > 0) F4 += R(mdig<D>(g, a)) * ga[a] * d3[g - ax_stride(a)];
+            G[g] = (R(1) - om4) * G[g] + (R(1) - R(0.5) * om4) * F4;
+        } else if (n >= 5) G[g] = R(0);
+    }
+    G[0] = rho;
+    G[EX] = R(0.5) * rho * gx;
+    G[EY] = R(0.5) * rho * gy;
+    if (D == 3) G[EZ] = R(0.5) * rho * gz;
+    shift<D>(G, ux, uy, uz);              // back to raw moments: a_0 + a_p
+#pragma unroll
+    for (int g = 0; g < N; ++g)
+        if (!retained<L>(g)) G[g] = R(0);
     G[0] = drho;                          // deviation from the weights
     reconstruct<L>(G);
     if (L == D3Q19) {

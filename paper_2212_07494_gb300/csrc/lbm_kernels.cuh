@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
         if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4);
         else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2);
+        else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4);
         else collide_bgk<L>(G[k], gx, gy, gz, om2);
         typename Store<ST>::T *dst = fout + own;
 #pragma unroll
@@ -343,6 +344,7 @@ template <int L> struct Dispatch {
         // tau_3 = tau_4 = 1 exactly: the trimmed collision, the same arithmetic
         // on the moments that stay non-zero
         if (coll == SMRT && p.om[3] == 1.0 && p.om[4] == 1.0) return step_s<SMRT_TRIM>(st, mask, cfg, p, fin, fout, s);
+        if (coll == SMRT_FNEQ) return step_s<SMRT_FNEQ>(st, mask, cfg, p, fin, fout, s);
         return coll == SMRT ? step_s<SMRT>(st, mask, cfg, p, fin, fout, s)
                             : step_s<BGK>(st, mask, cfg, p, fin, fout, s);
     }
@@ -397,8 +399,9 @@ template <int L> struct Dispatch {
     }
     static cudaError_t init(int coll, int st, bool mask, const KParams &p, const double *rho0, const double *u0,
                             void *target, cudaStream_t s) {
-        return coll == SMRT ? init_c<SMRT>(st, mask, p, rho0, u0, target, s)
-                            : init_c<BGK>(st, mask, p, rho0, u0, target, s);
+        // both SMRT forms start from zero non-equilibrium, where d_F^(n>=2) = 0
+        return coll == BGK ? init_c<BGK>(st, mask, p, rho0, u0, target, s)
+                           : init_c<SMRT>(st, mask, p, rho0, u0, target, s);
     }
 
     static cudaError_t unstream(int st, bool mask, const KParams &p, const void *T, void *P, cudaStream_t s) {

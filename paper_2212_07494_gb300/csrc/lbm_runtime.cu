@@ -293,7 +293,8 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     *out = nullptr;
     if (!d) return fail(nullptr, LBM_ERR_ARG, "desc is NULL");
     if (d->lattice < LBM_D2Q9 || d->lattice > LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "bad lattice");
-    if (d->collision != LBM_BGK && d->collision != LBM_SMRT) return fail(nullptr, LBM_ERR_ARG, "bad collision");
+    if (d->collision != LBM_BGK && d->collision != LBM_SMRT && d->collision != LBM_SMRT_FNEQ)
+        return fail(nullptr, LBM_ERR_ARG, "bad collision");
     if (d->storage < LBM_F64 || d->storage > LBM_BF16_SHIFT) return fail(nullptr, LBM_ERR_ARG, "bad storage");
     if (d->force_kind < LBM_G_NONE || d->force_kind > LBM_G_FIELD) return fail(nullptr, LBM_ERR_ARG, "bad force kind");
     const int D = lattice_D(d->lattice), Q = lattice_Q(d->lattice);
@@ -301,7 +302,7 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     if (D == 2 && d->nz != 1) return fail(nullptr, LBM_ERR_ARG, "nz must be 1 for D2Q9");
     if (d->ny > 65535 || d->nz > 65535) return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
     if (d->collision == LBM_BGK && !(d->tau[2] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau[2] must be > 1/2");
-    if (d->collision == LBM_SMRT)
+    if (d->collision != LBM_BGK)
         for (int n = 2; n <= 4; ++n)
             if (!(d->tau[n] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");
     if ((d->alloc == nullptr) != (d->free_ == nullptr))

@@ -31,12 +31,14 @@ def _samples(n, k, seed, D):
     return pts
 
 
-def test_kolmogorov_4096_sampled_nodes():
-    """D2Q9 SMRT FP32, 4096 x 4096, per-row force: the bench's workload."""
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ"])
+def test_kolmogorov_4096_sampled_nodes(coll):
+    """D2Q9 SMRT FP32, 4096 x 4096, per-row force: the bench's workload, also
+    with the force's non-equilibrium terms."""
     import paper_2212_07494_gb300 as P
     wl = W.kolmogorov(n=4096)
     n = 4096
-    lat = P.Lattice("D2Q9", "SMRT", wl.shape, wl.tau, "F32", wl.periodic, g=wl.g, force_kind="rows", u0=wl.u0)
+    lat = P.Lattice("D2Q9", coll, wl.shape, wl.tau, "F32", wl.periodic, g=wl.g, force_kind="rows", u0=wl.u0)
     lat.step(STEPS)
     f = lat.populations()                       # (9, 1, n, n)
     lat.close()
@@ -46,7 +48,7 @@ def test_kolmogorov_4096_sampled_nodes():
         rows = np.arange(y - R, y + R + 1) % n
         cols = np.arange(x - R, x + R + 1) % n
         u0 = wl.u0[:, :, rows][:, :, :, cols]
-        orc = O.Sim(O.D2Q9, O.SMRT, (2 * R + 1, 2 * R + 1, 1), (1, 1, 1), wl.tau, g=wl.g[rows],
+        orc = O.Sim(O.D2Q9, O.SMRT_FNEQ if coll == "SMRT_FNEQ" else O.SMRT, (2 * R + 1, 2 * R + 1, 1), (1, 1, 1), wl.tau, g=wl.g[rows],
                     force_kind="rows", u0=np.ascontiguousarray(u0))
         orc.step(STEPS)
         fo = orc.populations()[:, 0, R, R]

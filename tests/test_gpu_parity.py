@@ -20,13 +20,15 @@ LATTICES = ["D2Q9", "D3Q19", "D3Q27"]
 SHAPES = {"D2Q9": [(150, 37, 1), (530, 9, 1)], "D3Q19": [(70, 9, 7), (130, 5, 4)],
           "D3Q27": [(70, 9, 7), (130, 5, 4)]}
 # SMRT_TRIM: tau_3 = tau_4 = 1, the kernels' trimmed collision (orders 3 and 4
-# relax to zero exactly); the oracle runs its one general collision for both
-TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1), "SMRT_TRIM": (1.0, 1.3, 0.63, 1.0, 1.0)}
-COLLS = ["BGK", "SMRT", "SMRT_TRIM"]
+# relax to zero exactly); the oracle runs its one general collision for both.
+# SMRT_FNEQ: the force's non-equilibrium terms (Eq. Frc, third and fourth).
+TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1), "SMRT_TRIM": (1.0, 1.3, 0.63, 1.0, 1.0),
+       "SMRT_FNEQ": (1.0, 1.3, 0.63, 0.87, 1.1)}
+COLLS = ["BGK", "SMRT", "SMRT_TRIM", "SMRT_FNEQ"]
 
 
 def _model(coll):
-    return "BGK" if coll == "BGK" else "SMRT"
+    return {"BGK": "BGK", "SMRT_FNEQ": "SMRT_FNEQ"}.get(coll, "SMRT")
 
 
 def _D(lat):
@@ -46,7 +48,7 @@ def _random_state(lat, shape, seed, solid=None, amp=0.02):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", ["BGK", "SMRT"])
+@pytest.mark.parametrize("coll", ["BGK", "SMRT", "SMRT_FNEQ"])
 def test_initial_populations(lat, coll):
     shape = SHAPES[lat][0]
     rho0, u0 = W.random_near_equilibrium(lat, shape, seed=21, du=0.03)
@@ -112,7 +114,8 @@ def test_poiseuille_channel_f64():
 
 @pytest.mark.parametrize("kind", ["rows", "field"])
 @pytest.mark.parametrize("lat", ["D2Q9", "D3Q27"])
-def test_force_kinds(kind, lat):
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ"])
+def test_force_kinds(kind, lat, coll):
     shape = SHAPES[lat][0]
     nx, ny, nz = shape
     D = _D(lat)
@@ -124,7 +127,7 @@ def test_force_kinds(kind, lat):
     else:
         rng = np.random.default_rng(3)
         g = 1e-5 * rng.normal(size=(D, nz, ny, nx))
-    gl, orc = make_pair(lat, "SMRT", shape, TAU["SMRT"], "F64", (1, 1, 1), g=g, force_kind=kind)
+    gl, orc = make_pair(lat, coll, shape, TAU[coll], "F64", (1, 1, 1), g=g, force_kind=kind)
     gl.step(20)
     orc.step(20)
     assert rel_l2(gl.moments()[1], orc.moments()[1]) < 1e-12
@@ -139,7 +142,7 @@ def test_force_kinds(kind, lat):
 
 @pytest.mark.parametrize("lat", LATTICES)
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16"])
-@pytest.mark.parametrize("coll", ["SMRT", "SMRT_TRIM"])
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_TRIM", "SMRT_FNEQ"])
 def test_one_step_reduced_storage(lat, storage, coll):
     """One step from the same stored (rounded) state: GPU (FP32 arithmetic,
     rounding on store) vs the oracle (FP64 arithmetic, same rounding)."""
@@ -169,6 +172,34 @@ def test_one_step_reduced_storage(lat, storage, coll):
         # two sides round the same way almost everywhere
         assert np.all(np.abs(dg - do) <= 2 * ulp * np.abs(do) + 64 * eps32 * scale + 6e-8)
         assert np.mean(dg == do) > 0.97
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_noneq_force_terms_match_the_oracle(lat, storage):
+    """The change the non-equilibrium force terms make to one step (SMRT_FNEQ
+    minus SMRT from the same state), on the GPU and in the oracle: a kernel
+    that silently ran plain SMRT, or dropped d_F^(3) or d_F^(4), fails here.
+    A larger g makes the terms (g times a non-equilibrium moment) stand out
+    against FP32 rounding."""
+    shape = SHAPES[lat][0]
+    g = 50 * _gvec(lat)
+    f0 = _random_state(lat, shape, 81, amp=0.05)
+    out = {}
+    for coll in ("SMRT", "SMRT_FNEQ"):
+        gl, orc = make_pair(lat, coll, shape, TAU["SMRT"], storage, (1, 0, 1), g=g)
+        orc.set_populations(f0)
+        gl.set_populations(f0)
+        gl.step(1)
+        orc.step(1)
+        out[coll] = (gl.populations(), orc.populations())
+        gl.close()
+    dg = out["SMRT_FNEQ"][0] - out["SMRT"][0]
+    do = out["SMRT_FNEQ"][1] - out["SMRT"][1]
+    scale = np.abs(do).max()
+    assert scale > 1e-7
+    tol = 1e-14 if storage == "F64" else 64 * 2.0 ** -24 * 0.05
+    assert np.abs(dg - do).max() < tol, (np.abs(dg - do).max(), scale)
 
 
 def test_state_checkpoint_restart_is_bit_exact():
