@@ -28,7 +28,7 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
-BGK, SMRT, SMRT_FNEQ = 0, 1, 2
+BGK, SMRT, SMRT_FNEQ, MRT_RAW = 0, 1, 2, 3
 PACK = 121  # packed Hermite tensor length (1 + 3 + 9 + 27 + 81)
 ROUND_NONE, ROUND_F32, ROUND_F16, ROUND_BF16 = 0, 1, 2, 3
 

@@ -25,6 +25,10 @@
  *    d_F^(n) = n g d^(n-1) for n <= 4 (Eq. Frc, third and fourth terms), with
  *    d^(n-1) the moments of f itself, recovered from those of fbar by
  *    inverting Eq. (newf) order by order.
+ *  - the fourth collision mode (OR_MRT_RAW) is the raw-moment MRT of the
+ *    appendix: per-order relaxation of the raw non-equilibrium moments, the
+ *    fourth order from the appendix's recursion, the force's equilibrium part
+ *    a_F^(n) = n F u^(n-1) only.
  *  - retained Hermite components per lattice: D2Q9/D3Q27 keep components with
  *    per-axis multiplicity <= 2 and order <= 4; D3Q19 keeps orders <= 2 and
  *    the six (2,1,0) third-order components.  D3Q19 is a degree-5 rule, so a
@@ -54,7 +58,7 @@
 #define OR_PACK 121 /* 1 + 3 + 9 + 27 + 81 for D = 3 */
 
 enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
-enum { OR_BGK = 0, OR_SMRT = 1, OR_SMRT_FNEQ = 2 };
+enum { OR_BGK = 0, OR_SMRT = 1, OR_SMRT_FNEQ = 2, OR_MRT_RAW = 3 };
 
 typedef struct {
     int id, D, Q;
@@ -395,6 +399,57 @@ static void collide_smrt(const or_lattice *L, const double *tau, int fneq, const
     }
 }
 
+/* Raw-moment MRT of the appendix, at theta = 1 (u_1 = u_2 = u u):
+ *   a_p^(n) = a_0^(n) + (1 - 1/tau_n) a_1bar^(n) + (1 - 1/(2 tau_n)) a_F^(n),
+ * with a_1bar^(1) = -F/2, a_1bar^(2), a_1bar^(3) projected, the fourth order
+ * from the recursion
+ *   a_1bar^(4) = 4 u a_1bar^(3) - 6 u u a_1bar^(2) + 4 u u u a_1bar^(1)
+ * (each term summed over the distinct placements of the u's), and the
+ * force's equilibrium part a_F^(n) = n F u^(n-1) (placements of F among the
+ * n indices, u at the others). */
+static void collide_mrt_raw(const or_lattice *L, const double *tau, const double *dev,
+                            const double *gL, double *dpop)
+{
+    double drho, rho, u[3], g[3];
+    double abar[OR_PACK], a0[OR_PACK], a1[OR_PACK], aF[OR_PACK], tot[OR_PACK];
+    const int P = L->off[OR_MAXN + 1];
+    macroscopic(L, dev, gL, &drho, &rho, u, g);
+    project(L, dev, abar);
+    abar[0] = rho;
+    equilibrium_moments(L, rho, u, a0);
+    for (int k = 0; k < P; ++k) a1[k] = abar[k] - a0[k];
+    a1[0] = 0.0;
+    for (int k = 0; k < L->D; ++k) a1[L->off[1] + k] = -0.5 * rho * g[k];
+    for (int k = L->off[4]; k < L->off[5]; ++k) {
+        double acc = 0.0;
+        for (int S = 1; S < 15; ++S) {          /* non-empty proper subsets of the 4 positions */
+            int m = 0;
+            double p = 1.0;
+            for (int j = 0; j < 4; ++j)
+                if (S & (1 << j)) { p *= u[L->dig[k][j]]; ++m; }
+            acc += (m == 2 ? -1.0 : 1.0) * p * a1[L->rest[k][S]];
+        }
+        a1[k] = acc;
+    }
+    for (int k = 0; k < P; ++k) {
+        const int n = L->order[k];
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+            double p = rho * g[L->dig[k][j]];
+            for (int i = 0; i < n; ++i)
+                if (i != j) p *= u[L->dig[k][i]];
+            acc += p;
+        }
+        aF[k] = acc;
+    }
+    tot[0] = drho;                              /* rho - 1: reconstruct fbar_p - w */
+    for (int k = 1; k < P; ++k) {
+        const double t = tau[L->order[k]];
+        tot[k] = a0[k] + (1.0 - 1.0 / t) * a1[k] + (1.0 - 0.5 / t) * aF[k];
+    }
+    reconstruct(L, tot, dpop);
+}
+
 /* delta = f_eq - F/2 - w with the collision model's own equilibrium and force */
 static void initial_node(const or_lattice *L, int collision, double rho, const double *uL,
                          const double *gL, double *dev)
@@ -431,7 +486,7 @@ typedef struct {
 
 static int check_params(const or_params *p, or_lattice *L)
 {
-    if (p->lattice < 0 || p->lattice > 2 || p->collision < 0 || p->collision > 2) return -1;
+    if (p->lattice < 0 || p->lattice > 2 || p->collision < 0 || p->collision > 3) return -1;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
     lattice_init(p->lattice, L);
     if (L->D == 2 && p->nz != 1) return -1;
@@ -520,6 +575,7 @@ int or_collide_node(const or_params *p, const double *fbar, const double *gL, do
     if (check_params(p, &L)) return -1;
     for (int i = 0; i < L.Q; ++i) dev[i] = fbar[i] - L.w[i];
     if (p->collision == OR_BGK) collide_bgk(&L, p->tau, dev, gL, dp);
+    else if (p->collision == OR_MRT_RAW) collide_mrt_raw(&L, p->tau, dev, gL, dp);
     else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, dev, gL, dp, dbg);
     for (int i = 0; i < L.Q; ++i) fp[i] = L.w[i] + dp[i];
     return 0;
@@ -585,6 +641,7 @@ int or_step(const or_params *p, const unsigned char *solid, const double *g,
         for (int i = 0; i < L.Q; ++i) fb[i] = f_in[(size_t)i * N + x];
         for (int k = 0; k < L.D; ++k) gL[k] = g ? g[(size_t)k * N + x] : 0.0;
         if (p->collision == OR_BGK) collide_bgk(&L, p->tau, fb, gL, fp);
+        else if (p->collision == OR_MRT_RAW) collide_mrt_raw(&L, p->tau, fb, gL, fp);
         else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, fb, gL, fp, NULL);
         const int X = (int)(x % nx), Y = (int)((x / nx) % ny), Z = (int)(x / ((size_t)nx * ny));
         for (int i = 0; i < L.Q; ++i) {

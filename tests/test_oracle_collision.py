@@ -218,7 +218,7 @@ def test_collision_conserves_mass_and_adds_momentum(lat):
     c = c[:, :D].astype(float)
     rng = np.random.default_rng(14)
     for coll, tau in [(O.BGK, (1, 1, 0.7, 1, 1)), (O.SMRT, (1, 1.3, 0.57, 0.8, 1.2)),
-                      (O.SMRT_FNEQ, (1, 1.3, 0.57, 0.8, 1.2))]:
+                      (O.SMRT_FNEQ, (1, 1.3, 0.57, 0.8, 1.2)), (O.MRT_RAW, (1, 1.3, 0.57, 0.8, 1.2))]:
         p = O.make_params(lat, coll, (2, 2, 2 if D == 3 else 1), tau=tau)
         f = w * (1 + 0.05 * rng.normal(size=Q))
         g = rng.normal(size=D) * 1e-3

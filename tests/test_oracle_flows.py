@@ -34,7 +34,7 @@ def _shape(lat, n2=(6, 5), n3=(4, 3, 5)):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_uniform_state_velocity_grows_by_g(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat)
@@ -52,7 +52,7 @@ def test_uniform_state_velocity_grows_by_g(lat, coll):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_momentum_grows_by_Mg(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat, (8, 7), (5, 4, 6))
@@ -69,7 +69,7 @@ def test_momentum_grows_by_Mg(lat, coll):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ])
+@pytest.mark.parametrize("coll", [O.BGK, O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_mass_conserved_with_walls_and_solids(lat, coll):
     D = 2 if lat == O.D2Q9 else 3
     shape = _shape(lat, (12, 9), (6, 5, 4))
@@ -110,7 +110,7 @@ def test_poiseuille_closed_form():
     assert err < 1e-8, err
 
 
-@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ])
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_poiseuille_smrt_second_difference(coll):
     """SMRT in the same channel, with and without the force's non-equilibrium
     terms: the interior profile has the exact viscosity nu = (tau_2 - 1/2)/3,
@@ -127,7 +127,7 @@ def test_poiseuille_smrt_second_difference(coll):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ])
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_taylor_green_second_order(coll):
     """Sec. III.A; the non-equilibrium force terms (Eq. Frc) must keep the
     second-order convergence."""
