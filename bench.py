@@ -41,7 +41,7 @@ METRIC = "MLUPS and % of HBM roofline per lattice"
 UNIT = "MLUPS"
 WORKLOAD = "kolmogorov_d2q9_smrt_f32_4096x4096"
 PROFILE_TRAFFIC = {c: os.path.join(ROOT, "profiles", f"k_step_d2q9_{c.lower()}_f32_traffic.json")
-                   for c in ("SMRT", "SMRT_FNEQ")}
+                   for c in ("SMRT", "SMRT_FNEQ", "MRT_RAW")}
 
 
 def parse():
@@ -61,9 +61,9 @@ def parse():
                          "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
     ap.add_argument("--storage", default="F32", choices=["F32", "F16", "BF16"],
                     help="kolmogorov: storage of the populations (F32 is the benchmark configuration)")
-    ap.add_argument("--collision", default="SMRT", choices=["SMRT", "SMRT_FNEQ"],
-                    help="kolmogorov: SMRT (the benchmark configuration) or SMRT with the force's "
-                         "non-equilibrium terms (Eq. Frc, third and fourth)")
+    ap.add_argument("--collision", default="SMRT", choices=["SMRT", "SMRT_FNEQ", "MRT_RAW"],
+                    help="kolmogorov: SMRT (the benchmark configuration), SMRT with the force's "
+                         "non-equilibrium terms (Eq. Frc, third and fourth), or the appendix's raw-moment MRT")
     ap.add_argument("--channels", type=int, default=512, help="batch: number of channels (512: the benchmark)")
     ap.add_argument("--tune-only", action="store_true",
                     help="batch: autotune the tiles, print the chosen shape and stop (a short run for profilers)")
@@ -225,7 +225,7 @@ def oracle_strip(n, rows, seed=2212074940, collision="SMRT"):
         u0 = wl.u0[:, :, :rows]
         g = wl.g[:rows]
         tau = wl.tau
-    coll = O.SMRT_FNEQ if collision == "SMRT_FNEQ" else O.SMRT
+    coll = getattr(O, collision)
     return O.Sim(O.D2Q9, coll, (n, rows, 1), (1, 1, 1), tau, g=g, force_kind="rows",
                  u0=np.ascontiguousarray(u0))
 

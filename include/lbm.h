@@ -71,9 +71,13 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
  * non-equilibrium contributions in the co-moving frame (Eq. Frc, third and
  * fourth terms): d_F^(n) = n g d^(n-1) for n = 3, 4, with d the central
  * moments of f recovered from those of fbar by inverting Eq. (newf),
- * d^(n) = (1 - 1/(2 tau_n)) (dbar_1^(n) + d_F^(n)/2).  Both SMRT forms
- * start from the same state; batches (lbm_batch_create) take BGK and SMRT. */
-typedef enum { LBM_BGK = 0, LBM_SMRT = 1, LBM_SMRT_FNEQ = 2 } lbm_collision;
+ * d^(n) = (1 - 1/(2 tau_n)) (dbar_1^(n) + d_F^(n)/2).  LBM_MRT_RAW is the
+ * raw-moment MRT of the appendix: the raw (not co-moving) non-equilibrium
+ * moments relax order by order, a_p^(n) = a_0^(n) + (1 - 1/tau_n) a_1^(n)
+ * + (1 - 1/(2 tau_n)) a_F^(n), with a_F^(n) = n F u^(n-1) and the fourth
+ * order from the appendix's recursion.  All moment models start from the
+ * same state; batches (lbm_batch_create) take BGK and SMRT. */
+typedef enum { LBM_BGK = 0, LBM_SMRT = 1, LBM_SMRT_FNEQ = 2, LBM_MRT_RAW = 3 } lbm_collision;
 
 /* Storage of the populations.  All modes store the deviation
  * delta_i = fbar_i - w_i; arithmetic is FP64 for LBM_F64 and FP32 otherwise.
@@ -95,7 +99,7 @@ typedef struct {
     int storage;          /* lbm_storage */
     int nx, ny, nz;       /* nz = 1 for D2Q9; nx * ny * nz < 2^31 / Q */
     int periodic[3];      /* per axis; 0 => halfway bounce-back walls */
-    double tau[5];        /* tau per Hermite order n (index n); both SMRT forms use tau[2..4]
+    double tau[5];        /* tau per Hermite order n (index n); the moment models use tau[2..4]
                              (tau[0], tau[1] unused: orders 0 and 1 are conserved /
                              fixed by the force); BGK uses tau[2] */
     int force_kind;       /* lbm_force_kind */

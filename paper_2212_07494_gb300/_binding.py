@@ -12,13 +12,13 @@ _LIB_PATH = os.path.join(_HERE, "lib", "liblbm_gb300.so")
 
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_NOT_CONVERGED = 1
-LBM_BGK, LBM_SMRT, LBM_SMRT_FNEQ = 0, 1, 2
+LBM_BGK, LBM_SMRT, LBM_SMRT_FNEQ, LBM_MRT_RAW = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT = 0, 1, 2, 3
 LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD = 0, 1, 2, 3
 
 _NAMES = {
     "lattice": {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2},
-    "collision": {"BGK": 0, "SMRT": 1, "SMRT_FNEQ": 2},
+    "collision": {"BGK": 0, "SMRT": 1, "SMRT_FNEQ": 2, "MRT_RAW": 3},
     "storage": {"F64": 0, "F32": 1, "F16": 2, "F16_SHIFT": 2, "BF16": 3, "BF16_SHIFT": 3},
     "force": {"none": 0, "uniform": 1, "rows": 2, "field": 3},
 }

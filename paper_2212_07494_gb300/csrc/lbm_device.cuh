@@ -21,9 +21,9 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-// BGK, SMRT and SMRT_FNEQ carry the values of the C ABI's lbm_collision;
-// SMRT_TRIM is SMRT with tau_3 = tau_4 = 1 (a kernel choice only)
-enum { BGK = 0, SMRT = 1, SMRT_FNEQ = 2, SMRT_TRIM = 3 };
+// BGK, SMRT, SMRT_FNEQ and MRT_RAW carry the values of the C ABI's
+// lbm_collision; SMRT_TRIM is SMRT with tau_3 = tau_4 = 1 (a kernel choice only)
+enum { BGK = 0, SMRT = 1, SMRT_FNEQ = 2, MRT_RAW = 3, SMRT_TRIM = 4 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 enum { G_NONE = 0, G_UNIFORM = 1, G_ROWS = 2, G_FIELD = 3 };
 
@@ -530,6 +530,70 @@ __host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R g
     for (int g = 0; g < N; ++g)
         if (!retained<L>(g)) G[g] = R(0);
     G[0] = drho;                          // deviation from the weights
+    reconstruct<L>(G);
+    if (L == D3Q19) {
+#pragma unroll
+        for (int i = 0; i < Lat<L>::Q; ++i) G[gpos<L>(i)] *= R(weight<L>(i));
+    }
+}
+
+// Raw-moment MRT of the appendix: the raw (not co-moving) non-equilibrium
+// moments relax order by order,
+//   a_p^(n) = a_0^(n) + (1 - om_n) a_1^(n) + (1 - om_n/2) a_F^(n),
+// with a_1^(1) = -F/2, orders 2 and 3 projected, the fourth order from the
+// appendix's recursion, and the force's equilibrium part
+// a_F[m] = sum_a m_a rho g_a u^(m - e_a) (a_F^(n) = n F u^(n-1)).  The
+// recursion is the statement that the fourth-order central moment of the
+// non-equilibrium part vanishes, so it is applied as a round trip through
+// the co-moving frame with the orders >= 4 dropped.
+template <int L, typename R>
+__host__ __device__ __forceinline__ void collide_mrt_raw(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+    constexpr int D = Lat<L>::D;
+    constexpr int N = Grid<D>::N;
+    constexpr int EX = 1, EY = 3, EZ = 9;
+    project<D>(G);
+    const R drho = G[0];
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = G[EX] * inv + R(0.5) * gx;   // Eq. (half_F)
+    const R uy = G[EY] * inv + R(0.5) * gy;
+    const R uz = D == 3 ? G[EZ] * inv + R(0.5) * gz : R(0);
+    G[0] = rho;
+    shift<D>(G, -ux, -uy, -uz);           // central moments of fbar; the equilibrium's are rho e_0
+    G[0] = R(0);
+    G[EX] = R(-0.5) * rho * gx;           // a_1^(1) = -F/2
+    G[EY] = R(-0.5) * rho * gy;
+    if (D == 3) G[EZ] = R(-0.5) * rho * gz;
+#pragma unroll
+    for (int g = 0; g < N; ++g)
+        if (morder<D>(g) >= 4) G[g] = R(0);
+    shift<D>(G, ux, uy, uz);              // raw non-equilibrium moments, recursive fourth order
+    const R up[3][3] = {{R(1), ux, ux * ux}, {R(1), uy, uy * uy}, {R(1), uz, uz * uz}};
+    const R ga[3] = {gx, gy, gz};
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+        const int n = morder<D>(g);
+        if (n == 0) {
+            G[g] = drho;                  // deviation from the weights
+        } else if (n <= 4 && retained<L>(g)) {
+            R a0 = rho, aF = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) a0 *= up[a][mdig<D>(g, a)];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                if (mdig<D>(g, a) == 0) continue;
+                R t = R(mdig<D>(g, a)) * rho * ga[a] * up[a][mdig<D>(g, a) - 1];
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+                    if (b != a) t *= up[b][mdig<D>(g, b)];
+                aF += t;
+            }
+            const R om = n == 1 ? R(1) : (n == 2 ? om2 : (n == 3 ? om3 : om4));
+            G[g] = n == 1 ? a0 + R(0.5) * aF : a0 + (R(1) - om) * G[g] + (R(1) - R(0.5) * om) * aF;
+        } else {
+            G[g] = R(0);
+        }
+    }
     reconstruct<L>(G);
     if (L == D3Q19) {
 #pragma unroll

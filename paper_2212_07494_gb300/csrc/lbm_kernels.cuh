@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4);
         else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2);
         else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4);
+        else if (COLL == MRT_RAW) collide_mrt_raw<L>(G[k], gx, gy, gz, om2, om3, om4);
         else collide_bgk<L>(G[k], gx, gy, gz, om2);
         typename Store<ST>::T *dst = fout + own;
 #pragma unroll
@@ -345,6 +346,7 @@ template <int L> struct Dispatch {
         // on the moments that stay non-zero
         if (coll == SMRT && p.om[3] == 1.0 && p.om[4] == 1.0) return step_s<SMRT_TRIM>(st, mask, cfg, p, fin, fout, s);
         if (coll == SMRT_FNEQ) return step_s<SMRT_FNEQ>(st, mask, cfg, p, fin, fout, s);
+        if (coll == MRT_RAW) return step_s<MRT_RAW>(st, mask, cfg, p, fin, fout, s);
         return coll == SMRT ? step_s<SMRT>(st, mask, cfg, p, fin, fout, s)
                             : step_s<BGK>(st, mask, cfg, p, fin, fout, s);
     }
@@ -399,7 +401,8 @@ template <int L> struct Dispatch {
     }
     static cudaError_t init(int coll, int st, bool mask, const KParams &p, const double *rho0, const double *u0,
                             void *target, cudaStream_t s) {
-        // both SMRT forms start from zero non-equilibrium, where d_F^(n>=2) = 0
+        // the moment models all start from zero non-equilibrium with the same
+        // equilibrium and force expansions (d_F^(n>=2) = 0 there)
         return coll == BGK ? init_c<BGK>(st, mask, p, rho0, u0, target, s)
                            : init_c<SMRT>(st, mask, p, rho0, u0, target, s);
     }

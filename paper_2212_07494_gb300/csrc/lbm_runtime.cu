@@ -293,7 +293,7 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     *out = nullptr;
     if (!d) return fail(nullptr, LBM_ERR_ARG, "desc is NULL");
     if (d->lattice < LBM_D2Q9 || d->lattice > LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "bad lattice");
-    if (d->collision != LBM_BGK && d->collision != LBM_SMRT && d->collision != LBM_SMRT_FNEQ)
+    if (d->collision < LBM_BGK || d->collision > LBM_MRT_RAW)
         return fail(nullptr, LBM_ERR_ARG, "bad collision");
     if (d->storage < LBM_F64 || d->storage > LBM_BF16_SHIFT) return fail(nullptr, LBM_ERR_ARG, "bad storage");
     if (d->force_kind < LBM_G_NONE || d->force_kind > LBM_G_FIELD) return fail(nullptr, LBM_ERR_ARG, "bad force kind");

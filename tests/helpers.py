@@ -5,7 +5,7 @@ import numpy as np
 import oracle as O
 
 LAT = {"D2Q9": O.D2Q9, "D3Q19": O.D3Q19, "D3Q27": O.D3Q27}
-COLL = {"BGK": O.BGK, "SMRT": O.SMRT, "SMRT_FNEQ": O.SMRT_FNEQ}
+COLL = {"BGK": O.BGK, "SMRT": O.SMRT, "SMRT_FNEQ": O.SMRT_FNEQ, "MRT_RAW": O.MRT_RAW}
 ROUND = {"F64": O.ROUND_NONE, "F32": O.ROUND_F32, "F16": O.ROUND_F16, "BF16": O.ROUND_BF16}
 
 

@@ -31,10 +31,10 @@ def _samples(n, k, seed, D):
     return pts
 
 
-@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ"])
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ", "MRT_RAW"])
 def test_kolmogorov_4096_sampled_nodes(coll):
     """D2Q9 SMRT FP32, 4096 x 4096, per-row force: the bench's workload, also
-    with the force's non-equilibrium terms."""
+    with the force's non-equilibrium terms and with the raw-moment MRT."""
     import paper_2212_07494_gb300 as P
     wl = W.kolmogorov(n=4096)
     n = 4096
@@ -48,7 +48,7 @@ def test_kolmogorov_4096_sampled_nodes(coll):
         rows = np.arange(y - R, y + R + 1) % n
         cols = np.arange(x - R, x + R + 1) % n
         u0 = wl.u0[:, :, rows][:, :, :, cols]
-        orc = O.Sim(O.D2Q9, O.SMRT_FNEQ if coll == "SMRT_FNEQ" else O.SMRT, (2 * R + 1, 2 * R + 1, 1), (1, 1, 1), wl.tau, g=wl.g[rows],
+        orc = O.Sim(O.D2Q9, getattr(O, coll), (2 * R + 1, 2 * R + 1, 1), (1, 1, 1), wl.tau, g=wl.g[rows],
                     force_kind="rows", u0=np.ascontiguousarray(u0))
         orc.step(STEPS)
         fo = orc.populations()[:, 0, R, R]

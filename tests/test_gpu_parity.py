@@ -22,13 +22,14 @@ SHAPES = {"D2Q9": [(150, 37, 1), (530, 9, 1)], "D3Q19": [(70, 9, 7), (130, 5, 4)
 # SMRT_TRIM: tau_3 = tau_4 = 1, the kernels' trimmed collision (orders 3 and 4
 # relax to zero exactly); the oracle runs its one general collision for both.
 # SMRT_FNEQ: the force's non-equilibrium terms (Eq. Frc, third and fourth).
+# MRT_RAW: the raw-moment MRT of the appendix.
 TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1), "SMRT_TRIM": (1.0, 1.3, 0.63, 1.0, 1.0),
-       "SMRT_FNEQ": (1.0, 1.3, 0.63, 0.87, 1.1)}
-COLLS = ["BGK", "SMRT", "SMRT_TRIM", "SMRT_FNEQ"]
+       "SMRT_FNEQ": (1.0, 1.3, 0.63, 0.87, 1.1), "MRT_RAW": (1.0, 1.3, 0.63, 0.87, 1.1)}
+COLLS = ["BGK", "SMRT", "SMRT_TRIM", "SMRT_FNEQ", "MRT_RAW"]
 
 
 def _model(coll):
-    return {"BGK": "BGK", "SMRT_FNEQ": "SMRT_FNEQ"}.get(coll, "SMRT")
+    return "SMRT" if coll == "SMRT_TRIM" else coll
 
 
 def _D(lat):
@@ -48,7 +49,7 @@ def _random_state(lat, shape, seed, solid=None, amp=0.02):
 
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("coll", ["BGK", "SMRT", "SMRT_FNEQ"])
+@pytest.mark.parametrize("coll", ["BGK", "SMRT", "SMRT_FNEQ", "MRT_RAW"])
 def test_initial_populations(lat, coll):
     shape = SHAPES[lat][0]
     rho0, u0 = W.random_near_equilibrium(lat, shape, seed=21, du=0.03)
@@ -114,7 +115,7 @@ def test_poiseuille_channel_f64():
 
 @pytest.mark.parametrize("kind", ["rows", "field"])
 @pytest.mark.parametrize("lat", ["D2Q9", "D3Q27"])
-@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ"])
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_FNEQ", "MRT_RAW"])
 def test_force_kinds(kind, lat, coll):
     shape = SHAPES[lat][0]
     nx, ny, nz = shape
@@ -142,7 +143,7 @@ def test_force_kinds(kind, lat, coll):
 
 @pytest.mark.parametrize("lat", LATTICES)
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16"])
-@pytest.mark.parametrize("coll", ["SMRT", "SMRT_TRIM", "SMRT_FNEQ"])
+@pytest.mark.parametrize("coll", ["SMRT", "SMRT_TRIM", "SMRT_FNEQ", "MRT_RAW"])
 def test_one_step_reduced_storage(lat, storage, coll):
     """One step from the same stored (rounded) state: GPU (FP32 arithmetic,
     rounding on store) vs the oracle (FP64 arithmetic, same rounding)."""
