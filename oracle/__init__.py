@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("collision", C.c_int),
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("periodic", C.c_int * 3), ("tau", C.c_double * 5)]
+                ("periodic", C.c_int * 3), ("tau", C.c_double * 5), ("tau_bulk", C.c_double)]
 
 
 def lib():
@@ -103,7 +103,7 @@ def set_threads(n: int) -> int:
     return int(lib().or_set_threads(int(n)))
 
 
-def make_params(lattice, collision, shape, periodic=(1, 1, 1), tau=(1.0, 1.0, 0.8, 1.0, 1.0)):
+def make_params(lattice, collision, shape, periodic=(1, 1, 1), tau=(1.0, 1.0, 0.8, 1.0, 1.0), tau_bulk=0.0):
     nx, ny, nz = (list(shape) + [1, 1])[:3]
     p = Params()
     p.lattice, p.collision = int(lattice), int(collision)
@@ -113,6 +113,7 @@ def make_params(lattice, collision, shape, periodic=(1, 1, 1), tau=(1.0, 1.0, 0.
     t = list(tau) + [1.0] * (5 - len(tau))
     for k in range(5):
         p.tau[k] = float(t[k])
+    p.tau_bulk = float(tau_bulk)
     return p
 
 
@@ -222,8 +223,8 @@ class Sim:
     ``populations()`` / ``set_populations()`` speak fbar."""
 
     def __init__(self, lattice, collision, shape, periodic=(1, 1, 1), tau=(1, 1, 0.8, 1, 1),
-                 g=None, force_kind="uniform", solid=None, rho0=None, u0=None, round_mode=0):
-        self.p = make_params(lattice, collision, shape, periodic, tau)
+                 g=None, force_kind="uniform", solid=None, rho0=None, u0=None, round_mode=0, tau_bulk=0.0):
+        self.p = make_params(lattice, collision, shape, periodic, tau, tau_bulk)
         self.D, self.Q = LATTICE_DQ[lattice]
         p = self.p
         self.N = p.nx * p.ny * p.nz

@@ -25,6 +25,10 @@
  *    d_F^(n) = n g d^(n-1) for n <= 4 (Eq. Frc, third and fourth terms), with
  *    d^(n-1) the moments of f itself, recovered from those of fbar by
  *    inverting Eq. (newf) order by order.
+ *  - the second-order relaxation of both SMRT forms may split into the
+ *    traceless (shear) part and the trace (bulk) part, tau_{2,2} = tau[2] and
+ *    tau_{2,0} = tau_bulk (Eq. domg).  Orders 3 and 4 keep one tau each: their
+ *    trace parts need components the lattices do not carry.
  *  - the fourth collision mode (OR_MRT_RAW) is the raw-moment MRT of the
  *    appendix: per-order relaxation of the raw non-equilibrium moments, the
  *    fourth order from the appendix's recursion, the force's equilibrium part
@@ -342,9 +346,26 @@ static void force_order(const or_lattice *L, int n, const double *g, const doubl
     }
 }
 
-static void collide_smrt(const or_lattice *L, const double *tau, int fneq, const double *dev,
+/* The second-order block with its traceless (shear) and trace (bulk) parts
+ * scaled separately, Eq. (domg) with tau_{2,2} and tau_{2,0}:
+ *   out = cs (X - delta tr(X)/D) + cb delta tr(X)/D
+ *       = cs X + (cb - cs) delta tr(X)/D. */
+static void split_order2(const or_lattice *L, double cs, double cb, const double *X, double *out)
+{
+    const int o = L->off[2], D = L->D;
+    double tr = 0.0;
+    for (int a = 0; a < D; ++a) tr += X[o + a + a * D];
+    tr /= D;
+    for (int k = o; k < L->off[3]; ++k) {
+        const double iso = L->dig[k][0] == L->dig[k][1] ? tr : 0.0;
+        out[k] = cs * X[k] + (cb - cs) * iso;
+    }
+}
+
+static void collide_smrt(const or_lattice *L, const double *tau, double tau_b, int fneq, const double *dev,
                          const double *gL, double *dpop, double *dbg)
 {
+    double X[OR_PACK];
     double drho, rho, u[3], g[3], mu[3];
     double abar[OR_PACK], a0[OR_PACK], a1[OR_PACK], d1[OR_PACK], dp[OR_PACK], ap[OR_PACK];
     double tot[OR_PACK], dF[OR_PACK], d[OR_PACK];
@@ -373,17 +394,28 @@ static void collide_smrt(const or_lattice *L, const double *tau, int fneq, const
     if (fneq) {
         for (int n = 2; n <= OR_MAXN; ++n) {
             force_order(L, n, g, d, dF);
-            for (int k = L->off[n]; k < L->off[n + 1]; ++k)
-                d[k] = (1.0 - 0.5 / tau[n]) * (d1[k] + 0.5 * dF[k]);
+            for (int k = L->off[n]; k < L->off[n + 1]; ++k) X[k] = d1[k] + 0.5 * dF[k];
+            if (n == 2) {
+                split_order2(L, 1.0 - 0.5 / tau[2], 1.0 - 0.5 / tau_b, X, d);
+            } else {
+                for (int k = L->off[n]; k < L->off[n + 1]; ++k) d[k] = (1.0 - 0.5 / tau[n]) * X[k];
+            }
         }
     }
     /* relaxation with the force, order by order (Eq. RHS, explicit form):
-     * d_p^(n) = (1 - 1/tau_n) d_1^(n) + (1 - 1/(2 tau_n)) d_F^(n), d_p^(0) = 0 */
+     * d_p^(n) = (1 - 1/tau_n) d_1^(n) + (1 - 1/(2 tau_n)) d_F^(n), d_p^(0) = 0,
+     * the second order per traceless part (shear tau[2], bulk tau_b) */
     dp[0] = 0.0;
     for (int n = 1; n <= OR_MAXN; ++n) {
         const double t = tau[n];
         for (int k = L->off[n]; k < L->off[n + 1]; ++k)
             dp[k] = (1.0 - 1.0 / t) * d1[k] + (1.0 - 0.5 / t) * dF[k];
+    }
+    {
+        double r1[OR_PACK], r2[OR_PACK];
+        split_order2(L, 1.0 - 1.0 / tau[2], 1.0 - 1.0 / tau_b, d1, r1);
+        split_order2(L, 1.0 - 0.5 / tau[2], 1.0 - 0.5 / tau_b, dF, r2);
+        for (int k = L->off[2]; k < L->off[3]; ++k) dp[k] = r1[k] + r2[k];
     }
     shift(L, u, dp, ap);                    /* RCM -> RM (Eq. bbd1) */
     for (int k = 0; k < P; ++k) tot[k] = a0[k] + ap[k];
@@ -482,6 +514,7 @@ typedef struct {
     int nx, ny, nz;
     int periodic[3];
     double tau[5];
+    double tau_bulk;  /* tau_{2,0} of the SMRT forms; <= 0 means tau[2] */
 } or_params;
 
 static int check_params(const or_params *p, or_lattice *L)
@@ -491,6 +524,10 @@ static int check_params(const or_params *p, or_lattice *L)
     lattice_init(p->lattice, L);
     if (L->D == 2 && p->nz != 1) return -1;
     if (p->collision == OR_BGK && !(p->tau[2] > 0.5)) return -1;
+    if (p->tau_bulk > 0.0 && p->tau_bulk != p->tau[2] &&
+        !(p->collision == OR_SMRT || p->collision == OR_SMRT_FNEQ))
+        return -1;
+    if (p->tau_bulk > 0.0 && !(p->tau_bulk > 0.5)) return -1;
     if (p->collision != OR_BGK)
         for (int n = 2; n <= 4; ++n)
             if (!(p->tau[n] > 0.5)) return -1;
@@ -576,7 +613,8 @@ int or_collide_node(const or_params *p, const double *fbar, const double *gL, do
     for (int i = 0; i < L.Q; ++i) dev[i] = fbar[i] - L.w[i];
     if (p->collision == OR_BGK) collide_bgk(&L, p->tau, dev, gL, dp);
     else if (p->collision == OR_MRT_RAW) collide_mrt_raw(&L, p->tau, dev, gL, dp);
-    else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, dev, gL, dp, dbg);
+    else collide_smrt(&L, p->tau, p->tau_bulk > 0.0 ? p->tau_bulk : p->tau[2], p->collision == OR_SMRT_FNEQ,
+                      dev, gL, dp, dbg);
     for (int i = 0; i < L.Q; ++i) fp[i] = L.w[i] + dp[i];
     return 0;
 }
@@ -642,7 +680,8 @@ int or_step(const or_params *p, const unsigned char *solid, const double *g,
         for (int k = 0; k < L.D; ++k) gL[k] = g ? g[(size_t)k * N + x] : 0.0;
         if (p->collision == OR_BGK) collide_bgk(&L, p->tau, fb, gL, fp);
         else if (p->collision == OR_MRT_RAW) collide_mrt_raw(&L, p->tau, fb, gL, fp);
-        else collide_smrt(&L, p->tau, p->collision == OR_SMRT_FNEQ, fb, gL, fp, NULL);
+        else collide_smrt(&L, p->tau, p->tau_bulk > 0.0 ? p->tau_bulk : p->tau[2],
+                          p->collision == OR_SMRT_FNEQ, fb, gL, fp, NULL);
         const int X = (int)(x % nx), Y = (int)((x / nx) % ny), Z = (int)(x / ((size_t)nx * ny));
         for (int i = 0; i < L.Q; ++i) {
             int t[3] = {X + L.c[i][0], Y + L.c[i][1], Z + L.c[i][2]};

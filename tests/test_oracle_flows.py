@@ -126,6 +126,37 @@ def test_poiseuille_smrt_second_difference(coll):
     assert np.abs(d2 + 1e-6 / nu).max() < 1e-8 * 1e-6 / nu * 1e3
 
 
+@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q27])
+@pytest.mark.parametrize("tau_b", [0.6, 0.8, 1.4])
+def test_sound_attenuation_follows_bulk_viscosity(lat, tau_b):
+    """A standing sound wave rho = 1 + eps cos(kx) decays at
+    Gamma = k^2/2 [2 c_s^2 (tau_2 - 1/2)(D - 1)/D + (2/D) c_s^2 (tau_bulk - 1/2)]
+    (linearised Navier-Stokes with shear viscosity c_s^2 (tau_2 - 1/2) and
+    bulk viscosity (2/D) c_s^2 (tau_bulk - 1/2), the Chapman-Enskog result of
+    relaxing the trace of the second order with its own time, Eq. domg).
+    The acoustic energy c_s^2 A_rho^2 + A_u^2 decays as exp(-2 Gamma t)."""
+    D = O.LATTICE_DQ[lat][0]
+    nx, cs2, tau_s = 64, 1.0 / 3.0, 0.8
+    k = 2 * math.pi / nx
+    x = np.arange(nx)
+    shape = (nx, 1, 1)
+    rho0 = np.broadcast_to(1 + 1e-4 * np.cos(k * x), (1, 1, nx)).copy()
+    s = O.Sim(lat, O.SMRT, shape, (1, 1, 1), (1, 1, tau_s, 1, 1), rho0=rho0, tau_bulk=tau_b)
+    t, E = [], []
+    for n in range(0, 1201, 3):
+        if n:
+            s.step(3)
+        r, u, _ = s.moments()
+        Ar = 2 / nx * ((r[0, 0] - 1) * np.cos(k * x)).sum()
+        Au = 2 / nx * (u[0, 0, 0] * np.sin(k * x)).sum()
+        t.append(n)
+        E.append(cs2 * Ar * Ar + Au * Au)
+    t, E = np.array(t), np.array(E)
+    gamma = -np.polyfit(t[50:], np.log(E[50:]), 1)[0] / 2
+    theory = 0.5 * k * k * (2 * cs2 * (tau_s - 0.5) * (D - 1) / D + (2 / D) * cs2 * (tau_b - 0.5))
+    assert abs(gamma / theory - 1) < 5e-3, (gamma, theory)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
 def test_taylor_green_second_order(coll):

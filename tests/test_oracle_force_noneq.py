@@ -54,7 +54,7 @@ def _moment_matrix(xi, u, mult):
     return M
 
 
-def _trapezoidal_step(lat, fbar, gL, tau_hat, fneq):
+def _trapezoidal_step(lat, fbar, gL, tau_hat, fneq, tau_bulk=None):
     D, Q, c, w, _ = O.lattice_tables(lat)
     xi = SQ3 * c[:, :D].astype(float)
     g = SQ3 * np.asarray(gL, float)
@@ -65,6 +65,15 @@ def _trapezoidal_step(lat, fbar, gL, tau_hat, fneq):
     M = _moment_matrix(xi, u, mult)
     Minv = np.linalg.inv(M)
     T = np.diag([0.0 if n < 2 else 1.0 / (tau_hat[min(n, 4)] - 0.5) for n in order])
+    if tau_bulk is not None:
+        # second order: traceless part at 1/tau_2, trace part at 1/tau_bulk
+        # (Eq. domg with tau_{2,2}, tau_{2,0}); P projects onto the trace part
+        diag = [r for r, m in enumerate(mult) if sorted(m)[-1] == 2 and sum(m) == 2]
+        P = np.zeros_like(T)
+        for r in diag:
+            P[r, diag] = 1.0 / D
+        two = np.diag((order == 2).astype(float))
+        T = T - two / (tau_hat[2] - 0.5) + (two - P) / (tau_hat[2] - 0.5) + P / (tau_bulk - 0.5)
     G = np.zeros((len(mult), len(mult)))
     index = {m: r for r, m in enumerate(mult)}
     for r, m in enumerate(mult):
@@ -114,6 +123,26 @@ def test_smrt_is_the_trapezoidal_rule(lat, coll):
         fp, _ = O.collide_node(p, f, gL)
         ref = _trapezoidal_step(lat, f, gL, tau_hat, coll == O.SMRT_FNEQ)
         assert np.abs(fp - ref).max() < 5e-15, (taus, np.abs(fp - ref).max())
+
+
+@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q27])
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ])
+def test_split_bulk_tau_is_the_trapezoidal_rule(lat, coll):
+    """Eq. (domg) with the second order split into its traceless (shear,
+    tau_2) and trace (bulk, tau_bulk) parts, as the same trapezoidal
+    statement with a non-diagonal second-order block."""
+    D = O.LATTICE_DQ[lat][0]
+    rng = np.random.default_rng(45 + lat)
+    for taus, tb in [((0.57, 0.83, 1.31), 1.7), ((0.9, 1.0, 1.0), 0.52), ((1.7, 0.61, 0.74), 0.8)]:
+        tau_hat = (1.0, 1.0) + taus
+        p = O.make_params(lat, coll, (2, 2, 2 if D == 3 else 1), tau=tau_hat, tau_bulk=tb)
+        f = _span_state(lat, rng)
+        gL = rng.normal(size=D) * 3e-3
+        fp, _ = O.collide_node(p, f, gL)
+        ref = _trapezoidal_step(lat, f, gL, tau_hat, coll == O.SMRT_FNEQ, tau_bulk=tb)
+        assert np.abs(fp - ref).max() < 5e-15, (taus, tb, np.abs(fp - ref).max())
+        plain = _trapezoidal_step(lat, f, gL, tau_hat, coll == O.SMRT_FNEQ)
+        assert np.abs(ref - plain).max() > 1e-5
 
 
 @pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q27])
