@@ -111,6 +111,12 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *ctx); /* optional device allocator */
     void (*free_)(void *ptr, void *ctx);     /* its release function */
     void *alloc_ctx;
+    double tau_bulk;      /* relaxation time of the trace (bulk) part of the
+                             second-order moments, tau_{2,0} of Eq. (domg); the
+                             traceless (shear) part keeps tau[2].  0 => tau[2].
+                             Otherwise > 1/2, and a value other than tau[2] is
+                             for LBM_SMRT / LBM_SMRT_FNEQ only (LBM_ERR_ARG).
+                             The bulk viscosity is (2/D)(tau_bulk - 1/2)/3. */
 } lbm_desc;
 
 /* Create a lattice: validates the description, allocates two population
@@ -150,6 +156,20 @@ lbm_status lbm_check_device(lbm_handle *h, double *out_dev);
 /* Replace the body force (same kind and layout as at creation); takes effect
  * for the next step.  Asynchronous (the host array is copied first). */
 lbm_status lbm_set_force(lbm_handle *h, const double *g);
+
+/* Time-dependent uniform body force from a table, for forcing such as the
+ * oscillating pressure gradient of the Womersley case (Sec. III.B) without a
+ * host call per step: table[t][a] (period x D doubles, host, copied) is the
+ * acceleration g of the t-th step after this call, repeating with the
+ * given period, i.e. the collision of step s (and the velocity of
+ * Eq. half_F reported at step s) uses table[s mod period], s counted from
+ * this call.  The step counter lives on the device, so the schedule runs
+ * inside the captured step graphs.  Requires LBM_G_UNIFORM at creation
+ * (else LBM_ERR_STATE).  period = 0 removes the schedule (the force set
+ * last by lbm_set_force or at creation applies again); lbm_set_force also
+ * removes it.  The schedule's phase is not part of lbm_get_state's state.
+ * Synchronises the handle's stream. */
+lbm_status lbm_set_force_schedule(lbm_handle *h, const double *table, int64_t period);
 
 /* Pre-collision populations fbar_i(x, t) in FP64, host layout f[i][z][y][x]
  * (solid nodes: w_i).  Synchronises. */

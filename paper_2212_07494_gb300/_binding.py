@@ -35,7 +35,7 @@ class lbm_desc(C.Structure):
                 ("g", C.POINTER(C.c_double)), ("solid", C.POINTER(C.c_uint8)),
                 ("rho0", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free_", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("tau_bulk", C.c_double)]
 
 
 class LbmError(RuntimeError):
@@ -68,6 +68,7 @@ def library():
     L.lbm_residual.argtypes = [H, C.c_int, dp]
     L.lbm_check_device.argtypes = [H, C.c_void_p]
     L.lbm_set_force.argtypes = [H, dp]
+    L.lbm_set_force_schedule.argtypes = [H, dp, C.c_int64]
     L.lbm_get_populations.argtypes = [H, dp]
     L.lbm_set_populations.argtypes = [H, dp]
     L.lbm_state_bytes.argtypes = [H]
@@ -102,7 +103,7 @@ def library():
     L.lbm_last_error.restype = C.c_char_p
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
               "lbm_check_device",
-              "lbm_set_force", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
+              "lbm_set_force", "lbm_set_force_schedule", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
               "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc",
               "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
               "lbm_batch_moments", "lbm_batch_get_populations", "lbm_batch_set_tiles", "lbm_batch_autotune",
@@ -138,7 +139,8 @@ def _enum(kind, v):
 
 
 def make_desc(lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1), g=None,
-              force_kind=None, solid=None, rho0=None, u0=None, stream=None, alloc=None, free=None):
+              force_kind=None, solid=None, rho0=None, u0=None, stream=None, alloc=None, free=None,
+              tau_bulk=0.0):
     """Build an lbm_desc plus the arrays it points to (kept in the returned
     ``keep`` list for as long as the descriptor is used)."""
     lat = _enum("lattice", lattice)
@@ -157,6 +159,7 @@ def make_desc(lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1),
     for k in range(5):
         d.tau[k] = float(t[k])
     d.force_kind = fk
+    d.tau_bulk = float(tau_bulk)
     keep = []
     if fk != LBM_G_NONE:
         n = {LBM_G_UNIFORM: D, LBM_G_ROWS: ny * D, LBM_G_FIELD: D * N}[fk]
@@ -221,6 +224,10 @@ def lbm_set_force(h, g):
     _check(library().lbm_set_force(h, _dptr(g)), h)
 
 
+def lbm_set_force_schedule(h, table, period):
+    _check(library().lbm_set_force_schedule(h, _dptr(table) if table is not None else None, int(period)), h)
+
+
 def lbm_get_populations(h, out):
     _check(library().lbm_get_populations(h, _dptr(out)), h)
 
@@ -277,7 +284,7 @@ class Lattice:
     creates its own stream and uses cudaMalloc."""
 
     def __init__(self, lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1), g=None,
-                 force_kind=None, solid=None, rho0=None, u0=None, torch_stream=None):
+                 force_kind=None, solid=None, rho0=None, u0=None, torch_stream=None, tau_bulk=0.0):
         self.lattice = _enum("lattice", lattice)
         self.D, self.Q = _DQ[self.lattice]
         nx, ny, nz = (list(shape) + [1, 1])[:3]
@@ -301,7 +308,7 @@ class Lattice:
             alloc, free = ALLOC_FN(_alloc), FREE_FN(_free)
             self._cb = [alloc, free]
         desc, keep = make_desc(lattice, collision, shape, tau, storage, periodic, g, force_kind,
-                               solid, rho0, u0, stream, alloc, free)
+                               solid, rho0, u0, stream, alloc, free, tau_bulk)
         self.signature_fields = (desc.lattice, desc.collision, desc.storage, nx, ny, nz, solid is not None)
         self.force_kind = desc.force_kind
         self.h = lbm_create(desc)
@@ -331,6 +338,17 @@ class Lattice:
 
     def set_force(self, g):
         lbm_set_force(self.h, _f64(g))
+
+    def set_force_schedule(self, table):
+        """table: (period, D) accelerations of the next `period` steps, repeating;
+        None removes the schedule."""
+        if table is None:
+            lbm_set_force_schedule(self.h, None, 0)
+            return
+        t = np.ascontiguousarray(np.asarray(table, np.float64))
+        if t.ndim != 2 or t.shape[1] != self.D:
+            raise ValueError("schedule must have shape (period, D)")
+        lbm_set_force_schedule(self.h, t.ravel(), t.shape[0])
 
     def populations(self):
         f = np.empty(self.Q * self.N)

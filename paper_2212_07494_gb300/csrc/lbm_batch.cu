@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                     }
                     // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it, so
                     // that a channel evolves with the same arithmetic here and alone
-                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
-                    else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4);
+                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2, om2);
+                    else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
                     else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
                     T *dst = fout + (y * C.nxp + x);
 #pragma unroll
@@ -770,6 +770,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
             return bfail(nullptr, LBM_ERR_ARG, "batch channels take a uniform force or none");
         if (d.force_kind == LBM_G_UNIFORM && !d.g) return bfail(nullptr, LBM_ERR_ARG, "force values are NULL");
         if (d.collision == LBM_BGK && !(d.tau[2] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2] must be > 1/2");
+        if (d.tau_bulk != 0.0 && d.tau_bulk != d.tau[2])
+            return bfail(nullptr, LBM_ERR_ARG, "batches relax the second order with one tau (tau_bulk 0 or tau[2])");
         if (d.collision == LBM_SMRT)
             for (int k = 2; k <= 4; ++k)
                 if (!(d.tau[k] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");

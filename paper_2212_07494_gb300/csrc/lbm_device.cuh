@@ -169,6 +169,15 @@ struct KParams {
     const unsigned char *solid;    // [plane] or null
     double om[5];                  // 1 / tau_n
     float om32[5];
+    double omb;                    // 1 / tau of the trace (bulk) part of order 2; om[2] unless split
+    float omb32;
+    // force schedule (uniform g per step) or null: step t of the schedule uses
+    // gs[3 * ((*gs_t + gs_off) mod gs_period)]
+    const double *gs;
+    const float *gs32;
+    const long long *gs_t;         // steps since the schedule was set, mod gs_period (device)
+    long long gs_period;
+    int gs_off;                    // this launch's offset from *gs_t within its chunk
     // per population i, relative to a node's element index:
     long long doff[27];            // i*plane - (cx + cy*nxp + cz*nxp*ny): pull source
     long long poff[27];            // i*plane: the node's own entry
@@ -255,11 +264,29 @@ template <int L, typename R> __host__ __device__ __forceinline__ void reconstruc
 }
 
 // ------------------------------------------------------------------ collisions
+// Second-order central moments scaled by (1 - a) in their traceless (shear)
+// part and (1 - b) in their trace (bulk) part, Eq. (domg) with tau_{2,2} and
+// tau_{2,0}: G <- (1 - a) G + (a - b) delta tr(G)/D.  The grid entries with
+// per-axis orders 2e_k are the diagonal components; with a = b the added
+// term is an exact zero.
+template <int D, typename R> __host__ __device__ __forceinline__ void relax_order2(R *G, R a, R b) {
+    constexpr int N = Grid<D>::N;
+    R tr = G[2] + G[6];
+    if constexpr (D == 3) tr += G[18];
+    const R iso = tr * R(1.0 / D) * (a - b);
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+        if (morder<D>(g) != 2) continue;
+        const bool diag = g == 2 || g == 6 || g == 18;
+        G[g] = diag ? (R(1) - a) * G[g] + iso : (R(1) - a) * G[g];
+    }
+}
+
 // G holds the deviations delta on the velocity grid (zeros off-lattice) and is
 // overwritten with the post-collision deviations.  g: acceleration (lattice
 // units).  Returns nothing; rho/u are recomputed by the moments kernel.
 template <int L, typename R>
-__host__ __device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+__host__ __device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
     constexpr int D = Lat<L>::D;
     constexpr int N = Grid<D>::N;
     constexpr int EX = 1, EY = 3, EZ = 9;
@@ -274,11 +301,11 @@ __host__ __device__ __forceinline__ void collide_smrt(R *G, R gx, R gy, R gz, R 
     shift<D>(G, -ux, -uy, -uz);           // central moments of fbar
     // relaxation of the non-equilibrium central moments (equilibrium ones are
     // rho delta_{n0}); the force enters at first order only: d_p^(1) = rho g/2
+    relax_order2<D>(G, om2, omb);
 #pragma unroll
     for (int g = 0; g < N; ++g) {
         const int n = morder<D>(g);
-        if (n == 2) G[g] *= (R(1) - om2);
-        else if (n == 3) G[g] *= (R(1) - om3);
+        if (n == 3) G[g] *= (R(1) - om3);
         else if (n == 4) G[g] *= (R(1) - om4);
         else if (n >= 5) G[g] = R(0);
     }
@@ -417,7 +444,7 @@ __host__ __device__ __forceinline__ void shift_pass(R *a, R v) {
 // collide_smrt, whose orders-3/4 factors (1 - om) are then exactly zero,
 // with the passes restricted to what is non-zero or read.
 template <int L, typename R>
-__host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R gz, R om2) {
+__host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R gz, R om2, R omb) {
     constexpr int D = Lat<L>::D;
     constexpr int N = Grid<D>::N;
     constexpr int EX = 1, EY = 3, EZ = 9;
@@ -442,10 +469,7 @@ __host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R g
     shift_pass<D, 0, ALL, LOW>(G, -ux);
     shift_pass<D, 1, ALL, LOW>(G, -uy);
     if constexpr (D == 3) shift_pass<D, 2, ALL, LOW>(G, -uz);
-    static_for<N>([&](auto I) {
-        constexpr int g = decltype(I)::value;
-        if constexpr (((LOW >> g) & 1u) && morder<D>(g) == 2) G[g] *= (R(1) - om2);
-    });
+    relax_order2<D>(G, om2, omb);
     G[0] = rho;
     G[EX] = R(0.5) * rho * gx;
     G[EY] = R(0.5) * rho * gy;
@@ -481,7 +505,7 @@ __host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R g
 // d_F^(2) = 0, d_F^(3) = 3 g d^(2) and d_F^(4) = 4 g d^(3), each order needing
 // the one below it.  Relaxation as in collide_smrt with these d_F added.
 template <int L, typename R>
-__host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R gz, R om2, R om3, R om4) {
+__host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
     constexpr int D = Lat<L>::D;
     constexpr int N = Grid<D>::N;
     constexpr int EX = 1, EY = 3, EZ = 9;
@@ -497,7 +521,8 @@ __host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R g
     const R ga[3] = {gx, gy, gz};
     R d2[N], F3[N], d3[N];                // second- and third-order central moments of f, d_F^(3)
 #pragma unroll
-    for (int g = 0; g < N; ++g) d2[g] = morder<D>(g) == 2 ? (R(1) - R(0.5) * om2) * G[g] : R(0);
+    for (int g = 0; g < N; ++g) d2[g] = morder<D>(g) == 2 ? G[g] : R(0);
+    relax_order2<D>(d2, R(0.5) * om2, R(0.5) * omb);   // d^(2) = (1 - om/2) dbar_1^(2) per part
 #pragma unroll
     for (int g = 0; g < N; ++g) {
         F3[g] = R(0);
@@ -508,11 +533,11 @@ __host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R g
         }
         d3[g] = morder<D>(g) == 3 ? (R(1) - R(0.5) * om3) * (G[g] + R(0.5) * F3[g]) : R(0);
     }
+    relax_order2<D>(G, om2, omb);
 #pragma unroll
     for (int g = 0; g < N; ++g) {
         const int n = morder<D>(g);
-        if (n == 2) G[g] *= (R(1) - om2);
-        else if (n == 3) G[g] = (R(1) - om3) * G[g] + (R(1) - R(0.5) * om3) * F3[g];
+        if (n == 3) G[g] = (R(1) - om3) * G[g] + (R(1) - R(0.5) * om3) * F3[g];
         else if (n == 4) {
             R F4 = R(0);
 #pragma unroll
@@ -743,6 +768,9 @@ __device__ __forceinline__ void gather(const KParams &p, const typename Store<ST
 }
 
 template <typename R> __device__ __forceinline__ const R *force_ptr(const KParams &p);
+template <typename R> __device__ __forceinline__ const R *sched_ptr(const KParams &p);
+template <> __device__ __forceinline__ const double *sched_ptr<double>(const KParams &p) { return p.gs; }
+template <> __device__ __forceinline__ const float *sched_ptr<float>(const KParams &p) { return p.gs32; }
 template <> __device__ __forceinline__ const double *force_ptr<double>(const KParams &p) { return p.g; }
 template <> __device__ __forceinline__ const float *force_ptr<float>(const KParams &p) { return p.g32; }
 
@@ -752,6 +780,14 @@ __device__ __forceinline__ void load_force(const KParams &p, int y, long long no
     constexpr int D = Lat<L>::D;
     const R *g = force_ptr<R>(p);
     gx = gy = gz = R(0);
+    if (p.gs != nullptr) {                // scheduled uniform force of this step
+        const long long t = (*p.gs_t + p.gs_off) % p.gs_period;
+        const R *s = sched_ptr<R>(p) + 3 * t;
+        gx = s[0];
+        gy = s[1];
+        if (D == 3) gz = s[2];
+        return;
+    }
     if (p.force_kind == G_UNIFORM) {
         gx = __ldg(g + 0);
         gy = __ldg(g + 1);
@@ -770,5 +806,8 @@ __device__ __forceinline__ void load_force(const KParams &p, int y, long long no
 template <typename R> __device__ __forceinline__ R omega(const KParams &p, int n);
 template <> __device__ __forceinline__ double omega<double>(const KParams &p, int n) { return p.om[n]; }
 template <> __device__ __forceinline__ float omega<float>(const KParams &p, int n) { return p.om32[n]; }
+template <typename R> __device__ __forceinline__ R omega_bulk(const KParams &p);
+template <> __device__ __forceinline__ double omega_bulk<double>(const KParams &p) { return p.omb; }
+template <> __device__ __forceinline__ float omega_bulk<float>(const KParams &p) { return p.omb32; }
 
 }  // namespace lbm

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         if (MASK && act[k]) act[k] = p.solid[node_index(p, x, y, z)] == 0;
         if (act[k]) gather<L, ST, MASK>(p, fin, x, y, z, G[k]);
     }
-    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4);
+    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4), omb = omega_bulk<R>(p);
     R gx, gy, gz;
     const bool per_node_force = p.force_kind == G_FIELD;
     if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
@@ -36,9 +36,9 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         const int x = x0 + k * blockDim.x;
         const long long own = node_index(p, x, y, z);
         if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
-        if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4);
-        else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2);
-        else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4);
+        if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
+        else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2, omb);
+        else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
         else if (COLL == MRT_RAW) collide_mrt_raw<L>(G[k], gx, gy, gz, om2, om3, om4);
         else collide_bgk<L>(G[k], gx, gy, gz, om2);
         typename Store<ST>::T *dst = fout + own;

@@ -57,6 +57,10 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, dou
     }
 }
 
+// advance the force schedule's step counter by n (one thread; the counter is
+// read by the step and moments kernels and kept below the period)
+__global__ void k_sched_advance(long long *t, long long n, long long period) { *t = (*t + n) % period; }
+
 cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
@@ -89,6 +93,10 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // graph_steps steps starting from buf[0] / buf[1]
+    double *gs_dev = nullptr;    // force schedule [period][3], FP64 and FP32 copies
+    float *gs32_dev = nullptr;
+    long long *gs_t_dev = nullptr;
+    int64_t gs_period = 0;
     int graph_steps = 0;
     int64_t step = 0;
     void *(*alloc)(size_t, void *) = nullptr;
@@ -183,13 +191,42 @@ lbm_status upload_force(lbm_handle *h, const double *g) {
 
 lbm_status launch_steps(lbm_handle *h, int64_t n) {
     const Launchers &L = launchers_for(h->lattice);
+    KParams kp = h->kp;
     for (int64_t s = 0; s < n; ++s) {
-        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, h->kp, h->buf[h->cur],
+        kp.gs_off = (int)s;   // with a force schedule: step s of this chunk
+        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, kp, h->buf[h->cur],
                                h->buf[1 - h->cur], h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
         h->cur = 1 - h->cur;
     }
+    if (h->gs_dev && n > 0) {
+        k_sched_advance<<<1, 1, 0, h->stream>>>(h->gs_t_dev, (long long)n, (long long)h->gs_period);
+        LBM_CUDA(h, cudaGetLastError());
+    }
     return LBM_OK;
+}
+
+// graphs bake kernel parameters: drop them when those change
+void drop_graphs(lbm_handle *h) {
+    for (cudaGraphExec_t &ge : h->graph)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
+}
+
+void free_schedule(lbm_handle *h) {
+    dev_free(h, h->gs_dev);
+    dev_free(h, h->gs32_dev);
+    dev_free(h, h->gs_t_dev);
+    h->gs_dev = nullptr;
+    h->gs32_dev = nullptr;
+    h->gs_t_dev = nullptr;
+    h->gs_period = 0;
+    h->kp.gs = nullptr;
+    h->kp.gs32 = nullptr;
+    h->kp.gs_t = nullptr;
+    h->kp.gs_period = 0;
 }
 
 // the graph of graph_steps steps that starts from the buffer holding the
@@ -284,6 +321,9 @@ void lbm_destroy(lbm_handle *h) {
     dev_free(h, h->red_dev);
     dev_free(h, h->uprev);
     dev_free(h, h->fields);
+    dev_free(h, h->gs_dev);
+    dev_free(h, h->gs32_dev);
+    dev_free(h, h->gs_t_dev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -305,6 +345,11 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     if (d->collision != LBM_BGK)
         for (int n = 2; n <= 4; ++n)
             if (!(d->tau[n] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");
+    if (d->tau_bulk != 0.0) {
+        if (!(d->tau_bulk > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau_bulk must be 0 or > 1/2");
+        if (d->tau_bulk != d->tau[2] && d->collision != LBM_SMRT && d->collision != LBM_SMRT_FNEQ)
+            return fail(nullptr, LBM_ERR_ARG, "tau_bulk applies to the SMRT collisions only");
+    }
     if ((d->alloc == nullptr) != (d->free_ == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free_ must be given together");
 
@@ -342,6 +387,8 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
         kp.om[n] = d->tau[n] > 0.0 ? 1.0 / d->tau[n] : 0.0;
         kp.om32[n] = (float)kp.om[n];
     }
+    kp.omb = d->tau_bulk != 0.0 ? 1.0 / d->tau_bulk : kp.om[2];
+    kp.omb32 = (float)kp.omb;
     if (d->lattice == LBM_D2Q9) fill_offsets<D2Q9>(kp);
     else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
     else fill_offsets<D3Q27>(kp);
@@ -559,7 +606,58 @@ lbm_status lbm_check_device(lbm_handle *h, double *out_dev) {
 lbm_status lbm_set_force(lbm_handle *h, const double *g) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (h->force_kind == LBM_G_NONE) return fail(h, LBM_ERR_STATE, "created without a force");
+    if (h->gs_dev) {
+        // a constant force replaces the schedule
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        free_schedule(h);
+    }
     return upload_force(h, g);
+}
+
+lbm_status lbm_set_force_schedule(lbm_handle *h, const double *table, int64_t period) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (h->force_kind != LBM_G_UNIFORM) return fail(h, LBM_ERR_STATE, "a force schedule needs LBM_G_UNIFORM");
+    if (period < 0 || (period > 0 && !table)) return fail(h, LBM_ERR_ARG, "bad schedule");
+    if (period > (int64_t)1 << 30) return fail(h, LBM_ERR_ARG, "schedule period too long");
+    std::vector<double> tmp((size_t)period * 3, 0.0);
+    for (int64_t t = 0; t < period; ++t)
+        for (int a = 0; a < h->D; ++a) {
+            const double v = table[t * h->D + a];
+            if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "schedule contains a non-finite value");
+            tmp[(size_t)t * 3 + a] = v;
+        }
+    std::vector<float> tmp32(tmp.begin(), tmp.end());
+    // in-flight steps may still read the old schedule
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    free_schedule(h);
+    if (period == 0) return LBM_OK;
+    lbm_status st = alloc_into(h, &h->gs_dev, tmp.size() * sizeof(double), "force schedule");
+    if (st == LBM_OK) st = alloc_into(h, &h->gs32_dev, tmp32.size() * sizeof(float), "force schedule");
+    if (st == LBM_OK) st = alloc_into(h, &h->gs_t_dev, sizeof(long long), "force schedule counter");
+    if (st != LBM_OK) {
+        free_schedule(h);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->gs32_dev, tmp32.data(), tmp32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gs_t_dev, 0, sizeof(long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free_schedule(h);
+        return cuda_fail(h, e, "force schedule upload");
+    }
+    h->gs_period = period;
+    h->kp.gs = h->gs_dev;
+    h->kp.gs32 = h->gs32_dev;
+    h->kp.gs_t = h->gs_t_dev;
+    h->kp.gs_period = period;
+    h->kp.gs_off = 0;
+    return LBM_OK;
 }
 
 lbm_status lbm_get_populations(lbm_handle *h, double *f) {

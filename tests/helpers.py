@@ -25,15 +25,15 @@ def rel_l2(a, b):
 
 
 def make_pair(lattice, collision, shape, tau, storage="F64", periodic=(1, 1, 1), g=None,
-              force_kind="uniform", solid=None, rho0=None, u0=None, emulate_storage=False):
+              force_kind="uniform", solid=None, rho0=None, u0=None, emulate_storage=False, tau_bulk=0.0):
     """(gpu Lattice, oracle Sim) built from identical inputs."""
     from paper_2212_07494_gb300 import Lattice
     gl = Lattice(lattice, collision, shape, tau, storage, periodic, g,
-                 force_kind if g is not None else "none", solid, rho0, u0)
+                 force_kind if g is not None else "none", solid, rho0, u0, tau_bulk=tau_bulk)
     og = None
     if g is not None:
         og = g
     orc = O.Sim(LAT[lattice], COLL[collision], shape, periodic, tau, g=og, force_kind=force_kind,
                 solid=solid, rho0=rho0, u0=u0,
-                round_mode=ROUND[storage] if emulate_storage else 0)
+                round_mode=ROUND[storage] if emulate_storage else 0, tau_bulk=tau_bulk)
     return gl, orc

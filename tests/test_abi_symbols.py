@@ -76,3 +76,17 @@ def test_check_noalloc_rejects_oversized_problems_before_device_work(lib):
     with pytest.raises(P.LbmError) as e:
         P.lbm_check_noalloc(desc, 1, 1, None)
     assert "solid" in str(e.value)
+
+
+def test_bulk_tau_arguments_are_checked_without_a_gpu(lib):
+    """A bulk relaxation time must exceed 1/2 and applies to the SMRT
+    collisions only; both are rejected before any device work."""
+    import paper_2212_07494_gb300 as P
+    lib.lbm_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_last_error.argtypes = [ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    for coll, tb in [("SMRT", 0.4), ("BGK", 0.9), ("MRT_RAW", 0.9), ("SMRT_FNEQ", -1.0)]:
+        d, keep = P.make_desc("D2Q9", coll, (8, 8), (1, 1, 0.8, 1, 1), tau_bulk=tb)
+        assert lib.lbm_create(ctypes.byref(d), ctypes.byref(h)) == -1, coll
+        assert b"tau_bulk" in lib.lbm_last_error(None)
