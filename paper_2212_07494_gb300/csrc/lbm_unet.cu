@@ -15,8 +15,10 @@
 // Concatenation is free: producers write into channel slices of one buffer.
 // Master weights and Adam moments are FP32; each update repacks the BF16
 // copies used by the forward and input-gradient kernels.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <string>
@@ -199,17 +201,35 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
 // The same implicit GEMM as k_conv on the 5th-generation tensor cores: a CTA
 // computes 128 pixels x NT output channels, accumulating in TMEM (128 lanes x
 // NT FP32 columns).  Operand tiles are staged by cp.async into shared memory
-// in the K-major layout without swizzle that the MMA reads through matrix
-// descriptors: 8-row x 16-byte core matrices, adjacent along K at TC_KSTEP
-// bytes, adjacent 8-row groups at (BK / 8) * TC_KSTEP bytes.
-constexpr int TC_KSTEP = 128;
+// in the swizzled K-major layout the MMA reads through matrix descriptors.
+// A tile row (one pixel, or one output channel of the weights) is the K
+// block's BK channels, ROWB = 2 BK bytes; rows follow each other at ROWB, and
+// the 16-byte chunk c of row r sits at chunk position c XOR sw(r), with
+// sw(r) = r mod 8 (BK 64, 128-byte swizzle), (r / 2) mod 4 (BK 32, 64-byte)
+// or (r / 4) mod 2 (BK 16, 32-byte): the address bits 4.. XORed with bits
+// 7.., which is the pattern of the descriptor's swizzle modes.  Eight rows
+// form one swizzle atom, so 8-row groups are 8 ROWB apart (the descriptor's
+// stride offset); a whole row is one atom wide, so the MMA's K slices of 16
+// channels start 32 bytes apart within it.  The pattern lets a warp copy
+// whole pixel rows (coalesced global reads) into shared memory without bank
+// conflicts.
 constexpr long TC_SPIN = 1L << 22;
 
-__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+template <int BK> __host__ __device__ constexpr int sw_rowbytes() { return 2 * BK; }
+// descriptor swizzle mode for a row of 2 BK bytes: 2 = 128B, 4 = 64B, 6 = 32B
+template <int BK> __host__ __device__ constexpr uint64_t sw_mode() { return BK == 64 ? 2 : (BK == 32 ? 4 : 6); }
+template <int BK> __device__ __forceinline__ int sw_off(int r, int c) {
+    const int x = BK == 64 ? (r & 7) : (BK == 32 ? ((r >> 1) & 3) : ((r >> 2) & 1));
+    return r * sw_rowbytes<BK>() + ((c ^ x) << 4);
+}
+
+template <int BK> __device__ __forceinline__ uint64_t tc_desc_sw(unsigned saddr) {
+    constexpr unsigned SBO = 8 * sw_rowbytes<BK>();
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family; no swizzle, base offset 0
+    d |= (uint64_t)1 << 16;                    // leading offset: unused by the swizzled K-major layout
+    d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                    // descriptor version of the sm_100 family; base offset 0
+    d |= sw_mode<BK>() << 61;
     return d;
 }
 // kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major
@@ -248,12 +268,58 @@ __device__ __forceinline__ bool ws_wait(unsigned long long *mbar, unsigned parit
     return false;
 }
 
+// Epilogue of the tcgen05 convolutions: warp w (0-3) reads TMEM lanes
+// 32w .. 32w + 31, one output pixel per thread (m; -1: none), NT FP32
+// columns, adds the bias, applies ReLU and the gate, and stores bf16.
+template <int NT>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, unsigned tmem, int warp, int lane, long long m,
+                                              int co0) {
+#pragma unroll
+    for (int c = 0; c < NT; c += 16) {
+        unsigned r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int cb = co0 + c;
+        if (m < 0 || cb >= a.cout) continue;
+        float v[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            v[jj] = __uint_as_float(r[jj]);
+            if (a.bias && cb + jj < a.cout) v[jj] += a.bias[cb + jj];
+            if (a.relu) v[jj] = fmaxf(v[jj], 0.f);
+        }
+        if (a.gate) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+                if (cb + jj < a.cout && !(__bfloat162float(a.gate[m * a.gc + a.go + cb + jj]) > 0.f)) v[jj] = 0.f;
+        }
+        bf16 *dst = a.y + m * a.yc + a.yo + cb;
+        if (cb + 16 <= a.cout) {
+            __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) o[jj] = __floats2bfloat162_rn(v[2 * jj], v[2 * jj + 1]);
+            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+        } else {
+            for (int jj = 0; jj < 16 && cb + jj < a.cout; ++jj) dst[jj] = __float2bfloat16_rn(v[jj]);
+        }
+    }
+}
+
 template <int BK, int NT>
 __global__ void __launch_bounds__(160) k_conv_ws(const ConvArgs a, int *err) {
     constexpr int ABYTES = 128 * BK * 2, BBYTES = NT * BK * 2, STAGE = ABYTES + BBYTES;
-    constexpr int RGRP = (BK / 8) * TC_KSTEP;
     constexpr int NCOL = NT < 32 ? 32 : NT;
-    constexpr int CH = BK / 8;  // 16-byte chunks per tile row
+    constexpr int CH = BK / 8;    // 16-byte chunks per tile row
+    constexpr int RPW = 32 / CH;  // tile rows per warp-wide copy
+    // every stage and both tiles start on a swizzle atom (8 rows)
+    static_assert(NT % RPW == 0 && STAGE % (16 * BK) == 0 && ABYTES % (16 * BK) == 0, "tile shape");
     extern __shared__ __align__(1024) unsigned char ws_smem[];
     __shared__ __align__(8) unsigned long long full[WS_S], empty[WS_S], done;
     __shared__ unsigned tmem_base;
@@ -299,33 +365,33 @@ __global__ void __launch_bounds__(160) k_conv_ws(const ConvArgs a, int *err) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem = tmem_base;
     if (warp < WS_S) {
-        // ---- producer of stage `warp`: lane l copies tile rows l + 32 i
-        // (pixel coordinates from s_rows) and the weight rows l + 32 i
+        // ---- producer of stage `warp`: each warp-wide copy moves RPW whole
+        // tile rows, lane l taking chunk l % CH of row l / CH (pixel
+        // coordinates from s_rows), then the same for the weight rows
         unsigned char *sa = sm + warp * STAGE, *sb = sa + ABYTES;
+        const int lr = lane / CH, lc = lane % CH;
         for (int kb = warp, j = 0; kb < KB; kb += WS_S, ++j) {
             if (j >= 1 && !ws_wait(&empty[warp], (j - 1) & 1, &s_fail)) break;
             const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
             const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = lane + 32 * i;
+#pragma unroll 4
+            for (int r0 = 0; r0 < 128; r0 += RPW) {
+                const int r = r0 + lr;
                 const int an = s_rows[r][0];
                 const int yy = s_rows[r][1] + dy;
                 int xx = s_rows[r][2] + dx;
                 if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
                 const bool ok = an >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                const bf16 *src = ok ? a.x + ((long long)(an * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 : a.x;
-#pragma unroll
-                for (int cc = 0; cc < CH; ++cc)
-                    cp_async16(sa + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, ok ? src + cc * 8 : a.x, ok);
+                const bf16 *src = ok ? a.x + ((long long)(an * a.H + yy) * a.W + xx) * a.xc + a.xo + c0 + lc * 8 : a.x;
+                cp_async16(sa + sw_off<BK>(r, lc), src, ok);
             }
 #pragma unroll 4
-            for (int q = lane; q < NT * CH; q += 32) {
-                const int r = q / CH, cc = q % CH;
+            for (int r0 = 0; r0 < NT; r0 += RPW) {
+                const int r = r0 + lr;
                 const int co = co0 + r;
                 const bool ok = co < a.wrows;
-                const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + cc * 8 : a.w;
-                cp_async16(sb + (r >> 3) * RGRP + cc * TC_KSTEP + (r & 7) * 16, src, ok);
+                const bf16 *src = ok ? a.w + (long long)co * 9 * a.cin + tap * a.cin + c0 + lc * 8 : a.w;
+                cp_async16(sb + sw_off<BK>(r, lc), src, ok);
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -346,8 +412,8 @@ __global__ void __launch_bounds__(160) k_conv_ws(const ConvArgs a, int *err) {
             const unsigned sa = smem_addr(sm + s * STAGE), sb = sa + ABYTES;
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
-                const uint64_t da = tc_desc(sa + ks * 2 * TC_KSTEP, TC_KSTEP, RGRP);
-                const uint64_t db = tc_desc(sb + ks * 2 * TC_KSTEP, TC_KSTEP, RGRP);
+                const uint64_t da = tc_desc_sw<BK>(sa + ks * 32);
+                const uint64_t db = tc_desc_sw<BK>(sb + ks * 32);
                 const unsigned acc = (kb > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -367,48 +433,152 @@ __global__ void __launch_bounds__(160) k_conv_ws(const ConvArgs a, int *err) {
     if (warp < WS_S) {
         const bool ok = ws_wait(&done, 0, &s_fail) && !s_fail;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ok) {
-            // warp w holds TMEM lanes 32w .. 32w + 31: one pixel per thread
-            const long long m = m0 + warp * 32 + lane;
-#pragma unroll
-            for (int c = 0; c < NT; c += 16) {
-                unsigned r[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int cb = co0 + c;
-                if (m >= M || cb >= a.cout) continue;
-                float v[16];
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    v[jj] = __uint_as_float(r[jj]);
-                    if (a.bias && cb + jj < a.cout) v[jj] += a.bias[cb + jj];
-                    if (a.relu) v[jj] = fmaxf(v[jj], 0.f);
-                }
-                if (a.gate) {
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj)
-                        if (cb + jj < a.cout && !(__bfloat162float(a.gate[m * a.gc + a.go + cb + jj]) > 0.f)) v[jj] = 0.f;
-                }
-                bf16 *dst = a.y + m * a.yc + a.yo + cb;
-                if (cb + 16 <= a.cout) {
-                    __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) o[jj] = __floats2bfloat162_rn(v[2 * jj], v[2 * jj + 1]);
-                    reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
-                    reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
-                } else {
-                    for (int jj = 0; jj < 16 && cb + jj < a.cout; ++jj) dst[jj] = __float2bfloat16_rn(v[jj]);
-                }
-            }
-        }
+        if (ok) conv_epilogue<NT>(a, tmem, warp, lane, m0 + warp * 32 + lane < M ? m0 + warp * 32 + lane : -1, co0);
     }
     if (tid == 0 && s_fail) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
+// k_conv_tma: the same convolution with the operand tiles fetched by the
+// Tensor Memory Accelerator.  A tile is one x column: its 128 pixels are HB
+// consecutive rows y of NB images at one x (HB = min(H, 128), NB = 128 / HB).
+// A tap's shift dx moves the whole box to column x + dx (periodic padding:
+// modulo W; zero padding: a column outside the image reads as zeros), and dy
+// shifts its rows, those outside the image reading as zeros (the walls'
+// zero padding).  The activation box is channels c0 .. c0 + BK of
+// (x, rows, images) in a 4-D tensor map over [N][H][W][xc]; the weight box
+// is BK taps-and-channels of NT output channels in a 2-D map over
+// [wrows][9 cin].  Both land in the swizzled K-major layout of k_conv_ws.
+// One thread issues a stage's two copies after announcing their bytes on
+// full[s] (arrive.expect_tx), so every stage can be in flight at once; the
+// MMA warp and the epilogue are k_conv_ws's.  Every wait is bounded; after a
+// failure the producer waits (bounded) for the copies it still has in flight
+// before the TMEM is freed and the CTA exits.  Four stages by default, so
+// several CTAs share an SM; DEEP (for grids of under two CTAs per SM, where
+// nothing else hides a stage's latency) fills about 192 KB with up to 8.
+template <int BK, int NT> constexpr int tma_stage_bytes() { return (128 * BK * 2 + NT * BK * 2 + 1023) & ~1023; }
+template <int BK, int NT, bool DEEP> constexpr int tma_stages() {
+    return !DEEP ? 4
+         : (196608 / tma_stage_bytes<BK, NT>() < 4 ? 4
+         : (196608 / tma_stage_bytes<BK, NT>() > 8 ? 8 : 196608 / tma_stage_bytes<BK, NT>()));
+}
+
+template <int BK, int NT, bool DEEP>
+__global__ void __launch_bounds__(160) k_conv_tma(const ConvArgs a, const __grid_constant__ CUtensorMap tmA,
+                                                  const __grid_constant__ CUtensorMap tmB, int HB, int NB, int *err) {
+    constexpr int ABYTES = 128 * BK * 2, BBYTES = NT * BK * 2;
+    constexpr int STAGE = tma_stage_bytes<BK, NT>();
+    constexpr int TMA_S = tma_stages<BK, NT, DEEP>();
+    constexpr int NCOL = NT < 32 ? 32 : NT;
+    extern __shared__ __align__(1024) unsigned char tm_smem[];
+    __shared__ __align__(8) unsigned long long full[TMA_S], empty[TMA_S], done;
+    __shared__ unsigned tmem_base;
+    __shared__ volatile int s_fail;
+    __shared__ int s_consumed;  // K blocks the MMA warp received
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *sm = (unsigned char *)(((uintptr_t)tm_smem + 1023) & ~(uintptr_t)1023);
+    const int ytiles = a.H / HB;
+    const int xcol = blockIdx.x % a.W;
+    const int rest = blockIdx.x / a.W;
+    const int yt = rest % ytiles, ng = rest / ytiles;
+    const int co0 = blockIdx.y * NT;
+    const int cblocks = a.cin / BK;
+    const int KB = 9 * cblocks;
+    if (tid == 0) {
+        s_fail = 0;
+        s_consumed = 0;
+        for (int s = 0; s < TMA_S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    int issued = 0;
+    if (tid == 0) {
+        // ---- producer
+        const uint64_t pa = reinterpret_cast<uint64_t>(&tmA), pb = reinterpret_cast<uint64_t>(&tmB);
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % TMA_S;
+            if (kb >= TMA_S && !ws_wait(&empty[s], (kb / TMA_S - 1) & 1, &s_fail)) break;
+            const int tap = kb / cblocks, c0 = (kb - tap * cblocks) * BK;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            int xx = xcol + dx;
+            if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+            const unsigned sa = smem_addr(sm + s * STAGE), sb = sa + ABYTES, mb = smem_addr(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(ABYTES + BBYTES)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5}], [%6];" ::"r"(sa),
+                "l"(pa), "r"(c0), "r"(xx), "r"(yt * HB + dy), "r"(ng * NB), "r"(mb)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(sb),
+                "l"(pb), "r"(tap * a.cin + c0), "r"(co0), "r"(mb)
+                : "memory");
+            issued = kb + 1;
+        }
+    } else if (warp == 4 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t IDESC = tc_idesc(128, NT);
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int s = kb % TMA_S;
+            if (!ws_wait(&full[s], (kb / TMA_S) & 1, &s_fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned sa = smem_addr(sm + s * STAGE), sb = sa + ABYTES;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint64_t da = tc_desc_sw<BK>(sa + ks * 32);
+                const uint64_t db = tc_desc_sw<BK>(sb + ks * 32);
+                const unsigned acc = (kb > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                    "}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&empty[s])));
+        }
+        s_consumed = kb;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&done)));
+    }
+    if (warp < 4) {
+        // warp-uniform: the epilogue's TMEM loads are warp-aligned
+        const bool ok = __all_sync(0xffffffffu, ws_wait(&done, 0, &s_fail) && !s_fail);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            const int r = warp * 32 + lane;
+            const long long n = (long long)ng * NB + r / HB;
+            const int y = yt * HB + r % HB;
+            conv_epilogue<NT>(a, tmem, warp, lane, (n * a.H + y) * a.W + xcol, co0);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail) {
+        // copies still in flight land, and issued MMAs finish, before the
+        // CTA frees its TMEM and leaves
+        volatile int never = 0;
+        for (int kb = s_consumed; kb < issued; ++kb) ws_wait(&full[kb % TMA_S], (kb / TMA_S) & 1, &never);
+        ws_wait(&done, 0, &never);
+        atomicExch(err, 1);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
@@ -704,6 +874,7 @@ struct lbm_unet {
     int H = 0, W = 0, B = 0;
     int cin = 3;        // input channels of the first layer
     int wrapx = 0;      // periodic padding along x in every convolution
+    int sms = 152;      // multiprocessors of the device
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Layer L[kL];
@@ -782,11 +953,97 @@ template <int BK> lbm_status launch_tc_n(lbm_unet *u, const ConvArgs &a, long lo
     return launch_tc<BK, 128>(u, a, M);
 }
 
-// convolutions with N = cout a multiple of 16 (every layer but the head)
+// cuTensorMapEncodeTiled from the driver, looked up once (null: unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+template <int BK, int NT, bool DEEP>
+cudaError_t launch_tma_kernel(lbm_unet *u, const ConvArgs &a, const CUtensorMap &ta, const CUtensorMap &tb, int HB,
+                              int NB, dim3 grid) {
+    constexpr size_t STAGE = tma_stage_bytes<BK, NT>();
+    const int ncol = NT < 32 ? 32 : NT;
+    const size_t need = tma_stages<BK, NT, DEEP>() * STAGE + 1024, floor_ = 233472 / (512 / ncol + 1) - 1024 + 1;
+    const size_t smem = need > floor_ ? need : floor_;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv_tma<BK, NT, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_conv_tma<BK, NT, DEEP><<<grid, 160, smem, u->stream>>>(a, ta, tb, HB, NB, u->tc_err);
+    return cudaSuccess;
+}
+
+// The TMA convolution when the shape suits its column tiles: H <= 128
+// dividing 128 with N a multiple of 128 / H, or H a multiple of 128; every
+// global address and stride a multiple of 16 bytes.  Returns false (nothing
+// launched) otherwise, and when a tensor map cannot be made.
+template <int BK, int NT> bool launch_tma(lbm_unet *u, const ConvArgs &a, lbm_status *st) {
+    const int H = a.H, W = a.W, N = a.N;
+    const int HB = H <= 128 ? H : 128;
+    const int NB = H <= 128 ? 128 / H : 1;
+    if (H <= 128 ? (128 % H != 0 || N % NB != 0) : (H % 128 != 0)) return false;
+    if (a.cin % BK != 0 || a.xc % 8 != 0 || a.xo % 8 != 0 || ((uintptr_t)a.x) % 16 != 0 || ((uintptr_t)a.w) % 16 != 0 ||
+        (9 * a.cin) % 8 != 0)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const CUtensorMapSwizzle swz =
+        BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (BK == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    alignas(64) CUtensorMap ta, tb;
+    const cuuint64_t gdA[4] = {(cuuint64_t)a.cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t rowb = (cuuint64_t)a.xc * 2;
+    const cuuint64_t gsA[3] = {rowb, rowb * W, rowb * W * H};
+    const cuuint32_t boxA[4] = {(cuuint32_t)BK, 1u, (cuuint32_t)HB, (cuuint32_t)NB};
+    const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+    if (enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a.x + a.xo), gdA, gsA, boxA, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t gdB[2] = {(cuuint64_t)9 * a.cin, (cuuint64_t)a.wrows};
+    const cuuint64_t gsB[1] = {(cuuint64_t)9 * a.cin * 2};
+    const cuuint32_t boxB[2] = {(cuuint32_t)BK, (cuuint32_t)NT};
+    if (enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.w, gdB, gsB, boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    dim3 grid((unsigned)(W * (H / HB) * (N / NB)), (unsigned)nblk(a.cout, NT));
+    const bool deep = (long long)grid.x * grid.y < 2LL * u->sms;
+    cudaError_t e = deep ? launch_tma_kernel<BK, NT, true>(u, a, ta, tb, HB, NB, grid)
+                         : launch_tma_kernel<BK, NT, false>(u, a, ta, tb, HB, NB, grid);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    *st = e == cudaSuccess ? LBM_OK : ufail(u, LBM_ERR_CUDA, std::string("k_conv_tma: ") + cudaGetErrorString(e));
+    return true;
+}
+
+template <int BK> lbm_status launch_conv_n(lbm_unet *u, const ConvArgs &a, long long M) {
+    lbm_status st = LBM_OK;
+    if (a.cout <= 16) return launch_tma<BK, 16>(u, a, &st) ? st : launch_tc<BK, 16>(u, a, M);
+    if (a.cout <= 32) return launch_tma<BK, 32>(u, a, &st) ? st : launch_tc<BK, 32>(u, a, M);
+    if (a.cout <= 64) return launch_tma<BK, 64>(u, a, &st) ? st : launch_tc<BK, 64>(u, a, M);
+    return launch_tma<BK, 128>(u, a, &st) ? st : launch_tc<BK, 128>(u, a, M);
+}
+
+// convolutions with N = cout a multiple of 16 (every layer but the head):
+// TMA-fed where the shape allows, else cp.async-fed
 lbm_status conv_tc(lbm_unet *u, const ConvArgs &a, long long M) {
-    if (a.cin % 64 == 0) return launch_tc_n<64>(u, a, M);
-    if (a.cin % 32 == 0) return launch_tc_n<32>(u, a, M);
-    return launch_tc_n<16>(u, a, M);
+    if (a.cin % 64 == 0) return launch_conv_n<64>(u, a, M);
+    if (a.cin % 32 == 0) return launch_conv_n<32>(u, a, M);
+    return launch_conv_n<16>(u, a, M);
 }
 
 lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H, int W, bf16 *y, int yc, int yo,
@@ -1006,6 +1263,13 @@ lbm_status lbm_unet_create(int H, int W, int cin, int periodic_x, int max_batch,
     u->B = max_batch;
     u->cin = cin;
     u->wrapx = periodic_x;
+    {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            u->sms = n;
+        cudaGetLastError();
+    }
     if (stream) {
         u->stream = (cudaStream_t)stream;
     } else {

@@ -33,8 +33,13 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
 
+# (24, 40, 2) and batch-1 shapes take the cp.async-fed convolution at every
+# level; (128, 16, 8) takes the TMA-fed one at every level (column tiles of
+# 128 / H images), and (64, 32, 4) mixes the two (TMA where 128 / H divides
+# the batch)
 @pytest.mark.parametrize("H,W,n,cin,periodic_x", [(24, 40, 2, 3, False), (64, 128, 1, 3, False),
-                                                  (24, 40, 2, 5, True), (32, 64, 1, 16, True)])
+                                                  (24, 40, 2, 5, True), (32, 64, 1, 16, True),
+                                                  (128, 16, 8, 8, True), (64, 32, 4, 3, False)])
 def test_forward_matches_oracle(H, W, n, cin, periodic_x):
     import torch
     import paper_2212_07494_gb300 as P
@@ -57,11 +62,11 @@ def test_forward_matches_oracle(H, W, n, cin, periodic_x):
     net.close()
 
 
-@pytest.mark.parametrize("cin,periodic_x", [(3, False), (5, True)])
-def test_gradient_matches_oracle(cin, periodic_x):
+@pytest.mark.parametrize("H,W,n,cin,periodic_x", [(24, 40, 2, 3, False), (24, 40, 2, 5, True),
+                                                  (128, 16, 8, 8, True)])
+def test_gradient_matches_oracle(H, W, n, cin, periodic_x):
     import torch
     import paper_2212_07494_gb300 as P
-    H, W, n = 24, 40, 2
     params, x, t, m = _problem(H, W, n, 2, cin)
     net = P.UNet(H, W, n, cin=cin, periodic_x=periodic_x)
     net.set_params(params)
