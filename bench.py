@@ -652,11 +652,18 @@ def run_unet(args, ws, rank, local):
         for _ in range(max(args.warmup, 3)):
             net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, scale, 1e-4, ld.data_ptr())
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.4)
+        sampler.mark(0)
         e0.record(stream)
         for _ in range(args.steps):
             net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, scale, 1e-4, ld.data_ptr())
         e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(1)
+    sampler.stop()
     net.params()   # a synchronising call: reports a tensor-core wait that expired
     ms = e0.elapsed_time(e1) / args.steps
     flops = S.train_flops_per_sample(H, Wd) * B
@@ -673,7 +680,8 @@ def run_unet(args, ws, rank, local):
             "config": {"workload": "unet_train_step_128x256_batch8", "H": H, "W": Wd, "batch": B, "cin": S.NF,
                        "flops_per_step": flops},
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                         "traffic": None, "peak_source": "measured bf16_tflops_sustained"}}
+                         "traffic": None, "peak_source": "measured bf16_tflops_sustained"},
+            "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
