@@ -171,6 +171,17 @@ lbm_status lbm_set_force(lbm_handle *h, const double *g);
  * Synchronises the handle's stream. */
 lbm_status lbm_set_force_schedule(lbm_handle *h, const double *table, int64_t period);
 
+/* Time-dependent scaling of the force of any kind (uniform, per row or per
+ * node), for forcing of the form g(x, t) = s(t) g(x), such as the decaying
+ * force of the forced Taylor-Green case (Sec. III.A): the collision of step
+ * s (and the velocity of Eq. half_F at step s) uses scale[s mod period] times
+ * the force set at creation or by lbm_set_force, s counted from this call.
+ * scale: period doubles (host, copied).  The same device step counter as
+ * lbm_set_force_schedule, so it runs inside the step graphs; either schedule
+ * replaces the other.  period = 0 removes it; lbm_set_force also removes
+ * it.  LBM_ERR_STATE without a force.  Synchronises the handle's stream. */
+lbm_status lbm_set_force_scale_schedule(lbm_handle *h, const double *scale, int64_t period);
+
 /* Pre-collision populations fbar_i(x, t) in FP64, host layout f[i][z][y][x]
  * (solid nodes: w_i).  Synchronises. */
 lbm_status lbm_get_populations(lbm_handle *h, double *f);

@@ -16,7 +16,7 @@ from ._binding import (  # noqa: F401
     LBM_BF16_SHIFT, LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD, LbmError, Lattice,
     lbm_create, lbm_destroy, lbm_step, lbm_moments, lbm_moments_device, lbm_residual,
     lbm_check_device,
-    lbm_set_force, lbm_set_force_schedule, lbm_get_populations, lbm_set_populations, lbm_state_bytes, lbm_get_state,
+    lbm_set_force, lbm_set_force_schedule, lbm_set_force_scale_schedule, lbm_get_populations, lbm_set_populations, lbm_state_bytes, lbm_get_state,
     lbm_set_state, lbm_info, lbm_last_error, lbm_set_launch, lbm_autotune, lbm_check_noalloc, library, library_path,
     make_desc, Batch, lbm_batch_create, lbm_batch_run_to_steady, lbm_batch_step, lbm_batch_reset,
     lbm_batch_moments, lbm_batch_get_populations, lbm_batch_set_tiles, lbm_batch_autotune,

@@ -69,6 +69,7 @@ def library():
     L.lbm_check_device.argtypes = [H, C.c_void_p]
     L.lbm_set_force.argtypes = [H, dp]
     L.lbm_set_force_schedule.argtypes = [H, dp, C.c_int64]
+    L.lbm_set_force_scale_schedule.argtypes = [H, dp, C.c_int64]
     L.lbm_get_populations.argtypes = [H, dp]
     L.lbm_set_populations.argtypes = [H, dp]
     L.lbm_state_bytes.argtypes = [H]
@@ -103,7 +104,7 @@ def library():
     L.lbm_last_error.restype = C.c_char_p
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
               "lbm_check_device",
-              "lbm_set_force", "lbm_set_force_schedule", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
+              "lbm_set_force", "lbm_set_force_schedule", "lbm_set_force_scale_schedule", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
               "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc",
               "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
               "lbm_batch_moments", "lbm_batch_get_populations", "lbm_batch_set_tiles", "lbm_batch_autotune",
@@ -228,6 +229,10 @@ def lbm_set_force_schedule(h, table, period):
     _check(library().lbm_set_force_schedule(h, _dptr(table) if table is not None else None, int(period)), h)
 
 
+def lbm_set_force_scale_schedule(h, scale, period):
+    _check(library().lbm_set_force_scale_schedule(h, _dptr(scale) if scale is not None else None, int(period)), h)
+
+
 def lbm_get_populations(h, out):
     _check(library().lbm_get_populations(h, _dptr(out)), h)
 
@@ -338,6 +343,15 @@ class Lattice:
 
     def set_force(self, g):
         lbm_set_force(self.h, _f64(g))
+
+    def set_force_scale_schedule(self, scale):
+        """scale: (period,) factors applied to the force of the next `period`
+        steps, repeating; None removes the schedule."""
+        if scale is None:
+            lbm_set_force_scale_schedule(self.h, None, 0)
+            return
+        s = np.ascontiguousarray(np.asarray(scale, np.float64).ravel())
+        lbm_set_force_scale_schedule(self.h, s, s.size)
 
     def set_force_schedule(self, table):
         """table: (period, D) accelerations of the next `period` steps, repeating;

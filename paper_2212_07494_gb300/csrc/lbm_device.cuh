@@ -172,9 +172,12 @@ struct KParams {
     double omb;                    // 1 / tau of the trace (bulk) part of order 2; om[2] unless split
     float omb32;
     // force schedule (uniform g per step) or null: step t of the schedule uses
-    // gs[3 * ((*gs_t + gs_off) mod gs_period)]
+    // gs[3 * ((*gs_t + gs_off) mod gs_period)]; or a scale schedule (gsc), the
+    // force of any kind times gsc[(*gs_t + gs_off) mod gs_period]
     const double *gs;
     const float *gs32;
+    const double *gsc;
+    const float *gsc32;
     const long long *gs_t;         // steps since the schedule was set, mod gs_period (device)
     long long gs_period;
     int gs_off;                    // this launch's offset from *gs_t within its chunk
@@ -771,6 +774,9 @@ template <typename R> __device__ __forceinline__ const R *force_ptr(const KParam
 template <typename R> __device__ __forceinline__ const R *sched_ptr(const KParams &p);
 template <> __device__ __forceinline__ const double *sched_ptr<double>(const KParams &p) { return p.gs; }
 template <> __device__ __forceinline__ const float *sched_ptr<float>(const KParams &p) { return p.gs32; }
+template <typename R> __device__ __forceinline__ const R *scale_ptr(const KParams &p);
+template <> __device__ __forceinline__ const double *scale_ptr<double>(const KParams &p) { return p.gsc; }
+template <> __device__ __forceinline__ const float *scale_ptr<float>(const KParams &p) { return p.gsc32; }
 template <> __device__ __forceinline__ const double *force_ptr<double>(const KParams &p) { return p.g; }
 template <> __device__ __forceinline__ const float *force_ptr<float>(const KParams &p) { return p.g32; }
 
@@ -800,6 +806,12 @@ __device__ __forceinline__ void load_force(const KParams &p, int y, long long no
         gx = __ldg(g + node);
         gy = __ldg(g + p.plane + node);
         if (D == 3) gz = __ldg(g + 2 * p.plane + node);
+    }
+    if (p.gsc != nullptr) {               // scaled force of this step
+        const R f = scale_ptr<R>(p)[(*p.gs_t + p.gs_off) % p.gs_period];
+        gx *= f;
+        gy *= f;
+        gz *= f;
     }
 }
 

@@ -93,8 +93,9 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // graph_steps steps starting from buf[0] / buf[1]
-    double *gs_dev = nullptr;    // force schedule [period][3], FP64 and FP32 copies
+    double *gs_dev = nullptr;    // force schedule [period][3] or scale schedule [period], FP64 and FP32 copies
     float *gs32_dev = nullptr;
+    bool gs_scale = false;       // gs_dev holds a scale schedule
     long long *gs_t_dev = nullptr;
     int64_t gs_period = 0;
     int graph_steps = 0;
@@ -223,8 +224,11 @@ void free_schedule(lbm_handle *h) {
     h->gs32_dev = nullptr;
     h->gs_t_dev = nullptr;
     h->gs_period = 0;
+    h->gs_scale = false;
     h->kp.gs = nullptr;
     h->kp.gs32 = nullptr;
+    h->kp.gsc = nullptr;
+    h->kp.gsc32 = nullptr;
     h->kp.gs_t = nullptr;
     h->kp.gs_period = 0;
 }
@@ -266,6 +270,48 @@ lbm_status run_moments(lbm_handle *h, double *rho, double *u, void *uprev, doubl
     if (nb > h->max_blocks) return fail(h, LBM_ERR_STATE, "partial-sum scratch too small");
     e = launch_finalize(h->partials, nb, out ? out : h->red_dev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "finalize launch");
+    return LBM_OK;
+}
+
+// upload a schedule of `width` doubles per step (3: a uniform force, 1: a
+// scale) and arm it from the next step on
+lbm_status set_schedule(lbm_handle *h, const std::vector<double> &tmp, int64_t period, bool scale) {
+    std::vector<float> tmp32(tmp.begin(), tmp.end());
+    // in-flight steps may still read the old schedule
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    free_schedule(h);
+    if (period == 0) return LBM_OK;
+    lbm_status st = alloc_into(h, &h->gs_dev, tmp.size() * sizeof(double), "force schedule");
+    if (st == LBM_OK) st = alloc_into(h, &h->gs32_dev, tmp32.size() * sizeof(float), "force schedule");
+    if (st == LBM_OK) st = alloc_into(h, &h->gs_t_dev, sizeof(long long), "force schedule counter");
+    if (st != LBM_OK) {
+        free_schedule(h);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->gs32_dev, tmp32.data(), tmp32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gs_t_dev, 0, sizeof(long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free_schedule(h);
+        return cuda_fail(h, e, "force schedule upload");
+    }
+    h->gs_period = period;
+    h->gs_scale = scale;
+    if (scale) {
+        h->kp.gsc = h->gs_dev;
+        h->kp.gsc32 = h->gs32_dev;
+    } else {
+        h->kp.gs = h->gs_dev;
+        h->kp.gs32 = h->gs32_dev;
+    }
+    h->kp.gs_t = h->gs_t_dev;
+    h->kp.gs_period = period;
+    h->kp.gs_off = 0;
     return LBM_OK;
 }
 
@@ -615,6 +661,7 @@ lbm_status lbm_set_force(lbm_handle *h, const double *g) {
     return upload_force(h, g);
 }
 
+
 lbm_status lbm_set_force_schedule(lbm_handle *h, const double *table, int64_t period) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (h->force_kind != LBM_G_UNIFORM) return fail(h, LBM_ERR_STATE, "a force schedule needs LBM_G_UNIFORM");
@@ -627,37 +674,18 @@ lbm_status lbm_set_force_schedule(lbm_handle *h, const double *table, int64_t pe
             if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "schedule contains a non-finite value");
             tmp[(size_t)t * 3 + a] = v;
         }
-    std::vector<float> tmp32(tmp.begin(), tmp.end());
-    // in-flight steps may still read the old schedule
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    drop_graphs(h);
-    free_schedule(h);
-    if (period == 0) return LBM_OK;
-    lbm_status st = alloc_into(h, &h->gs_dev, tmp.size() * sizeof(double), "force schedule");
-    if (st == LBM_OK) st = alloc_into(h, &h->gs32_dev, tmp32.size() * sizeof(float), "force schedule");
-    if (st == LBM_OK) st = alloc_into(h, &h->gs_t_dev, sizeof(long long), "force schedule counter");
-    if (st != LBM_OK) {
-        free_schedule(h);
-        return st;
-    }
-    cudaError_t e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
-                                    h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->gs32_dev, tmp32.data(), tmp32.size() * sizeof(float), cudaMemcpyHostToDevice,
-                            h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->gs_t_dev, 0, sizeof(long long), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        free_schedule(h);
-        return cuda_fail(h, e, "force schedule upload");
-    }
-    h->gs_period = period;
-    h->kp.gs = h->gs_dev;
-    h->kp.gs32 = h->gs32_dev;
-    h->kp.gs_t = h->gs_t_dev;
-    h->kp.gs_period = period;
-    h->kp.gs_off = 0;
-    return LBM_OK;
+    return set_schedule(h, tmp, period, false);
+}
+
+lbm_status lbm_set_force_scale_schedule(lbm_handle *h, const double *scale, int64_t period) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (h->force_kind == LBM_G_NONE) return fail(h, LBM_ERR_STATE, "created without a force");
+    if (period < 0 || (period > 0 && !scale)) return fail(h, LBM_ERR_ARG, "bad schedule");
+    if (period > (int64_t)1 << 30) return fail(h, LBM_ERR_ARG, "schedule period too long");
+    std::vector<double> tmp(scale, scale + period);
+    for (double v : tmp)
+        if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "schedule contains a non-finite value");
+    return set_schedule(h, tmp, period, true);
 }
 
 lbm_status lbm_get_populations(lbm_handle *h, double *f) {

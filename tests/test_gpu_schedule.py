@@ -121,3 +121,38 @@ def test_womersley_on_the_gpu_with_a_schedule():
     orc.set_force([-A * math.cos(om * t), 0.0])
     assert rel_l2(gl.moments()[1][0, 0, :, 0], orc.moments()[1][0, 0, :, 0]) < 1e-12
     gl.close()
+
+
+def test_forced_taylor_green_second_order_on_the_gpu():
+    """Sec. III.A on the GPU: L = 16, 32, 64, FP64 storage.  The force field
+    decays as exp(-2 (k1^2 + k2^2) nu t) (reading C-9); the scale schedule
+    applies that factor inside the step graphs.  The E2 error at t = T falls
+    at second order, and at L = 16 the run equals the oracle's, whose force
+    is set before every step."""
+    import lbm_workloads as W
+    import paper_2212_07494_gb300 as P
+    cfg = GOLD["taylor_green_2d"]
+    errs = []
+    for L in cfg["L"]:
+        tau, T, uinit, force = W.taylor_green_2d(L, cfg["u0"], cfg["Re"])
+        k, nu = 2 * np.pi / L, cfg["u0"] * L / cfg["Re"]
+        scale = np.exp(-2.0 * (2.0 * k * k) * nu * np.arange(T + 1))
+        gl = P.Lattice("D2Q9", "SMRT", (L, L, 1), (1, 1, tau, 1, 1), "F64", (1, 1, 1), g=force(0),
+                       force_kind="field", u0=uinit)
+        gl.set_force_scale_schedule(scale)
+        gl.step(T)
+        u = gl.moments()[1]
+        gl.close()
+        ua = uinit * math.exp(-2 * k * k * nu * T)
+        errs.append(math.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+        if L == cfg["L"][0]:
+            orc = O.Sim(O.D2Q9, O.SMRT, (L, L, 1), (1, 1, 1), (1, 1, tau, 1, 1), g=force(0),
+                        force_kind="field", u0=uinit)
+            for t in range(T):
+                orc.set_force(force(t), "field")
+                orc.step(1)
+            orc.set_force(force(T), "field")
+            assert rel_l2(u, orc.moments()[1]) < 1e-12
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    lo, hi = cfg["slope_range"]
+    assert all(lo <= s <= hi for s in slopes), (errs, slopes)
