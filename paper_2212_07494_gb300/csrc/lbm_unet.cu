@@ -946,13 +946,6 @@ template <int BK, int NT> lbm_status launch_tc(lbm_unet *u, const ConvArgs &a, l
     return LBM_OK;
 }
 
-template <int BK> lbm_status launch_tc_n(lbm_unet *u, const ConvArgs &a, long long M) {
-    if (a.cout <= 16) return launch_tc<BK, 16>(u, a, M);
-    if (a.cout <= 32) return launch_tc<BK, 32>(u, a, M);
-    if (a.cout <= 64) return launch_tc<BK, 64>(u, a, M);
-    return launch_tc<BK, 128>(u, a, M);
-}
-
 // cuTensorMapEncodeTiled from the driver, looked up once (null: unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
