@@ -845,7 +845,7 @@ def run_womersley(args, ws, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "note": "10,000 nodes per step: launch latency bounds it, not HBM",
                          "peak_source": f"{peak_kind} hbm_gbs (copy)"},
-            "gpu_launches": steps + steps // 64,
+            "gpu_launches": 2 * steps + steps // 64,   # k_step and the force update per step, a counter advance per 64
             "clocks": sampler.summary(),
             "per_step_set_force": {"seconds": host_s, "steps": t_end, "mlups": N * t_end / host_s / 1e6,
                                    "us_per_step": host_s / t_end * 1e6},

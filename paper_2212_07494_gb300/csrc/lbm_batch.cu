@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
                     }
                     // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it, so
                     // that a channel evolves with the same arithmetic here and alone
-                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2, om2);
+                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
                     else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
                     else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
                     T *dst = fout + (y * C.nxp + x);

@@ -171,16 +171,6 @@ struct KParams {
     float om32[5];
     double omb;                    // 1 / tau of the trace (bulk) part of order 2; om[2] unless split
     float omb32;
-    // force schedule (uniform g per step) or null: step t of the schedule uses
-    // gs[3 * ((*gs_t + gs_off) mod gs_period)]; or a scale schedule (gsc), the
-    // force of any kind times gsc[(*gs_t + gs_off) mod gs_period]
-    const double *gs;
-    const float *gs32;
-    const double *gsc;
-    const float *gsc32;
-    const long long *gs_t;         // steps since the schedule was set, mod gs_period (device)
-    long long gs_period;
-    int gs_off;                    // this launch's offset from *gs_t within its chunk
     // per population i, relative to a node's element index:
     long long doff[27];            // i*plane - (cx + cy*nxp + cz*nxp*ny): pull source
     long long poff[27];            // i*plane: the node's own entry
@@ -447,7 +437,7 @@ __host__ __device__ __forceinline__ void shift_pass(R *a, R v) {
 // collide_smrt, whose orders-3/4 factors (1 - om) are then exactly zero,
 // with the passes restricted to what is non-zero or read.
 template <int L, typename R>
-__host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R gz, R om2, R omb) {
+__host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R gz, R om2) {
     constexpr int D = Lat<L>::D;
     constexpr int N = Grid<D>::N;
     constexpr int EX = 1, EY = 3, EZ = 9;
@@ -472,7 +462,12 @@ __host__ __device__ __forceinline__ void collide_smrt_trim(R *G, R gx, R gy, R g
     shift_pass<D, 0, ALL, LOW>(G, -ux);
     shift_pass<D, 1, ALL, LOW>(G, -uy);
     if constexpr (D == 3) shift_pass<D, 2, ALL, LOW>(G, -uz);
-    relax_order2<D>(G, om2, omb);
+    // one relaxation time for the whole second order: a split bulk time runs
+    // the general collision
+    static_for<N>([&](auto I) {
+        constexpr int g = decltype(I)::value;
+        if constexpr (((LOW >> g) & 1u) && morder<D>(g) == 2) G[g] *= (R(1) - om2);
+    });
     G[0] = rho;
     G[EX] = R(0.5) * rho * gx;
     G[EY] = R(0.5) * rho * gy;
@@ -771,12 +766,6 @@ __device__ __forceinline__ void gather(const KParams &p, const typename Store<ST
 }
 
 template <typename R> __device__ __forceinline__ const R *force_ptr(const KParams &p);
-template <typename R> __device__ __forceinline__ const R *sched_ptr(const KParams &p);
-template <> __device__ __forceinline__ const double *sched_ptr<double>(const KParams &p) { return p.gs; }
-template <> __device__ __forceinline__ const float *sched_ptr<float>(const KParams &p) { return p.gs32; }
-template <typename R> __device__ __forceinline__ const R *scale_ptr(const KParams &p);
-template <> __device__ __forceinline__ const double *scale_ptr<double>(const KParams &p) { return p.gsc; }
-template <> __device__ __forceinline__ const float *scale_ptr<float>(const KParams &p) { return p.gsc32; }
 template <> __device__ __forceinline__ const double *force_ptr<double>(const KParams &p) { return p.g; }
 template <> __device__ __forceinline__ const float *force_ptr<float>(const KParams &p) { return p.g32; }
 
@@ -786,14 +775,6 @@ __device__ __forceinline__ void load_force(const KParams &p, int y, long long no
     constexpr int D = Lat<L>::D;
     const R *g = force_ptr<R>(p);
     gx = gy = gz = R(0);
-    if (p.gs != nullptr) {                // scheduled uniform force of this step
-        const long long t = (*p.gs_t + p.gs_off) % p.gs_period;
-        const R *s = sched_ptr<R>(p) + 3 * t;
-        gx = s[0];
-        gy = s[1];
-        if (D == 3) gz = s[2];
-        return;
-    }
     if (p.force_kind == G_UNIFORM) {
         gx = __ldg(g + 0);
         gy = __ldg(g + 1);
@@ -806,12 +787,6 @@ __device__ __forceinline__ void load_force(const KParams &p, int y, long long no
         gx = __ldg(g + node);
         gy = __ldg(g + p.plane + node);
         if (D == 3) gz = __ldg(g + 2 * p.plane + node);
-    }
-    if (p.gsc != nullptr) {               // scaled force of this step
-        const R f = scale_ptr<R>(p)[(*p.gs_t + p.gs_off) % p.gs_period];
-        gx *= f;
-        gy *= f;
-        gz *= f;
     }
 }
 

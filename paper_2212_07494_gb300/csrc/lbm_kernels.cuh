@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
         const long long own = node_index(p, x, y, z);
         if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
         if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
-        else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2, omb);
+        else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2);
         else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
         else if (COLL == MRT_RAW) collide_mrt_raw<L>(G[k], gx, gy, gz, om2, om3, om4);
         else collide_bgk<L>(G[k], gx, gy, gz, om2);
@@ -342,9 +342,10 @@ template <int L> struct Dispatch {
     }
     static cudaError_t step(int coll, int st, bool mask, StepCfg cfg, const KParams &p, const void *fin,
                             void *fout, cudaStream_t s) {
-        // tau_3 = tau_4 = 1 exactly: the trimmed collision, the same arithmetic
-        // on the moments that stay non-zero
-        if (coll == SMRT && p.om[3] == 1.0 && p.om[4] == 1.0) return step_s<SMRT_TRIM>(st, mask, cfg, p, fin, fout, s);
+        // tau_3 = tau_4 = 1 exactly, one second-order tau: the trimmed
+        // collision, the same arithmetic on the moments that stay non-zero
+        if (coll == SMRT && p.om[3] == 1.0 && p.om[4] == 1.0 && p.omb == p.om[2])
+            return step_s<SMRT_TRIM>(st, mask, cfg, p, fin, fout, s);
         if (coll == SMRT_FNEQ) return step_s<SMRT_FNEQ>(st, mask, cfg, p, fin, fout, s);
         if (coll == MRT_RAW) return step_s<MRT_RAW>(st, mask, cfg, p, fin, fout, s);
         return coll == SMRT ? step_s<SMRT>(st, mask, cfg, p, fin, fout, s)

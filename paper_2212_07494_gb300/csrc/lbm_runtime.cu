@@ -57,9 +57,33 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, dou
     }
 }
 
-// advance the force schedule's step counter by n (one thread; the counter is
-// read by the step and moments kernels and kept below the period)
+// Force schedules.  The step kernels read the force buffers as always; after
+// each step k_sched_apply writes the force of the next step into them, from
+// the schedule's entry (*t + off): a uniform g (table of 3 per step), or the
+// saved base force times a factor (table of 1 per step), over `count` values
+// of the device layout.  The tables hold period + 64 entries, entry i being
+// the schedule's entry i mod period, and *t < period, off <= 64, so no modulo
+// is taken on the device.  k_sched_advance moves the counter on (one
+// thread) and keeps it below the period.
 __global__ void k_sched_advance(long long *t, long long n, long long period) { *t = (*t + n) % period; }
+
+__global__ void k_sched_apply(const double *table, const long long *t, int off, int scale, const double *base,
+                              long long count, double *g, float *g32) {
+    const long long idx = *t + off;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!scale) {
+        if (i < 3) {
+            g[i] = table[3 * idx + i];
+            g32[i] = (float)table[3 * idx + i];
+        }
+        return;
+    }
+    if (i < count) {
+        const double v = table[idx] * base[i];
+        g[i] = v;
+        g32[i] = (float)v;
+    }
+}
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(partials, nblocks, out);
@@ -93,8 +117,9 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // graph_steps steps starting from buf[0] / buf[1]
-    double *gs_dev = nullptr;    // force schedule [period][3] or scale schedule [period], FP64 and FP32 copies
-    float *gs32_dev = nullptr;
+    double *gs_dev = nullptr;    // force schedule [period + 64][3] or scale schedule [period + 64]
+    double *gbase_dev = nullptr; // the force a scale schedule multiplies (device layout of g_dev)
+    size_t gdev_count = 0;       // doubles of g_dev
     bool gs_scale = false;       // gs_dev holds a scale schedule
     long long *gs_t_dev = nullptr;
     int64_t gs_period = 0;
@@ -190,18 +215,35 @@ lbm_status upload_force(lbm_handle *h, const double *g) {
     return LBM_OK;
 }
 
+lbm_status sched_apply(lbm_handle *h, int off) {
+    const long long count = h->gs_scale ? (long long)h->gdev_count : 3;
+    k_sched_apply<<<(unsigned)((count + 255) / 256), 256, 0, h->stream>>>(
+        h->gs_dev, h->gs_t_dev, off, h->gs_scale ? 1 : 0, h->gbase_dev, count, h->g_dev, h->g32_dev);
+    LBM_CUDA(h, cudaGetLastError());
+    return LBM_OK;
+}
+
 lbm_status launch_steps(lbm_handle *h, int64_t n) {
     const Launchers &L = launchers_for(h->lattice);
-    KParams kp = h->kp;
+    int since = 0;   // with a force schedule: steps since the counter last advanced (< 64)
     for (int64_t s = 0; s < n; ++s) {
-        kp.gs_off = (int)s;   // with a force schedule: step s of this chunk
-        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, kp, h->buf[h->cur],
+        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, h->kp, h->buf[h->cur],
                                h->buf[1 - h->cur], h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
         h->cur = 1 - h->cur;
+        if (h->gs_dev) {
+            // the force of the next step
+            lbm_status st = sched_apply(h, since + 1);
+            if (st != LBM_OK) return st;
+        }
+        if (h->gs_dev && ++since == 64) {
+            k_sched_advance<<<1, 1, 0, h->stream>>>(h->gs_t_dev, 64LL, (long long)h->gs_period);
+            LBM_CUDA(h, cudaGetLastError());
+            since = 0;
+        }
     }
-    if (h->gs_dev && n > 0) {
-        k_sched_advance<<<1, 1, 0, h->stream>>>(h->gs_t_dev, (long long)n, (long long)h->gs_period);
+    if (h->gs_dev && since > 0) {
+        k_sched_advance<<<1, 1, 0, h->stream>>>(h->gs_t_dev, (long long)since, (long long)h->gs_period);
         LBM_CUDA(h, cudaGetLastError());
     }
     return LBM_OK;
@@ -216,21 +258,27 @@ void drop_graphs(lbm_handle *h) {
         }
 }
 
+// drop a schedule; the force it replaced goes back into the force buffers
+// (the force set last by lbm_set_force or at creation applies again)
 void free_schedule(lbm_handle *h) {
+    if (h->gbase_dev) {
+        const size_t n = h->gdev_count;
+        std::vector<double> base(n);
+        if (cudaMemcpy(base.data(), h->gbase_dev, n * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            std::vector<float> base32(base.begin(), base.end());
+            cudaMemcpy(h->g_dev, base.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+            cudaMemcpy(h->g32_dev, base32.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        }
+        cudaGetLastError();
+    }
     dev_free(h, h->gs_dev);
-    dev_free(h, h->gs32_dev);
+    dev_free(h, h->gbase_dev);
     dev_free(h, h->gs_t_dev);
     h->gs_dev = nullptr;
-    h->gs32_dev = nullptr;
+    h->gbase_dev = nullptr;
     h->gs_t_dev = nullptr;
     h->gs_period = 0;
     h->gs_scale = false;
-    h->kp.gs = nullptr;
-    h->kp.gs32 = nullptr;
-    h->kp.gsc = nullptr;
-    h->kp.gsc32 = nullptr;
-    h->kp.gs_t = nullptr;
-    h->kp.gs_period = 0;
 }
 
 // the graph of graph_steps steps that starts from the buffer holding the
@@ -275,43 +323,42 @@ lbm_status run_moments(lbm_handle *h, double *rho, double *u, void *uprev, doubl
 
 // upload a schedule of `width` doubles per step (3: a uniform force, 1: a
 // scale) and arm it from the next step on
-lbm_status set_schedule(lbm_handle *h, const std::vector<double> &tmp, int64_t period, bool scale) {
-    std::vector<float> tmp32(tmp.begin(), tmp.end());
+lbm_status set_schedule(lbm_handle *h, const std::vector<double> &table, int64_t period, bool scale) {
     // in-flight steps may still read the old schedule
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     free_schedule(h);
     if (period == 0) return LBM_OK;
+    // extended by 64 wrapped entries: the kernels index it at counter + offset
+    const size_t width = scale ? 1 : 3;
+    std::vector<double> tmp(width * (size_t)(period + 64));
+    for (int64_t i = 0; i < period + 64; ++i)
+        for (size_t a = 0; a < width; ++a) tmp[(size_t)i * width + a] = table[(size_t)(i % period) * width + a];
     lbm_status st = alloc_into(h, &h->gs_dev, tmp.size() * sizeof(double), "force schedule");
-    if (st == LBM_OK) st = alloc_into(h, &h->gs32_dev, tmp32.size() * sizeof(float), "force schedule");
     if (st == LBM_OK) st = alloc_into(h, &h->gs_t_dev, sizeof(long long), "force schedule counter");
+    if (st == LBM_OK) st = alloc_into(h, &h->gbase_dev, h->gdev_count * sizeof(double), "force schedule base");
     if (st != LBM_OK) {
         free_schedule(h);
         return st;
     }
     cudaError_t e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
                                     h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->gs32_dev, tmp32.data(), tmp32.size() * sizeof(float), cudaMemcpyHostToDevice,
-                            h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->gs_t_dev, 0, sizeof(long long), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->gbase_dev, h->g_dev, h->gdev_count * sizeof(double), cudaMemcpyDeviceToDevice,
+                            h->stream);
     if (e != cudaSuccess) {
         free_schedule(h);
         return cuda_fail(h, e, "force schedule upload");
     }
     h->gs_period = period;
     h->gs_scale = scale;
-    if (scale) {
-        h->kp.gsc = h->gs_dev;
-        h->kp.gsc32 = h->gs32_dev;
-    } else {
-        h->kp.gs = h->gs_dev;
-        h->kp.gs32 = h->gs32_dev;
+    // the force of the first step
+    if ((st = sched_apply(h, 0)) != LBM_OK) {
+        free_schedule(h);
+        return st;
     }
-    h->kp.gs_t = h->gs_t_dev;
-    h->kp.gs_period = period;
-    h->kp.gs_off = 0;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 
@@ -368,7 +415,7 @@ void lbm_destroy(lbm_handle *h) {
     dev_free(h, h->uprev);
     dev_free(h, h->fields);
     dev_free(h, h->gs_dev);
-    dev_free(h, h->gs32_dev);
+    dev_free(h, h->gbase_dev);
     dev_free(h, h->gs_t_dev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -461,6 +508,7 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     h->max_blocks = kMomGridMax;
     const size_t N = h->N();
     h->g_count = g_count_for(h);
+    h->gdev_count = std::max<size_t>(3, h->force_kind == LBM_G_FIELD ? (size_t)D * plane : h->g_count);
     if ((st = alloc_into(h, &h->buf[0], h->state_bytes, "population buffer A")) ||
         (st = alloc_into(h, &h->buf[1], h->state_bytes, "population buffer B")) ||
         (st = alloc_into(h, &h->partials, (size_t)h->max_blocks * kPartials * sizeof(double), "partials")) ||
