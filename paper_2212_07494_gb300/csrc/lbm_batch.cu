@@ -170,7 +170,7 @@ __host__ __device__ inline int tiles_for(int nx, int ny, long long active, int g
 
 // batch storage is FP32 or FP64 (loads through L2: ld.global.cg)
 template <int COLL, int ST>
-__global__ void __launch_bounds__(256, 3) k_batch(const BatchRun r) {
+__global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
     typedef typename Store<ST>::T T;
     typedef typename Store<ST>::R R;
     __shared__ int s_c, s_tile, s_tiles, s_quit;
