@@ -23,8 +23,9 @@ order, a missing fourth-order force term or a mean taken where the paper sums
 over placements breaks the equality.  D2Q9 has a complete basis of nine
 multi-indices.  On D3Q27 the scheme keeps Hermite orders <= 4, so the result
 is projected onto the raw orders <= 4 and the input is drawn from that span.
-D3Q19's retained set is not a complete basis; it is covered by the invariants
-below and by GPU-vs-oracle parity.
+D3Q19's retained set is not a complete basis; test_oracle_d3q19 pins it at one
+relaxation time for every order, the invariants below and GPU-vs-oracle parity
+at the others.
 """
 import itertools
 import math
