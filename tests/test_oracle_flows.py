@@ -114,8 +114,8 @@ def test_poiseuille_closed_form():
 def test_poiseuille_smrt_second_difference(coll):
     """SMRT in the same channel, with and without the force's non-equilibrium
     terms: the interior profile has the exact viscosity nu = (tau_2 - 1/2)/3,
-    i.e. second difference -g/nu (wall slip depends on tau_3 and is left to
-    the GPU-oracle parity)."""
+    i.e. second difference -g/nu (the wall slip, which depends on tau_3, is pinned by
+    test_poiseuille_smrt_slip_closed_form)."""
     ny = 32
     s = O.Sim(O.D2Q9, coll, (4, ny, 1), periodic=(1, 0, 1), tau=(1, 1, 0.8, 1.0, 1.0), g=[1e-6, 0])
     s.step(20000)
@@ -124,6 +124,30 @@ def test_poiseuille_smrt_second_difference(coll):
     nu = 0.3 / 3
     d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
     assert np.abs(d2 + 1e-6 / nu).max() < 1e-8 * 1e-6 / nu * 1e3
+
+
+@pytest.mark.parametrize("taus", [(0.8, 0.8, 0.8), (0.8, 1.0, 1.0), (0.8, 0.6, 0.8), (1.1, 0.7, 1.1), (0.8, 0.7, 1.0)])
+def test_poiseuille_smrt_slip_closed_form(taus):
+    """The SMRT wall slip of halfway bounce-back.  In steady force-driven
+    channel flow the even moments relax with tau_2 and the odd ones with
+    tau_3, as in a two-relaxation-time scheme, whose steady link-wise
+    analysis (Ginzburg and co-workers) gives the parabola with the exact
+    viscosity plus a uniform slip
+        u_slip = g (16 Lambda - 3) / (24 nu),  Lambda = (tau_2 - 1/2)(tau_3 - 1/2),
+    (BGK: Lambda = a^2, the closed form above).  The fourth order plays no
+    part, so tau_4 = 1 gives the same profile."""
+    t2, t3, t4 = taus
+    ny, g = 32, 1e-6
+    s = O.Sim(O.D2Q9, O.SMRT, (4, ny, 1), periodic=(1, 0, 1), tau=(1, 1, t2, t3, t4), g=[g, 0])
+    s.step(20000)
+    _, u, _ = s.moments()
+    ux = u[0, 0, :, 0]
+    nu = (t2 - 0.5) / 3
+    y = np.arange(ny) + 0.5
+    lam = (t2 - 0.5) * (t3 - 0.5)
+    ua = g / (2 * nu) * ((ny / 2) ** 2 - (y - ny / 2) ** 2) + g * (16 * lam - 3) / (24 * nu)
+    err = np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+    assert err < 1e-8, err
 
 
 @pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q27])
