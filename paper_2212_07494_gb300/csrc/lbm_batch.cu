@@ -459,6 +459,14 @@ lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
                          std::string(#call) + ": " + cudaGetErrorString(e__));                \
     } while (0)
 
+// a blocking copy in the batch stream's order: the stream need not
+// synchronise with the legacy default stream, and a plain cudaMemcpy from
+// pageable memory may return before its data reaches the device
+cudaError_t bcopy(lbm_batch *b, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, b->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(b->stream) : e;
+}
+
 template <typename T>
 lbm_status balloc(lbm_batch *b, T **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -542,9 +550,9 @@ lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
     cudaGraphExecDestroy(ge);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
     int errflag = 0;
-    B_CUDA(b, cudaMemcpy(&errflag, b->error, sizeof(int), cudaMemcpyDeviceToHost));
+    B_CUDA(b, bcopy(b, &errflag, b->error, sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<BatchCtl> ctl(b->n);
-    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    B_CUDA(b, bcopy(b, ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
     for (int c = 0; c < b->n; ++c) b->steps[c] = ctl[c].steps;
     if (errflag) return bfail(b, (lbm_status)errflag, "batch kernel stopped: no progress within the scan limit");
     return LBM_OK;
@@ -592,7 +600,7 @@ const void *channel_state(const lbm_batch *b, int c) {
 // as if the kernel had run it to the end.
 lbm_status run_parked(lbm_batch *b, double tol, int K, int64_t max_steps) {
     std::vector<BatchCtl> ctl(b->n);
-    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    B_CUDA(b, bcopy(b, ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
     struct Run {
         int p;
         lbm_handle *h;
@@ -622,7 +630,7 @@ lbm_status run_parked(lbm_batch *b, double tol, int K, int64_t max_steps) {
         std::vector<unsigned char> mask;
         if (C.solid_off >= 0) {
             std::vector<unsigned char> pad((size_t)C.plane);
-            cudaError_t e = cudaMemcpy(pad.data(), b->solid + C.solid_off, (size_t)C.plane, cudaMemcpyDeviceToHost);
+            cudaError_t e = bcopy(b, pad.data(), b->solid + C.solid_off, (size_t)C.plane, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) {
                 cleanup();
                 return bfail(b, LBM_ERR_CUDA, std::string("handoff mask: ") + cudaGetErrorString(e));
@@ -674,7 +682,7 @@ lbm_status run_parked(lbm_batch *b, double tol, int K, int64_t max_steps) {
             if (!q.running) continue;
             double v[8] = {0};
             cudaError_t e = cudaStreamSynchronize(handle_stream(q.h));
-            if (e == cudaSuccess && q.check) e = cudaMemcpy(v, red + 8 * k, 7 * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && q.check) e = bcopy(b, v, red + 8 * k, 7 * sizeof(double), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) {
                 cleanup();
                 return bfail(b, LBM_ERR_CUDA, std::string("handoff: ") + cudaGetErrorString(e));
@@ -722,7 +730,7 @@ lbm_status run_parked(lbm_batch *b, double tol, int K, int64_t max_steps) {
         }
     }
     cleanup();
-    B_CUDA(b, cudaMemcpy(b->ctl_dev, ctl.data(), sizeof(BatchCtl) * b->n, cudaMemcpyHostToDevice));
+    B_CUDA(b, bcopy(b, b->ctl_dev, ctl.data(), sizeof(BatchCtl) * b->n, cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -961,7 +969,7 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int K, int64_t max_
     if (st != LBM_OK && st != LBM_ERR_TIMEOUT) return st;
     if (st == LBM_OK && (st = run_parked(b, tol, K, max_steps)) != LBM_OK) return st;
     std::vector<BatchCtl> ctl(b->n);
-    B_CUDA(b, cudaMemcpy(ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
+    B_CUDA(b, bcopy(b, ctl.data(), b->ctl_dev, sizeof(BatchCtl) * b->n, cudaMemcpyDeviceToHost));
     for (int p = 0; p < b->n; ++p) {
         const int c = b->order[p];
         if (steps_out) steps_out[c] = ctl[p].steps;

@@ -259,15 +259,22 @@ void drop_graphs(lbm_handle *h) {
 }
 
 // drop a schedule; the force it replaced goes back into the force buffers
-// (the force set last by lbm_set_force or at creation applies again)
+// (the force set last by lbm_set_force or at creation applies again).  The
+// copies run on the handle's stream, which need not synchronise with the
+// legacy default stream, and are waited for before the buffers are freed.
 void free_schedule(lbm_handle *h) {
     if (h->gbase_dev) {
         const size_t n = h->gdev_count;
         std::vector<double> base(n);
-        if (cudaMemcpy(base.data(), h->gbase_dev, n * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        cudaError_t e = cudaMemcpyAsync(h->g_dev, h->gbase_dev, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base.data(), h->gbase_dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) {
             std::vector<float> base32(base.begin(), base.end());
-            cudaMemcpy(h->g_dev, base.data(), n * sizeof(double), cudaMemcpyHostToDevice);
-            cudaMemcpy(h->g32_dev, base32.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(h->g32_dev, base32.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         }
         cudaGetLastError();
     }
@@ -341,12 +348,17 @@ lbm_status set_schedule(lbm_handle *h, const std::vector<double> &table, int64_t
         free_schedule(h);
         return st;
     }
-    cudaError_t e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
-                                    h->stream);
+    // the base force first: free_schedule restores the force buffers from it
+    cudaError_t e = cudaMemcpyAsync(h->gbase_dev, h->g_dev, h->gdev_count * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) {
+        dev_free(h, h->gbase_dev);
+        h->gbase_dev = nullptr;
+        free_schedule(h);
+        return cuda_fail(h, e, "force schedule upload");
+    }
+    e = cudaMemcpyAsync(h->gs_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->gs_t_dev, 0, sizeof(long long), h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->gbase_dev, h->g_dev, h->gdev_count * sizeof(double), cudaMemcpyDeviceToDevice,
-                            h->stream);
     if (e != cudaSuccess) {
         free_schedule(h);
         return cuda_fail(h, e, "force schedule upload");
