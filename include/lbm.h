@@ -293,7 +293,8 @@ void lbm_batch_destroy(lbm_batch *b);
  * [up path, skip], linear 3x3 head.  BF16 weights and activations, FP32
  * accumulation on the tensor cores (every convolution and input-gradient
  * convolution but the 3-output head as an implicit GEMM on tcgen05 with TMEM
- * accumulators; the head and the weight gradients on mma.sync), FP32 master
+ * accumulators, the weight gradients too where H divides 64 or is a multiple
+ * of 64; the head and the other weight gradients on mma.sync), FP32 master
  * weights and Adam moments.  A tcgen05 convolution whose bounded wait
  * expires is reported as LBM_ERR_TIMEOUT by the next lbm_unet_grad or
  * lbm_unet_get_params (the calls that synchronise).
@@ -320,6 +321,13 @@ lbm_status lbm_unet_adam(lbm_unet *u, float lr, float beta1, float beta2, float 
  * (nullable).  Asynchronous. */
 lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_dev, const float *m_dev, int n,
                                float scale, float lr, double *loss_dev);
+/* Which kernel computes the weight gradients: LBM_UNET_WGRAD_AUTO (the
+ * default) takes the tcgen05 one wherever the shape allows, and
+ * LBM_UNET_WGRAD_MMA_SYNC the mma.sync one everywhere.  Both compute the
+ * same sums in FP32 in different orders.  Synchronises the network's
+ * stream; LBM_ERR_ARG for another kind. */
+enum { LBM_UNET_WGRAD_AUTO = 0, LBM_UNET_WGRAD_MMA_SYNC = 1 };
+lbm_status lbm_unet_set_wgrad(lbm_unet *u, int kind);
 const char *lbm_unet_last_error(const lbm_unet *u);
 void lbm_unet_destroy(lbm_unet *u);
 

@@ -22,4 +22,5 @@ from ._binding import (  # noqa: F401
     lbm_batch_moments, lbm_batch_get_populations, lbm_batch_set_tiles, lbm_batch_autotune,
     lbm_batch_set_spin_limit, lbm_batch_set_handoff, lbm_batch_info, lbm_batch_last_error, lbm_batch_destroy, LBM_NOT_CONVERGED,
     UNet, lbm_unet_create, lbm_unet_num_params, lbm_unet_set_params, lbm_unet_get_params, lbm_unet_forward,
-    lbm_unet_grad, lbm_unet_adam, lbm_unet_train_step, lbm_unet_destroy, lbm_unet_last_error)
+    lbm_unet_grad, lbm_unet_adam, lbm_unet_train_step, lbm_unet_set_wgrad, UNET_WGRAD_AUTO, UNET_WGRAD_MMA_SYNC,
+    lbm_unet_destroy, lbm_unet_last_error)

@@ -574,12 +574,13 @@ def _unet_lib():
         L.lbm_unet_grad.argtypes = [U, fp, fp, fp, C.c_int, C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)]
         L.lbm_unet_adam.argtypes = [U, C.c_float, C.c_float, C.c_float, C.c_float]
         L.lbm_unet_train_step.argtypes = [U, fp, fp, fp, C.c_int, C.c_float, C.c_float, C.c_void_p]
+        L.lbm_unet_set_wgrad.argtypes = [U, C.c_int]
         L.lbm_unet_last_error.argtypes = [U]
         L.lbm_unet_last_error.restype = C.c_char_p
         L.lbm_unet_destroy.argtypes = [U]
         L.lbm_unet_destroy.restype = None
         for n in ("lbm_unet_create", "lbm_unet_set_params", "lbm_unet_get_params", "lbm_unet_forward",
-                  "lbm_unet_grad", "lbm_unet_adam", "lbm_unet_train_step"):
+                  "lbm_unet_grad", "lbm_unet_adam", "lbm_unet_train_step", "lbm_unet_set_wgrad"):
             getattr(L, n).restype = C.c_int
         L._unet_ready = True
     return L
@@ -631,6 +632,13 @@ def lbm_unet_train_step(u, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr=None):
     _ucheck(_unet_lib().lbm_unet_train_step(u, x_ptr, t_ptr, m_ptr, int(n), float(scale), float(lr), loss_ptr), u)
 
 
+UNET_WGRAD_AUTO, UNET_WGRAD_MMA_SYNC = 0, 1
+
+
+def lbm_unet_set_wgrad(u, kind):
+    _ucheck(_unet_lib().lbm_unet_set_wgrad(u, int(kind)), u)
+
+
 def lbm_unet_destroy(u):
     _unet_lib().lbm_unet_destroy(u)
 
@@ -665,6 +673,10 @@ class UNet:
 
     def train_step(self, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr=None):
         lbm_unet_train_step(self.u, x_ptr, t_ptr, m_ptr, n, scale, lr, loss_ptr)
+
+    def set_wgrad(self, kind):
+        """"auto" (tcgen05 where the shape allows) or "mma_sync"."""
+        lbm_unet_set_wgrad(self.u, {"auto": UNET_WGRAD_AUTO, "mma_sync": UNET_WGRAD_MMA_SYNC}[kind])
 
     def close(self):
         if getattr(self, "u", None) is not None:

@@ -11,7 +11,8 @@
 //   input grad   dx[p][ci] = sum_{tap,co} dz[p-tap][co] W[co][tap][ci]
 //                (the same kernel with the flipped, transposed weights)
 //   weight grad  dW[co][tap][ci] = sum_p dz[p][co] x[p+tap][ci]
-//                (split over pixel chunks, FP32 atomics)
+//                (split over pixel chunks, FP32 atomics; tcgen05 with
+//                MN-major operands where the shape allows, else mma.sync)
 // Concatenation is free: producers write into channel slices of one buffer.
 // Master weights and Adam moments are FP32; each update repacks the BF16
 // copies used by the forward and input-gradient kernels.
@@ -686,6 +687,200 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
             }
 }
 
+// ------------------------------------------- weight gradient on tcgen05 (TMEM)
+// dW[co][tap][ci] = sum_p dz[p][co] x[p + tap][ci] as one GEMM per CTA on the
+// 5th-generation tensor cores, D[m][co] += sum_p A[m][p] B[co][p]: a row m of
+// D is one input channel of one (tap, channel block) pair, 128 rows per CTA
+// (128 / CA pairs of CA channels), and N = the layer's padded output
+// channels.  The contraction runs over pixels in blocks of 64 along one x
+// column: HB rows y of NB images (HB NB = 64), as the forward kernel's column
+// tiles.  The x operand of pair (tap, block) for a pixel block is the TMA box
+// at column x + dx (modulo W, or reading zeros outside the image) and rows
+// y + dy (zeros outside), the dz operand the unshifted box, so every operand
+// is one plain 4-D box per atom.
+// Both operands arrive channel-contiguous, i.e. MN-major: an atom is CA (A)
+// or CB (B) channels wide -- the swizzle width, 64 -> 128 B, 32 -> 64 B,
+// 16 -> 32 B -- and 64 pixel rows deep; the atoms of an operand lie one atom
+// apart (the descriptor's leading offset), 8-row pixel groups 8 rows apart
+// (its stride offset), and the MMA's K slices of 16 pixels start 16 rows
+// apart.  The instruction descriptor marks both operands MN-major.  CTAs
+// split the pixel blocks between them and add their 128 x N partial sums to
+// dW with FP32 atomics.  One thread issues the copies, one the MMAs; four
+// stages; every wait is bounded, as in k_conv_tma.
+struct WgTcArgs {
+    float *dw;           // [cout][9][cin]
+    int cin, cout;       // padded channels (cout = the MMA's N)
+    int H, W;
+    int HB, NB;          // a pixel block: HB rows of NB images at one x
+    int wrapx;
+    int CA, CB;          // atom widths of the x and dz operands (channels)
+    int pairs;           // 9 cin / CA (tap, channel block) pairs
+    long long kb_total;  // pixel blocks
+    int kb_per;          // pixel blocks per CTA
+    unsigned ncol;       // TMEM columns (power of two >= 32, >= cout)
+};
+constexpr int WG_S = 4;
+constexpr unsigned WG_ABYTES = 128 * 64 * 2;  // the x operand: 128 rows of 64 pixels
+constexpr unsigned wg_stage_bytes(int cout) { return WG_ABYTES + (unsigned)cout * 64 * 2; }
+
+__device__ __forceinline__ uint64_t sw_mode_bytes(int rowbytes) { return rowbytes == 128 ? 2 : (rowbytes == 64 ? 4 : 6); }
+
+// shared memory descriptor of an MN-major swizzled operand
+__device__ __forceinline__ uint64_t tc_desc_mn(unsigned saddr, unsigned lbo, unsigned sbo, uint64_t mode) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= mode << 61;
+    return d;
+}
+
+__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(160) k_wgrad_tc(const WgTcArgs a, const __grid_constant__ CUtensorMap tmX,
+                                                  const __grid_constant__ CUtensorMap tmZ, int *err) {
+    extern __shared__ __align__(1024) unsigned char wg_smem[];
+    __shared__ __align__(8) unsigned long long full[WG_S], empty[WG_S], done;
+    __shared__ unsigned tmem_base;
+    __shared__ volatile int s_fail;
+    __shared__ int s_consumed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *sm = (unsigned char *)(((uintptr_t)wg_smem + 1023) & ~(uintptr_t)1023);
+    const unsigned STAGE = wg_stage_bytes(a.cout);
+    const int per_tile = 128 / a.CA;                // pairs per CTA
+    const int p0 = blockIdx.y * per_tile;
+    const int np = min(per_tile, a.pairs - p0);     // pairs this CTA loads (>= 1)
+    const int cblocks = a.cin / a.CA;
+    const int ytiles = a.H / a.HB;
+    const int nb_atoms = a.cout / a.CB;
+    const unsigned arow = 2u * a.CA, brow = 2u * a.CB;      // bytes of one pixel row of an atom
+    const unsigned aatom = 64u * arow, batom = 64u * brow;  // bytes of one atom
+    const long long kb0 = (long long)blockIdx.x * a.kb_per;
+    const int KB = (int)min((long long)a.kb_per, a.kb_total - kb0);  // >= 1
+    if (tid == 0) {
+        s_fail = 0;
+        s_consumed = 0;
+        for (int s = 0; s < WG_S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(a.ncol));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    int issued = 0;
+    if (tid == 0) {
+        // ---- producer: np x boxes and nb_atoms dz boxes per pixel block
+        const unsigned tx = (unsigned)np * aatom + (unsigned)nb_atoms * batom;
+        for (int i = 0; i < KB; ++i) {
+            const int s = i % WG_S;
+            if (i >= WG_S && !ws_wait(&empty[s], (i / WG_S - 1) & 1, &s_fail)) break;
+            const long long kb = kb0 + i;
+            const int xcol = (int)(kb % a.W);
+            const long long rest = kb / a.W;
+            const int y0 = (int)(rest % ytiles) * a.HB, n0 = (int)(rest / ytiles) * a.NB;
+            const unsigned sa = smem_addr(sm + (size_t)s * STAGE), sb = sa + WG_ABYTES, mb = smem_addr(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx) : "memory");
+            for (int j = 0; j < np; ++j) {
+                const int pr = p0 + j;
+                const int tap = pr / cblocks, c0 = (pr - tap * cblocks) * a.CA;
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                int xx = xcol + dx;
+                if (a.wrapx) xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+                tma_load4(sa + j * aatom, &tmX, c0, xx, y0 + dy, n0, mb);
+            }
+            for (int j = 0; j < nb_atoms; ++j) tma_load4(sb + j * batom, &tmZ, j * a.CB, xcol, y0, n0, mb);
+            issued = i + 1;
+        }
+    } else if (warp == 4 && lane == 0) {
+        // ---- MMA issuer: M = 128, N = cout, both operands MN-major
+        const uint32_t idesc = tc_idesc(128, a.cout) | (1u << 15) | (1u << 16);
+        const uint64_t amode = sw_mode_bytes(arow), bmode = sw_mode_bytes(brow);
+        int i = 0;
+        for (; i < KB; ++i) {
+            const int s = i % WG_S;
+            if (!ws_wait(&full[s], (i / WG_S) & 1, &s_fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned sa = smem_addr(sm + (size_t)s * STAGE), sb = sa + WG_ABYTES;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t da = tc_desc_mn(sa + ks * 16 * arow, aatom, 8 * arow, amode);
+                const uint64_t db = tc_desc_mn(sb + ks * 16 * brow, batom, 8 * brow, bmode);
+                const unsigned acc = (i > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                    "}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&empty[s])));
+        }
+        s_consumed = i;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&done)));
+    }
+    if (warp < 4) {
+        // epilogue: warp w holds rows 32w .. 32w + 31; rows of pairs this CTA
+        // did not load are never written
+        const bool ok = __all_sync(0xffffffffu, ws_wait(&done, 0, &s_fail) && !s_fail);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            const int m = warp * 32 + lane;
+            const int j = m / a.CA;
+            const int pr = p0 + j;
+            const int tap = pr / cblocks;
+            const int ci = (pr - tap * cblocks) * a.CA + (m - j * a.CA);
+            const bool valid = j < np;
+            float *dst = a.dw + (long long)tap * a.cin + ci;
+            const long long co_stride = 9LL * a.cin;
+            for (int c = 0; c < a.cout; c += 16) {
+                unsigned r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) atomicAdd(dst + (c + jj) * co_stride, __uint_as_float(r[jj]));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail) {
+        // copies still in flight land, and issued MMAs finish, before the
+        // CTA frees its TMEM and leaves
+        volatile int never = 0;
+        for (int i = s_consumed; i < issued; ++i) ws_wait(&full[i % WG_S], (i / WG_S) & 1, &never);
+        ws_wait(&done, 0, &never);
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.ncol));
+}
+
 // ------------------------------------------------------------- small kernels
 // bias gradient: db[c] += sum_p dz[p][c].  A block of 8 x 32 threads takes
 // 32 channels of a chunk of kBiasChunk pixels: a warp reads 32 adjacent
@@ -875,6 +1070,7 @@ struct lbm_unet {
     int cin = 3;        // input channels of the first layer
     int wrapx = 0;      // periodic padding along x in every convolution
     int sms = 152;      // multiprocessors of the device
+    int wgrad_kind = LBM_UNET_WGRAD_AUTO;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Layer L[kL];
@@ -1083,8 +1279,96 @@ lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H
     return LBM_OK;
 }
 
+// The tcgen05 weight gradient when the shape suits its pixel blocks (64
+// pixels of one column: H <= 64 dividing 64 with n a multiple of 64 / H, or H
+// a multiple of 64) and every global address and stride is a multiple of 16
+// bytes.  Returns false (nothing launched) otherwise, and when a tensor map
+// cannot be made.  The pixel blocks are split so that about two CTAs per SM
+// run, each taking at least 8 blocks (its 128 x N atomics stay small against
+// its MMA work).
+bool launch_wgrad_tc(lbm_unet *u, const Layer &l, const bf16 *dz, int dzc, const bf16 *x, int xc, int xo, int n,
+                     int H, int W, lbm_status *st) {
+    const int HB = H <= 64 ? H : 64;
+    const int NB = H <= 64 ? 64 / H : 1;
+    if (H <= 64 ? (64 % H != 0 || n % NB != 0) : (H % 64 != 0)) return false;
+    const int cin = l.cinp, cout = l.coutp;
+    // atom widths are swizzle widths: 16, 32 or 64 channels
+    if ((cin < 64 ? (cin != 16 && cin != 32) : cin % 64 != 0) || cout > 256 || (cout < 64 ? cout != 32 : cout % 64 != 0))
+        return false;
+    if (xc % 8 != 0 || xo % 8 != 0 || dzc % 8 != 0 || xc < xo + cin || dzc < cout ||
+        ((uintptr_t)(x + xo)) % 16 != 0 || ((uintptr_t)dz) % 16 != 0)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const int CA = cin >= 64 ? 64 : cin, CB = cout >= 64 ? 64 : cout;
+    auto swz = [](int ch) {
+        return ch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    };
+    alignas(64) CUtensorMap tx, tz;
+    const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+    const cuuint64_t gdX[4] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t rx = (cuuint64_t)xc * 2;
+    const cuuint64_t gsX[3] = {rx, rx * W, rx * W * H};
+    const cuuint32_t boxX[4] = {(cuuint32_t)CA, 1u, (cuuint32_t)HB, (cuuint32_t)NB};
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(x + xo), gdX, gsX, boxX, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz(CA), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t gdZ[4] = {(cuuint64_t)cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t rz = (cuuint64_t)dzc * 2;
+    const cuuint64_t gsZ[3] = {rz, rz * W, rz * W * H};
+    const cuuint32_t boxZ[4] = {(cuuint32_t)CB, 1u, (cuuint32_t)HB, (cuuint32_t)NB};
+    if (enc(&tz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)dz, gdZ, gsZ, boxZ, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swz(CB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    WgTcArgs a{};
+    a.dw = u->g + l.woff;
+    a.cin = cin;
+    a.cout = cout;
+    a.H = H;
+    a.W = W;
+    a.HB = HB;
+    a.NB = NB;
+    a.wrapx = u->wrapx;
+    a.CA = CA;
+    a.CB = CB;
+    a.pairs = 9 * cin / CA;
+    a.kb_total = (long long)n * H * W / 64;
+    a.ncol = cout <= 32 ? 32u : (cout <= 64 ? 64u : (cout <= 128 ? 128u : 256u));
+    const int mtiles = (a.pairs + 128 / CA - 1) / (128 / CA);
+    long long splits = (2LL * u->sms + mtiles - 1) / mtiles;
+    const long long cap = a.kb_total / 8 > 0 ? a.kb_total / 8 : 1;
+    if (splits > cap) splits = cap;
+    a.kb_per = (int)((a.kb_total + splits - 1) / splits);
+    splits = (a.kb_total + a.kb_per - 1) / a.kb_per;  // every CTA gets at least one block
+    const size_t smem = (size_t)WG_S * wg_stage_bytes(256) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            *st = ufail(u, LBM_ERR_CUDA, std::string("k_wgrad_tc attribute: ") + cudaGetErrorString(e));
+            return true;
+        }
+        attr = true;
+    }
+    const size_t need = (size_t)WG_S * wg_stage_bytes(cout) + 1024;
+    k_wgrad_tc<<<dim3((unsigned)splits, (unsigned)mtiles), 160, need, u->stream>>>(a, tx, tz, u->tc_err);
+    cudaError_t e = cudaGetLastError();
+    *st = e == cudaSuccess ? LBM_OK : ufail(u, LBM_ERR_CUDA, std::string("k_wgrad_tc: ") + cudaGetErrorString(e));
+    return true;
+}
+
 lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, int xc, int xo, int n, int H, int W) {
     const Layer &l = u->L[li];
+    const long long P = (long long)n * H * W;
+    lbm_status st = LBM_OK;
+    if (u->wgrad_kind == LBM_UNET_WGRAD_AUTO && launch_wgrad_tc(u, l, dz, dzc, x, xc, xo, n, H, W, &st)) {
+        if (st != LBM_OK) return st;
+        k_bias_grad<<<dim3(nblk(P, kBiasChunk), (l.cout + 31) / 32), 256, 0, u->stream>>>(dz, dzc, 0, l.cout, P,
+                                                                                         u->g + l.boff);
+        U_CUDA(u, cudaGetLastError());
+        return LBM_OK;
+    }
     WgradArgs a{};
     a.dz = dz;
     a.dzc = dzc;
@@ -1099,7 +1383,6 @@ lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, in
     a.cin = l.cinp;
     a.cout = l.coutp;
     a.wrapx = u->wrapx;
-    const long long P = (long long)n * H * W;
     a.pix = 2048;
     dim3 grid(nblk(P, a.pix), nblk(l.coutp, WBM), 9 * ((l.cinp + WBN - 1) / WBN));
     k_wgrad<<<grid, 128, 0, u->stream>>>(a);
@@ -1437,6 +1720,15 @@ lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_d
     if (st == LBM_OK) st = lbm_unet_adam(u, lr, 0.9f, 0.999f, 1e-8f);
     if (st != LBM_OK) return st;
     if (loss_dev) U_CUDA(u, cudaMemcpyAsync(loss_dev, u->loss, sizeof(double), cudaMemcpyDeviceToDevice, u->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_set_wgrad(lbm_unet *u, int kind) {
+    if (!u) return ufail(nullptr, LBM_ERR_ARG, "network is NULL");
+    if (kind != LBM_UNET_WGRAD_AUTO && kind != LBM_UNET_WGRAD_MMA_SYNC)
+        return ufail(u, LBM_ERR_ARG, "kind must be LBM_UNET_WGRAD_AUTO or LBM_UNET_WGRAD_MMA_SYNC");
+    U_CUDA(u, cudaStreamSynchronize(u->stream));
+    u->wgrad_kind = kind;
     return LBM_OK;
 }
 

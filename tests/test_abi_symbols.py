@@ -90,3 +90,8 @@ def test_bulk_tau_arguments_are_checked_without_a_gpu(lib):
         d, keep = P.make_desc("D2Q9", coll, (8, 8), (1, 1, 0.8, 1, 1), tau_bulk=tb)
         assert lib.lbm_create(ctypes.byref(d), ctypes.byref(h)) == -1, coll
         assert b"tau_bulk" in lib.lbm_last_error(None)
+
+
+def test_unet_wgrad_selector_rejects_a_null_network(lib):
+    lib.lbm_unet_set_wgrad.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.lbm_unet_set_wgrad(None, 0) == -1

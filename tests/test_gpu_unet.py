@@ -94,6 +94,44 @@ def test_gradient_matches_oracle(H, W, n, cin, periodic_x):
     net.close()
 
 
+# shapes where the tcgen05 weight gradient takes every layer (128 x 16 x 8,
+# 128 x 160 x 8) or the layers whose H divides 64 with the batch a multiple of
+# 64 / H (64 x 32 x 4; the 8 x 4 bottom stays on mma.sync)
+@pytest.mark.parametrize("H,W,n,cin,periodic_x", [(128, 16, 8, 8, True), (64, 32, 4, 3, False),
+                                                  (128, 160, 8, 8, True)])
+def test_weight_gradient_kernels_agree(H, W, n, cin, periodic_x):
+    """The tcgen05 weight gradient (MN-major operands, pixel blocks split
+    over CTAs) and the mma.sync one sum the same BF16 products in FP32 in
+    different orders: every layer's weight gradient agrees to 1e-4 relative
+    L2.  One dropped or doubled 64-pixel block, a wrong tap or a transposed
+    operand is far above that; the oracle comparison above bounds both."""
+    import paper_2212_07494_gb300 as P
+    params, x, t, m = _problem(H, W, n, 5, cin)
+    net = P.UNet(H, W, n, cin=cin, periodic_x=periodic_x)
+    net.set_params(params)
+    scale = 1.0 / (3.0 * m.sum())
+    xd, td, md = _dev(x), _dev(t), _dev(m)
+    loss_a, ga = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), n, scale)
+    net.set_wgrad("mma_sync")
+    loss_b, gb = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), n, scale)
+    net.set_wgrad("auto")
+    loss_c, gc = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), n, scale)
+    net.close()
+    assert abs(loss_a - loss_b) <= 1e-12 * abs(loss_b) and abs(loss_c - loss_b) <= 1e-12 * abs(loss_b)
+    sl, total = U.layer_slices(cin)
+    worst = {}
+    for name, ci, co, relu, wo, bo in sl:
+        wa, wb = ga[wo:bo].astype(np.float64), gb[wo:bo].astype(np.float64)
+        worst[name] = np.linalg.norm(wa - wb) / np.linalg.norm(wb)
+        ba, bb = ga[bo:bo + co].astype(np.float64), gb[bo:bo + co].astype(np.float64)
+        assert np.linalg.norm(ba - bb) <= 1e-5 * np.linalg.norm(bb), name   # bias: the same kernel
+    print("weight gradient, tcgen05 vs mma.sync, rel L2 per layer: " +
+          " ".join(f"{k} {v:.1e}" for k, v in worst.items()))
+    assert max(worst.values()) < 1e-4, worst
+    rerun = max(np.linalg.norm(gc[wo:bo] - ga[wo:bo]) / np.linalg.norm(ga[wo:bo]) for _, _, _, _, wo, bo in sl)
+    assert rerun < 1e-5, rerun
+
+
 def test_params_round_trip():
     import paper_2212_07494_gb300 as P
     params, *_ = _problem(16, 16, 1, 3)
