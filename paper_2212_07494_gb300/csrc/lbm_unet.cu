@@ -882,33 +882,40 @@ __global__ void __launch_bounds__(160) k_wgrad_tc(const WgTcArgs a, const __grid
 }
 
 // ------------------------------------------------------------- small kernels
-// bias gradient: db[c] += sum_p dz[p][c].  A block of 8 x 32 threads takes
-// 32 channels of a chunk of kBiasChunk pixels: a warp reads 32 adjacent
-// channels of one pixel, each thread keeps four independent sums over every
-// 8th pixel, the 8 rows meet in shared memory, one atomic per channel.
-constexpr int kBiasChunk = 512;
-__global__ void __launch_bounds__(256) k_bias_grad(const bf16 *dz, int dzc, int dzo, int C, long long P, float *db) {
-    const int cl = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int c = blockIdx.y * 32 + cl;
-    const long long p0 = (long long)blockIdx.x * kBiasChunk;
-    const long long p1 = p0 + kBiasChunk < P ? p0 + kBiasChunk : P;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    if (c < C) {
-        long long p = p0 + row;
-        for (; p + 24 < p1; p += 32) {
+// bias gradient: db[c] += sum_p dz[p][c].  A block of 256 threads takes all
+// C channels of a chunk of pixels.  Thread t reads the 8 channels of group
+// t mod G (G = ceil(C / 8)) 16 bytes at a time, in R = 256 / G pixel rows
+// (row t / G takes pixels p0 + row, p0 + row + R, ...); the rows meet in
+// shared memory and each channel's sum goes out in one atomic.  Channels
+// C .. 8 G - 1 are read (the buffer has them: its stride is a multiple of 8)
+// but never written.
+constexpr int kBiasLoads = 16;  // loads per thread and block
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16 *dz, int dzc, int C, long long P, int chunk, float *db) {
+    __shared__ float sh[256 * 8];
+    const int G = (C + 7) >> 3, R = 256 / G;
+    const int t = threadIdx.x, g = t % G, r = t / G;
+    const long long p0 = (long long)blockIdx.x * chunk;
+    const long long p1 = p0 + chunk < P ? p0 + chunk : P;
+    if (r < R) {
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (long long p = p0 + r; p < p1; p += R) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(dz + p * dzc + g * 8);
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s[k] += __bfloat162float(dz[(p + 8 * k) * dzc + dzo + c]);
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(h[k]);
+                s[2 * k] += f.x;
+                s[2 * k + 1] += f.y;
+            }
         }
-        for (; p < p1; p += 8) s[0] += __bfloat162float(dz[p * dzc + dzo + c]);
-    }
-    __shared__ float sh[8][32];
-    sh[row][cl] = (s[0] + s[1]) + (s[2] + s[3]);
-    __syncthreads();
-    if (row == 0 && c < C) {
-        float t = 0.f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) t += sh[r][cl];
-        atomicAdd(db + c, t);
+        for (int k = 0; k < 8; ++k) sh[(r * G + g) * 8 + k] = s[k];
+    }
+    __syncthreads();
+    for (int c = t; c < C; c += 256) {
+        float tot = 0.f;
+        for (int rr = 0; rr < R; ++rr) tot += sh[rr * G * 8 + c];
+        atomicAdd(db + c, tot);
     }
 }
 
@@ -1279,6 +1286,19 @@ lbm_status conv(lbm_unet *u, int li, const bf16 *x, int xc, int xo, int n, int H
     return LBM_OK;
 }
 
+// db += the per-channel sums of dz (C <= 256 channels of a buffer whose
+// channel stride dzc is a multiple of 8 and at least 8 ceil(C / 8), 16-byte
+// aligned: every gradient buffer of the network is)
+lbm_status bias_grad(lbm_unet *u, const bf16 *dz, int dzc, int C, long long P, float *db) {
+    const int G = (C + 7) / 8;
+    if (C < 1 || C > 256 || dzc % 8 != 0 || dzc < 8 * G || ((uintptr_t)dz) % 16 != 0)
+        return ufail(u, LBM_ERR_STATE, "bias gradient: unsupported gradient buffer layout");
+    const int chunk = (256 / G) * kBiasLoads;
+    k_bias_grad<<<nblk(P, chunk), 256, 0, u->stream>>>(dz, dzc, C, P, chunk, db);
+    U_CUDA(u, cudaGetLastError());
+    return LBM_OK;
+}
+
 // The tcgen05 weight gradient when the shape suits its pixel blocks (64
 // pixels of one column: H <= 64 dividing 64 with n a multiple of 64 / H, or H
 // a multiple of 64) and every global address and stride is a multiple of 16
@@ -1364,10 +1384,7 @@ lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, in
     lbm_status st = LBM_OK;
     if (u->wgrad_kind == LBM_UNET_WGRAD_AUTO && launch_wgrad_tc(u, l, dz, dzc, x, xc, xo, n, H, W, &st)) {
         if (st != LBM_OK) return st;
-        k_bias_grad<<<dim3(nblk(P, kBiasChunk), (l.cout + 31) / 32), 256, 0, u->stream>>>(dz, dzc, 0, l.cout, P,
-                                                                                         u->g + l.boff);
-        U_CUDA(u, cudaGetLastError());
-        return LBM_OK;
+        return bias_grad(u, dz, dzc, l.cout, P, u->g + l.boff);
     }
     WgradArgs a{};
     a.dz = dz;
@@ -1387,10 +1404,7 @@ lbm_status wgrad(lbm_unet *u, int li, const bf16 *dz, int dzc, const bf16 *x, in
     dim3 grid(nblk(P, a.pix), nblk(l.coutp, WBM), 9 * ((l.cinp + WBN - 1) / WBN));
     k_wgrad<<<grid, 128, 0, u->stream>>>(a);
     U_CUDA(u, cudaGetLastError());
-    k_bias_grad<<<dim3(nblk(P, kBiasChunk), (l.cout + 31) / 32), 256, 0, u->stream>>>(dz, dzc, 0, l.cout, P,
-                                                                                     u->g + l.boff);
-    U_CUDA(u, cudaGetLastError());
-    return LBM_OK;
+    return bias_grad(u, dz, dzc, l.cout, P, u->g + l.boff);
 }
 
 lbm_status repack(lbm_unet *u) {

@@ -85,8 +85,14 @@ def test_gradient_matches_oracle(H, W, n, cin, periodic_x):
     sl, total = U.layer_slices(cin)
     per = {name: np.linalg.norm(g[wo:bo + co] - gr[wo:bo + co]) / np.linalg.norm(gr[wo:bo + co])
            for name, ci, co, relu, wo, bo in sl}
+    # the bias gradients alone (their own kernel): per-channel sums of dz
+    bias = {name: np.linalg.norm(g[bo:bo + co] - gr[bo:bo + co]) / np.linalg.norm(gr[bo:bo + co])
+            for name, ci, co, relu, wo, bo in sl}
     print(f"loss {loss:.6g} vs {lr_:.6g}; grad cos {cos:.5f} rel {rel:.2e}; worst layer "
-          f"{max(per, key=per.get)} {max(per.values()):.2e}")
+          f"{max(per, key=per.get)} {max(per.values()):.2e}; worst bias {max(bias, key=bias.get)} "
+          f"{max(bias.values()):.2e}")
+    for name, r in bias.items():
+        assert r < 0.2, ("bias", name, r)
     assert abs(loss - lr_) / lr_ < 1e-2, (loss, lr_)
     assert cos > 0.99 and rel < 1e-1, (cos, rel)
     for name, r in per.items():
