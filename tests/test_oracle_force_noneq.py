@@ -24,8 +24,9 @@ over placements breaks the equality.  D2Q9 has a complete basis of nine
 multi-indices.  On D3Q27 the scheme keeps Hermite orders <= 4, so the result
 is projected onto the raw orders <= 4 and the input is drawn from that span.
 D3Q19's retained set is not a complete basis; test_oracle_d3q19 pins it at one
-relaxation time for every order, the invariants below and GPU-vs-oracle parity
-at the others.
+relaxation time for every order, the shear-wave test of test_oracle_flows at
+unequal ones (its decay rate is the shear viscosity's), and the invariants
+below and GPU-vs-oracle parity cover the rest.
 """
 import itertools
 import math
