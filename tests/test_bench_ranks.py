@@ -65,3 +65,32 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
 
     bench.run_reference(A(), 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_carries_the_contract_keys(capsys):
+    """Rank 0 of the reference arm times the FP64 oracle on a strip of the
+    workload and prints one JSON line with the GPU arm's metric, unit and
+    workload, its own cpu_baseline, and an e2e with no host-device bytes."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        n, steps, warmup = 64, 3, 3
+
+    bench.run_reference(A(), 1, 0)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"]["workload"] == bench.WORKLOAD
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (3, 3, 1)
+    assert d["ms_per_step"] > 0 and d["scaling"] == "weak" and d["data"] == "synthetic"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == d["unit"]
+    assert cb["cores"] >= 1 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
