@@ -47,6 +47,14 @@
  *    collision section).
  *  - boundaries: periodic, or halfway bounce-back at -1/2 and n-1/2 and at
  *    solid nodes.
+ *
+ * Pins: every computation here is checked by CPU tests (tests/test_oracle_*)
+ * against something other than itself -- quadrature and orthogonality
+ * identities, exact transform and shift identities, the textbook Guo update,
+ * the trapezoidal rule restated in population space (D2Q9, D3Q27), raw-moment
+ * relaxation at one relaxation time (D3Q19), brute-force streaming, and
+ * closed-form flows (Poiseuille with its wall slip, Kolmogorov, shear and
+ * sound waves, Taylor-Green, Womersley).  No function is parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>

@@ -17,7 +17,9 @@ with the CUDA library: for each layer in LAYERS order, W[co][ky][kx][ci]
 followed by b[co].
 
 This module is plain numpy, written from the definitions above; it shares no
-code with the CUDA path.
+code with the CUDA path.  Pins (tests/test_oracle_unet.py): the convolution
+equals the direct sum over taps and channels, the backward pass is the exact
+adjoint of the forward one, and the gradient matches finite differences.
 """
 from __future__ import annotations
 
