@@ -36,8 +36,8 @@ def _dev(a):
 # (24, 40, 2) and batch-1 shapes take the cp.async-fed convolution at every
 # level; (128, 16, 8) takes the TMA-fed one at every level (column tiles of
 # 128 / H images), and (64, 32, 4) mixes the two (TMA where 128 / H divides
-# the batch); (128, 160, 8) has 1280 column tiles at full resolution, which
-# run persistent
+# the batch); (128, 160, 8) has 1280 column tiles at full resolution, more
+# CTAs than the SMs hold at once
 @pytest.mark.parametrize("H,W,n,cin,periodic_x", [(24, 40, 2, 3, False), (64, 128, 1, 3, False),
                                                   (24, 40, 2, 5, True), (32, 64, 1, 16, True),
                                                   (128, 16, 8, 8, True), (64, 32, 4, 3, False),
