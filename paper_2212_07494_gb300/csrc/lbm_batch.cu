@@ -168,7 +168,9 @@ __host__ __device__ inline int tiles_for(int nx, int ny, long long active, int g
     return (ny + rows - 1) / rows;
 }
 
-// batch storage is FP32 or FP64 (loads through L2: ld.global.cg)
+// batch storage is FP32 or FP64 (loads through L2: ld.global.cg).  The
+// launch bounds cap the kernel at 64 registers (no spills in FP32), so 8
+// blocks of 128 threads share an SM instead of 6.
 template <int COLL, int ST>
 __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
     typedef typename Store<ST>::T T;
