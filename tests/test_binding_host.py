@@ -1,7 +1,6 @@
 """The Python binding's argument marshalling, on the CPU: make_desc lays out
 the C descriptor as include/lbm.h defines it and refuses arrays of the wrong
 size before anything reaches the library."""
-import ctypes
 
 import numpy as np
 import pytest
