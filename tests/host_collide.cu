@@ -31,6 +31,44 @@ int run(int coll, const double *din, const double *g, const double *tau, double 
     return 0;
 }
 
+// An arithmetic type that counts the additions (and subtractions),
+// multiplications and divisions done on it: the collision templates
+// instantiated with it give their operation counts per node, as written in
+// the source, before the compiler fuses or hoists anything.
+struct Cnt {
+    double v;
+    static long long add, mul, div;
+    __host__ __device__ Cnt() : v(0) {}
+    __host__ __device__ Cnt(double x) : v(x) {}
+    __host__ __device__ explicit operator double() const { return v; }
+};
+long long Cnt::add = 0, Cnt::mul = 0, Cnt::div = 0;
+#ifndef __CUDA_ARCH__
+#define HC_COUNT(k) (++Cnt::k)
+#else
+#define HC_COUNT(k) ((void)0)
+#endif
+__host__ __device__ inline Cnt operator+(Cnt a, Cnt b) { HC_COUNT(add); return Cnt(a.v + b.v); }
+__host__ __device__ inline Cnt operator-(Cnt a, Cnt b) { HC_COUNT(add); return Cnt(a.v - b.v); }
+__host__ __device__ inline Cnt operator*(Cnt a, Cnt b) { HC_COUNT(mul); return Cnt(a.v * b.v); }
+__host__ __device__ inline Cnt operator/(Cnt a, Cnt b) { HC_COUNT(div); return Cnt(a.v / b.v); }
+__host__ __device__ inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+__host__ __device__ inline Cnt &operator+=(Cnt &a, Cnt b) { return a = a + b; }
+__host__ __device__ inline Cnt &operator-=(Cnt &a, Cnt b) { return a = a - b; }
+__host__ __device__ inline Cnt &operator*=(Cnt &a, Cnt b) { return a = a * b; }
+
+template <int L> int count_ops(int coll, long long *out) {
+    double din[Lat<L>::Q], dout[Lat<L>::Q];
+    for (int i = 0; i < Lat<L>::Q; ++i) din[i] = 1e-3 * (i + 1);
+    const double g[3] = {1e-6, -2e-6, 3e-6}, tau[5] = {1.0, 1.0, 0.8, 1.1, 1.2};
+    Cnt::add = Cnt::mul = Cnt::div = 0;
+    const int st = run<L, Cnt>(coll, din, g, tau, coll == SMRT_TRIM ? 0.0 : 0.9, dout);
+    out[0] = Cnt::add;
+    out[1] = Cnt::mul;
+    out[2] = Cnt::div;
+    return st;
+}
+
 template <int L> void velocities(int *c) {
     for (int i = 0; i < Lat<L>::Q; ++i) {
         c[3 * i + 0] = Lat<L>::cx(i);
@@ -53,6 +91,15 @@ extern "C" int host_collide(int lat, int coll, int fp32, const double *din, cons
                                   : run<D3Q19, double>(coll, din, g, tau, tau_bulk, dout);
     if (lat == D3Q27) return fp32 ? run<D3Q27, float>(coll, din, g, tau, tau_bulk, dout)
                                   : run<D3Q27, double>(coll, din, g, tau, tau_bulk, dout);
+    return -1;
+}
+
+// operations one collision of one node performs, as written: out[0]
+// additions and subtractions, out[1] multiplications, out[2] divisions
+extern "C" int host_collide_ops(int lat, int coll, long long *out) {
+    if (lat == D2Q9) return count_ops<D2Q9>(coll, out);
+    if (lat == D3Q19) return count_ops<D3Q19>(coll, out);
+    if (lat == D3Q27) return count_ops<D3Q27>(coll, out);
     return -1;
 }
 

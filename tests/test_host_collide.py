@@ -51,6 +51,7 @@ def harness():
     P = ctypes.POINTER(ctypes.c_double)
     lib.host_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_double, P]
     lib.host_velocities.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.host_collide_ops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     return lib
 
 
@@ -91,3 +92,24 @@ def test_kernel_collision_matches_the_oracle(harness, lat, coll, fp32):
         assert worst <= 1e-6 * scale, (worst, scale)
     else:
         assert worst <= 1e-15, worst
+
+
+def _ops(harness, lat, coll):
+    out = (ctypes.c_longlong * 3)()
+    assert harness.host_collide_ops(lat, coll, out) == 0
+    return sum(out), list(out)
+
+
+def test_trimmed_collision_saves_the_operations_it_claims(harness):
+    """With tau_3 = tau_4 = 1 the kernel's trimmed SMRT skips the transforms
+    of moments that relax to zero.  Counted on the collision templates
+    themselves (additions, multiplications, divisions as written, before any
+    compiler fusion): D2Q9 210 -> 162 operations (23 % fewer), D3Q19 811 ->
+    444, D3Q27 873 -> 550 (37 % fewer).  One division per node (1 / rho)."""
+    for lat, lo in [(0, 0.2), (1, 0.4), (2, 0.35)]:
+        full, f3 = _ops(harness, lat, 1)
+        trim, t3 = _ops(harness, lat, 4)
+        assert trim < (1 - lo) * full, (lat, full, trim)
+        assert f3[2] == 1 and t3[2] == 1
+    assert (_ops(harness, 0, 1)[0], _ops(harness, 0, 4)[0]) == (210, 162)
+    assert (_ops(harness, 2, 1)[0], _ops(harness, 2, 4)[0]) == (873, 550)
