@@ -94,3 +94,21 @@ def test_reference_arm_line_carries_the_contract_keys(capsys):
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_is_reported_only_for_the_kernel_it_was_measured_on(tmp_path, monkeypatch):
+    """bench.py scales the committed ncu DRAM bytes per node to a launch, and
+    reports null once the kernel sources differ from the ones the counters
+    were taken on (their hash is stored beside the figure)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    good = tmp_path / "good.json"
+    good.write_text(json.dumps({"kernel_sources_sha": bench.kernel_sources_sha(), "dram_bytes_per_node": 60.0}))
+    stale = tmp_path / "stale.json"
+    stale.write_text(json.dumps({"kernel_sources_sha": "0" * 16, "dram_bytes_per_node": 60.0}))
+    monkeypatch.setattr(bench, "PROFILE_TRAFFIC", {"SMRT": str(good), "MRT_RAW": str(stale)})
+    assert bench.traffic_per_launch(1000, "SMRT") == 60000.0
+    assert bench.traffic_per_launch(1000, "MRT_RAW") is None
+    assert bench.traffic_per_launch(1000, "SMRT_FNEQ") is None
+
