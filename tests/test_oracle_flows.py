@@ -346,17 +346,19 @@ def _womersley_transient(y, t, A, om, nu, Lh, nmax=200):
 
 
 @pytest.mark.slow
-def test_womersley():
-    """Sec. III.B with halfway bounce-back in place of diffuse reflection.  The
-    flow is uniform in x, so a one-node-wide periodic strip is the same flow
-    as the 50-wide domain (checked for a few hundred steps below)."""
+@pytest.mark.parametrize("coll", [O.SMRT, O.SMRT_FNEQ, O.MRT_RAW])
+def test_womersley(coll):
+    """Sec. III.B with halfway bounce-back in place of diffuse reflection, for
+    the three moment collisions.  The flow is uniform in x, so a
+    one-node-wide periodic strip is the same flow as the 50-wide domain
+    (checked for a few hundred steps below)."""
     cfg = GOLD["womersley"]
     ny, T, nu, A = cfg["ny"], cfg["T"], cfg["nu"], cfg["Ap"]
     tau = 3 * nu + 0.5
     om = 2 * math.pi / T
     Lh = ny / 2
     y = np.arange(ny) + 0.5 - Lh
-    s = O.Sim(O.D2Q9, O.SMRT, (1, ny, 1), periodic=(1, 0, 1), tau=(1, 1, tau, 1, 1), g=[-A, 0])
+    s = O.Sim(O.D2Q9, coll, (1, ny, 1), periodic=(1, 0, 1), tau=(1, 1, tau, 1, 1), g=[-A, 0])
     t = 0
     worst = 0.0
     for n in range(cfg["periods"] * 16 + 15):
