@@ -179,7 +179,8 @@ def test_shear_wave_decays_at_the_shear_viscosity(lat, coll, taus):
 
 
 @pytest.mark.parametrize("coll,tau", [(O.SMRT, (1, 1, 0.6, 1, 1)), (O.BGK, (1, 1, 0.8, 1, 1)),
-                                      (O.SMRT, (1, 1, 0.9, 0.7, 1.2))])
+                                      (O.SMRT, (1, 1, 0.9, 0.7, 1.2)), (O.SMRT_FNEQ, (1, 1, 0.9, 0.7, 1.2)),
+                                      (O.MRT_RAW, (1, 1, 0.9, 0.7, 1.2))])
 def test_kolmogorov_steady_profile_second_order(coll, tau):
     """The benchmark's kind of forcing, a per-row g_x = g0 sin(ky) on a
     periodic domain: the steady laminar Kolmogorov flow is
