@@ -300,7 +300,7 @@ def test_sound_speed_is_that_of_the_isothermal_lattice(lat, coll, taus):
     assert abs(cs * math.sqrt(3) - 1) < 1e-3, cs
 
 
-@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q27])
+@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q19, O.D3Q27])
 @pytest.mark.parametrize("tau_b", [0.6, 0.8, 1.4])
 def test_sound_attenuation_follows_bulk_viscosity(lat, tau_b):
     """A standing sound wave rho = 1 + eps cos(kx) decays at
