@@ -205,6 +205,32 @@ def test_kolmogorov_steady_profile_second_order(coll, tau):
     assert 3.2 < errs[0] / errs[1] < 4.8, errs
 
 
+@pytest.mark.parametrize("lat,coll", [(O.D3Q19, O.SMRT_FNEQ), (O.D3Q19, O.MRT_RAW), (O.D3Q27, O.SMRT)])
+def test_kolmogorov_steady_profile_in_3d(lat, coll):
+    """The steady Kolmogorov profile u_x = g0 sin(ky) / (nu k^2) on the 3-D
+    lattices (a strip one node wide in x and z, periodic), at unequal
+    (tau_2, tau_3, tau_4): under 1 % at L = 32 and second order (error ratio
+    3.5-4.5 at L = 64), with no transverse velocity.  Covers the force's
+    non-equilibrium terms and the raw-moment relaxation on D3Q19 in a forced
+    flow."""
+    tau = (1, 1, 0.9, 0.7, 1.2)
+    nu = (tau[2] - 0.5) / 3
+    errs = []
+    for L in (32, 64):
+        k = 2 * math.pi / L
+        y = np.arange(L)
+        g = np.zeros((L, 3))
+        g[:, 0] = 1e-6 * np.sin(k * y)
+        s = O.Sim(lat, coll, (1, L, 1), (1, 1, 1), tau, g=g, force_kind="rows")
+        s.step(int(12 / (nu * k * k)))
+        u = s.moments()[1]
+        assert np.abs(u[1:]).max() < 1e-17
+        ua = 1e-6 * np.sin(k * y) / (nu * k * k)
+        errs.append(np.linalg.norm(u[0, 0, :, 0] - ua) / np.linalg.norm(ua))
+    assert errs[0] < 1e-2, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
 @pytest.mark.parametrize("taus", [(0.8, 0.8, 0.8), (0.8, 1.0, 1.0), (0.8, 0.6, 0.8), (1.1, 0.7, 1.1), (0.8, 0.7, 1.0)])
 def test_poiseuille_smrt_slip_closed_form(taus):
     """The SMRT wall slip of halfway bounce-back.  In steady force-driven
