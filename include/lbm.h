@@ -361,8 +361,12 @@ void lbm_unet_destroy(lbm_unet *u);
  * synchronously), so make it before any stream capture on that device.
  * All calls on a device share the array, which keeps the last call's
  * snapshot: the residual entries compare with the velocity of the previous
- * call on the same device (zero before the first one).  Calls that overlap
- * on the GPU (different streams without ordering) race on the array. */
+ * call on the same device, if that call had the same lattice, storage, nx,
+ * ny and nz.  The first call on a device, and a call whose layout differs
+ * from the previous call's, compare with zero instead (the call clears the
+ * snapshot on its stream first), so there sum |u - u_snap|^2 = sum |u|^2.
+ * Calls that overlap on the GPU (different streams without ordering) race
+ * on the array. */
 lbm_status lbm_check_noalloc(const lbm_desc *desc, const void *state_dev, double *out_dev, void *stream);
 
 #ifdef __cplusplus
