@@ -111,7 +111,8 @@ def job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
 
 
 # the sources that define the D2Q9 stream-collide kernel and its launch
-STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h", "lbm_inst_d2q9.cu")
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h", "lbm_inst_d2q9.cu", "lbm_step_vec.cuh",
+                "lbm_vec_d2q9_f32.cu")
 
 
 def kernel_sources_sha():
@@ -309,10 +310,7 @@ def run_gpu(args, ws, rank, local):
                     u0=wl.u0, torch_stream=stream, tau_bulk=args.tau_bulk)
     D, Q, _, bytes_per_node = lat.info()
     steps = max(1, args.steps)
-    C = max(1, min(args.check_every, steps))
-    # exactly `steps` steps per timed region: full check intervals, then the rest
-    chunk_sizes = [C] * (steps // C) + ([steps % C] if steps % C else [])
-    chunks = len(chunk_sizes)
+    C = max(1, args.check_every)
     warm = torch.zeros(7, dtype=torch.float64, device=f"cuda:{local}")
     # warm-up: graphs captured, clocks up; its time sizes the repeats
     wsteps = max(args.warmup, 3)
@@ -325,21 +323,24 @@ def run_gpu(args, ws, rank, local):
         w1.record(stream)
     torch.cuda.synchronize()
     est_ms = w0.elapsed_time(w1) / wsteps * steps
-    # the timed region (exactly `steps` steps) is repeated until about
+    # The timed region (exactly `steps` steps) is repeated until about
     # --min-seconds of device work has run, so that the clock sampler sees the
-    # GPU under load; the line reports the median region
+    # GPU under load.  The FP64 check keeps the workload's cadence (every
+    # check_every steps counted over all regions), so the regions together
+    # are a run of repeats * steps steps with its checks.
     repeats = int(max(1, min(args.max_repeats, math.ceil(args.min_seconds * 1e3 / max(est_ms, 1e-3)))))
     if args.repeats:
         repeats = args.repeats
-    checks = torch.zeros((repeats, chunks, 7), dtype=torch.float64, device=f"cuda:{local}")
-    ev_s = [[torch.cuda.Event(enable_timing=True) for _ in range(chunks)] for _ in range(repeats)]
-    ev_e = [[torch.cuda.Event(enable_timing=True) for _ in range(chunks)] for _ in range(repeats)]
+    n_checks = repeats * steps // C
+    checks = torch.zeros((max(1, n_checks), 7), dtype=torch.float64, device=f"cuda:{local}")
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(repeats)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(repeats)]
+    chunk_ev = []          # (start, end, steps) of every run of step launches
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.4)
-    region_ms = []
+    done = 0               # steps since the timed work began
+    k = 0
     for r in range(repeats):
         if dist:
             dist.barrier()
@@ -348,35 +349,43 @@ def run_gpu(args, ws, rank, local):
             sampler.mark(0)
         with torch.cuda.stream(stream):
             e0[r].record(stream)
-            for c, cs in enumerate(chunk_sizes):
-                ev_s[r][c].record(stream)
-                lat.step(cs)
-                ev_e[r][c].record(stream)
-                lat.check_device(checks[r, c].data_ptr())
+            left = steps
+            while left > 0:
+                n_run = min(left, C - done % C)
+                es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                es.record(stream)
+                lat.step(n_run)
+                ee.record(stream)
+                chunk_ev.append((es, ee, n_run))
+                done += n_run
+                left -= n_run
+                if done % C == 0:
+                    lat.check_device(checks[k].data_ptr())
+                    k += 1
             e1[r].record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
     sampler.mark(1)
     sampler.stop()
-    region_ms = [e0[r].elapsed_time(e1[r]) for r in range(repeats)]
-    region_ms = [reduce_max(t, dist, f"cuda:{local}") for t in region_ms]
-    total_ms = statistics.median(region_ms)
-    kern_ms = sum(ev_s[r][c].elapsed_time(ev_e[r][c]) for r in range(repeats) for c in range(chunks)) / (steps * repeats)
-    ck = checks.cpu().numpy().reshape(repeats * chunks, 7)
+    region_ms = [reduce_max(e0[r].elapsed_time(e1[r]), dist, f"cuda:{local}") for r in range(repeats)]
+    total_ms = sum(region_ms)
+    kern_ms = sum(es.elapsed_time(ee) for es, ee, _ in chunk_ev) / sum(n for _, _, n in chunk_ev)
+    bx, npt, layout = lat.launch()
+    ck = checks[:max(1, k)].cpu().numpy()
     finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
-    last_c = chunk_sizes[-1]
-    res = float(math.sqrt(ck[-1, 4]) / (last_c * math.sqrt(ck[-1, 5]))) if len(ck) > 1 and ck[-1, 5] > 0 else None
-    mass_drift = float(abs(ck[-1, 0] - ck[0, 0]) / ck[0, 0])
+    res = float(math.sqrt(ck[-1, 4]) / (C * math.sqrt(ck[-1, 5]))) if k > 1 and ck[-1, 5] > 0 else None
+    mass_drift = float(abs(ck[-1, 0] - ck[0, 0]) / ck[0, 0]) if k > 0 else None
     lat.close()
 
-    value = job_rate(ws, N * steps, total_ms * 1e-3) / 1e6
+    all_steps = steps * repeats
+    value = job_rate(ws, N * all_steps, total_ms * 1e-3) / 1e6
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_node * N
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(N, coll) if st == "F32" and not args.tau_bulk else None
     clocks = sampler.summary()
-    launches = steps + 2 * chunks   # step kernels, and the moments and finalize kernels per check
+    launches = all_steps + 2 * k   # step kernels, and the moments and finalize kernels per check
 
     e2e = None
     if not args.no_e2e:
@@ -388,16 +397,19 @@ def run_gpu(args, ws, rank, local):
                       args.tau_bulk)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
-            "repeats": repeats, "timing": f"median of {repeats} timed regions of exactly {steps} steps each "
-                                          f"(min {min(region_ms) / steps:.5f}, max {max(region_ms) / steps:.5f} ms per step)",
+            "warmup": args.warmup, "ms_per_step": total_ms / all_steps, "higher_is_better": True,
+            "repeats": repeats,
+            "timing": f"{repeats} timed regions of exactly {steps} steps each, each bracketed by a barrier and a "
+                      f"device synchronisation; value and ms_per_step over all of them (per region: median "
+                      f"{statistics.median(region_ms) / steps:.5f}, min {min(region_ms) / steps:.5f}, max "
+                      f"{max(region_ms) / steps:.5f} ms per step)",
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if st == "F32" else f"{st.lower()} storage, f32 arithmetic",
             "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("_smrt_f32_", f"_{coll.lower()}_{st.lower()}_") +
                                    (f"_bulk{args.tau_bulk:g}" if args.tau_bulk else ""),
                        "lattice": "D2Q9", "collision": coll, "storage": st, "tau_bulk": args.tau_bulk or None,
                        "nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)",
-                       "check_every": C, "checks_per_region": chunks,
+                       "check_every": C, "checks_timed": k,
                        "l2": (f"inputs larger than L2 (two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers)"
                               if N * Q * (4 if st == 'F32' else 2) > 129e6 else
                               f"two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers fit in L2: "
@@ -405,7 +417,10 @@ def run_gpu(args, ws, rank, local):
                        "replicas": ws},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"k_step<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st}>", "bytes_per_launch": algo_bytes,
+                         "kernel": (f"k_step_vec<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st},{npt}>" if layout
+                                    else f"k_step<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st},{npt}>"),
+                         "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided"},
+                         "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,
             "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res}}

@@ -199,16 +199,40 @@ size_t lbm_state_bytes(const lbm_handle *h);
 lbm_status lbm_get_state(lbm_handle *h, void *host, size_t bytes, int64_t *step);
 lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t step);
 
+/* Node layout of a thread in the fused stream-collide kernel (the pull of
+ * Sec. II.C with the collision in between; the two compute the same values).
+ *   LBM_LAYOUT_STRIDED: nodes_per_thread (1 or 2) nodes, block_x apart along
+ *     x; each population of each node is one load.
+ *   LBM_LAYOUT_VECTOR: nodes_per_thread consecutive nodes along x; each
+ *     population of them is one aligned vector load and store (D2Q9: up to
+ *     16 bytes), the one-node shift of the pull taken from the neighbouring
+ *     lane.  Only without an obstacle mask and with Q * plane < 2^32 (plane
+ *     as in lbm_get_state); the widths built per lattice and storage are
+ *     given by lbm_launch_widths. */
+typedef enum { LBM_LAYOUT_STRIDED = 0, LBM_LAYOUT_VECTOR = 1 } lbm_layout;
+
 /* Launch shape of the fused stream-collide kernel: threads per block along x
- * (block_x: 32, 64, 128 or 256) and nodes per thread along x (1 or 2).
- * Drops the captured step graph.  Results do not depend on the shape. */
+ * (block_x: 32, 64, 128 or 256), nodes per thread along x and their layout.
+ * Drops the captured step graphs; synchronises the handle's stream.  Results
+ * do not depend on the shape.  A new handle starts with the vector layout at
+ * the wider width for D2Q9 and the narrower one on the 3-D lattices when the
+ * layout applies, else the strided layout.  LBM_ERR_ARG for a shape not
+ * listed. */
+lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout);
+/* lbm_set_launch_layout with LBM_LAYOUT_STRIDED (nodes_per_thread 1 or 2). */
 lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread);
+/* The current launch shape (outputs nullable). */
+lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout);
+/* The two vector widths (nodes per thread; equal when only one is built) of
+ * LBM_LAYOUT_VECTOR for a lattice and storage (outputs nullable). */
+lbm_status lbm_launch_widths(int lattice, int storage, int *lo, int *hi);
 
 /* Time every supported launch shape over `trials` launches each (CUDA events
  * on the handle's stream; the kernel reads the current state and writes the
- * spare buffer, so the state does not advance), keep the fastest and return
- * it (outputs nullable) with its mean launch time in milliseconds.
- * Synchronises. */
+ * spare buffer, so the state does not advance): the strided shapes, and the
+ * vector shapes where that layout applies.  Keep the fastest and return its
+ * block_x and nodes_per_thread (outputs nullable; lbm_get_launch gives its
+ * layout) with its mean launch time in milliseconds.  Synchronises. */
 lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms);
 
 /* Information: D, Q, the step counter, and the device population buffer
@@ -330,6 +354,62 @@ enum { LBM_UNET_WGRAD_AUTO = 0, LBM_UNET_WGRAD_MMA_SYNC = 1 };
 lbm_status lbm_unet_set_wgrad(lbm_unet *u, int kind);
 const char *lbm_unet_last_error(const lbm_unet *u);
 void lbm_unet_destroy(lbm_unet *u);
+
+/* ------------------------------------------------------------------------
+ * Split domains: the domain decomposition of the stream step (Sec. II.C).
+ *
+ * The pull f_i(x, t + 1) = f_i,p(x - c_i, t) couples a node only to its
+ * neighbours one layer away, so a domain split into slabs along its
+ * outermost axis (y in 2-D, z in 3-D) needs, per time step, one exchange:
+ * each slab's first and last owned layer pull the populations that cross the
+ * cut from a halo layer holding the neighbouring slab's layer.  Those with
+ * c = +1 along the axis fill the lower halo, those with c = -1 the upper.
+ * The FP64 check is the sum of the slabs' checks (an all-reduce of the mass,
+ * the momentum and the residual terms).  The result is the same, bit for
+ * bit, as the whole domain's: every node runs the same arithmetic on the
+ * same values.
+ *
+ * Here every slab lives on the current device, in its own population
+ * buffers, and all share the stream of desc (the library's own when NULL);
+ * the exchange is one kernel over a table of layer copies.
+ */
+typedef struct lbm_split lbm_split;
+
+/* Slab layout and exchange schedule of `parts` slabs of an axis of n_all
+ * layers (host only, no device work).  Slab p owns the global layers
+ * [layers[2p], layers[2p] + layers[2p + 1]): n_all / parts each, the first
+ * n_all % parts one more.  Local layer 0 and n + 1 of a slab with n layers
+ * are its halo layers, 1 .. n its own.  copies (5 ints each: destination
+ * slab, destination local layer, source slab, source local layer,
+ * population index) lists the copies of one exchange in order; with
+ * periodic = 0 none crosses the domain's ends.  Outputs nullable;
+ * *n_copies receives the count; LBM_ERR_ARG if max_copies is too small, if
+ * parts < 1 or parts > n_all. */
+lbm_status lbm_split_schedule(int lattice, int n_all, int parts, int periodic, int *layers, int *copies,
+                              int max_copies, int *n_copies);
+/* Create the whole domain of desc (as lbm_create; its initial state) and
+ * `parts` slabs of it along the outermost axis.  Device memory: the whole
+ * domain's buffers plus every slab's (n + 2 layers each). */
+lbm_status lbm_split_create(const lbm_desc *desc, int parts, lbm_split **out);
+/* nsteps time steps: every slab's stream-collide step, then the exchange.
+ * Asynchronous on the split's stream. */
+lbm_status lbm_split_step(lbm_split *s, int64_t nsteps);
+/* The FP64 check of lbm_check_device summed over the slabs in slab order
+ * (each slab keeps its own velocity snapshot), 7 device doubles at out_dev.
+ * Asynchronous. */
+lbm_status lbm_split_check_device(lbm_split *s, double *out_dev);
+/* The slabs' layers assembled into the whole domain, then lbm_moments,
+ * lbm_get_state (layout of lbm_get_state; *step nullable) or
+ * lbm_get_populations on it.  Synchronise. */
+lbm_status lbm_split_moments(lbm_split *s, double *rho, double *u, double *totals);
+size_t lbm_split_state_bytes(const lbm_split *s);
+lbm_status lbm_split_get_state(lbm_split *s, void *host, size_t bytes, int64_t *step);
+lbm_status lbm_split_get_populations(lbm_split *s, double *f);
+/* lbm_set_launch_layout on every slab. */
+lbm_status lbm_split_set_launch_layout(lbm_split *s, int block_x, int nodes_per_thread, int layout);
+/* Last error message of s (of the calling thread when s is NULL). */
+const char *lbm_split_last_error(const lbm_split *s);
+void lbm_split_destroy(lbm_split *s);
 
 /* lbm_check_noalloc -- the FP64 check of lbm_check_device for callers that
  * cannot allocate device memory.  The paper has no counterpart: it is a

@@ -15,12 +15,14 @@ LBM_NOT_CONVERGED = 1
 LBM_BGK, LBM_SMRT, LBM_SMRT_FNEQ, LBM_MRT_RAW = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT = 0, 1, 2, 3
 LBM_G_NONE, LBM_G_UNIFORM, LBM_G_ROWS, LBM_G_FIELD = 0, 1, 2, 3
+LBM_LAYOUT_STRIDED, LBM_LAYOUT_VECTOR = 0, 1
 
 _NAMES = {
     "lattice": {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2},
     "collision": {"BGK": 0, "SMRT": 1, "SMRT_FNEQ": 2, "MRT_RAW": 3},
     "storage": {"F64": 0, "F32": 1, "F16": 2, "F16_SHIFT": 2, "BF16": 3, "BF16_SHIFT": 3},
     "force": {"none": 0, "uniform": 1, "rows": 2, "field": 3},
+    "layout": {"strided": 0, "vector": 1},
 }
 _DQ = {0: (2, 9), 1: (3, 19), 2: (3, 27)}
 
@@ -79,8 +81,27 @@ def library():
     L.lbm_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                            C.POINTER(C.c_size_t)]
     L.lbm_set_launch.argtypes = [H, C.c_int, C.c_int]
+    L.lbm_set_launch_layout.argtypes = [H, C.c_int, C.c_int, C.c_int]
+    L.lbm_get_launch.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_launch_widths.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_autotune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.lbm_check_noalloc.argtypes = [C.POINTER(lbm_desc), C.c_void_p, C.c_void_p, C.c_void_p]
+    S = C.c_void_p
+    ip = C.POINTER(C.c_int)
+    L.lbm_split_schedule.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, ip]
+    L.lbm_split_create.argtypes = [C.POINTER(lbm_desc), C.c_int, C.POINTER(S)]
+    L.lbm_split_step.argtypes = [S, C.c_int64]
+    L.lbm_split_check_device.argtypes = [S, C.c_void_p]
+    L.lbm_split_moments.argtypes = [S, dp, dp, dp]
+    L.lbm_split_state_bytes.argtypes = [S]
+    L.lbm_split_state_bytes.restype = C.c_size_t
+    L.lbm_split_get_state.argtypes = [S, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64)]
+    L.lbm_split_get_populations.argtypes = [S, dp]
+    L.lbm_split_set_launch_layout.argtypes = [S, C.c_int, C.c_int, C.c_int]
+    L.lbm_split_last_error.argtypes = [S]
+    L.lbm_split_last_error.restype = C.c_char_p
+    L.lbm_split_destroy.argtypes = [S]
+    L.lbm_split_destroy.restype = None
     B = C.c_void_p
     L.lbm_batch_create.argtypes = [C.POINTER(lbm_desc), C.c_int, C.POINTER(B)]
     L.lbm_batch_run_to_steady.argtypes = [B, C.c_double, C.c_int, C.c_int64, C.POINTER(C.c_int64),
@@ -105,7 +126,10 @@ def library():
     for n in ("lbm_create", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_residual",
               "lbm_check_device",
               "lbm_set_force", "lbm_set_force_schedule", "lbm_set_force_scale_schedule", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
-              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_autotune", "lbm_check_noalloc",
+              "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_set_launch_layout", "lbm_get_launch",
+              "lbm_launch_widths", "lbm_autotune", "lbm_check_noalloc", "lbm_split_schedule", "lbm_split_create",
+              "lbm_split_step", "lbm_split_check_device", "lbm_split_moments", "lbm_split_get_state",
+              "lbm_split_get_populations", "lbm_split_set_launch_layout",
               "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
               "lbm_batch_moments", "lbm_batch_get_populations", "lbm_batch_set_tiles", "lbm_batch_autotune",
               "lbm_batch_set_spin_limit", "lbm_batch_set_handoff", "lbm_batch_info"):
@@ -265,6 +289,23 @@ def lbm_set_launch(h, block_x, nodes_per_thread):
     _check(library().lbm_set_launch(h, int(block_x), int(nodes_per_thread)), h)
 
 
+def lbm_set_launch_layout(h, block_x, nodes_per_thread, layout):
+    _check(library().lbm_set_launch_layout(h, int(block_x), int(nodes_per_thread), _enum("layout", layout)), h)
+
+
+def lbm_get_launch(h):
+    bx, npt, lay = C.c_int(), C.c_int(), C.c_int()
+    _check(library().lbm_get_launch(h, C.byref(bx), C.byref(npt), C.byref(lay)), h)
+    return bx.value, npt.value, lay.value
+
+
+def lbm_launch_widths(lattice, storage):
+    lo, hi = C.c_int(), C.c_int()
+    _check(library().lbm_launch_widths(_enum("lattice", lattice), _enum("storage", storage), C.byref(lo),
+                                       C.byref(hi)))
+    return lo.value, hi.value
+
+
 def lbm_autotune(h, trials=20):
     bx, npt, ms = C.c_int(), C.c_int(), C.c_double()
     _check(library().lbm_autotune(h, int(trials), C.byref(bx), C.byref(npt), C.byref(ms)), h)
@@ -383,8 +424,13 @@ class Lattice:
     def info(self):
         return lbm_info(self.h)
 
-    def set_launch(self, block_x, nodes_per_thread):
-        lbm_set_launch(self.h, block_x, nodes_per_thread)
+    def set_launch(self, block_x, nodes_per_thread, layout=0):
+        """layout 0 / "strided" or 1 / "vector" (see lbm_set_launch_layout)."""
+        lbm_set_launch_layout(self.h, block_x, nodes_per_thread, layout)
+
+    def launch(self):
+        """(block_x, nodes_per_thread, layout) of the step kernel."""
+        return lbm_get_launch(self.h)
 
     def autotune(self, trials=20, cache=None):
         """Pick the fastest launch shape (see lbm_autotune).  With a cache path,
@@ -401,7 +447,7 @@ class Lattice:
         bx, npt, ms = lbm_autotune(self.h, trials)
         if cache:
             from . import autotune as A
-            A.store(cache, key, (bx, npt), ms)
+            A.store(cache, key, self.launch(), ms)
         return bx, npt, ms
 
     def close(self):
@@ -420,6 +466,130 @@ class Lattice:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------- split domains
+def _scheck(status, s=None):
+    if status != 0:
+        msg = library().lbm_split_last_error(s)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def lbm_split_schedule(lattice, n_all, parts, periodic):
+    """(layers [(g0, n)] per slab, copies [(dst_part, dst_layer, src_part,
+    src_layer, pop)]) of one exchange; host only."""
+    L = library()
+    lat = _enum("lattice", lattice)
+    cnt = C.c_int()
+    _scheck(L.lbm_split_schedule(lat, int(n_all), int(parts), int(bool(periodic)), None, None, 0, C.byref(cnt)))
+    lay = (C.c_int * (2 * parts))()
+    cp = (C.c_int * max(1, 5 * cnt.value))()
+    _scheck(L.lbm_split_schedule(lat, int(n_all), int(parts), int(bool(periodic)), lay, cp, cnt.value,
+                                 C.byref(cnt)))
+    layers = [(lay[2 * p], lay[2 * p + 1]) for p in range(parts)]
+    copies = [tuple(cp[5 * k:5 * k + 5]) for k in range(cnt.value)]
+    return layers, copies
+
+
+def lbm_split_create(desc, parts):
+    s = C.c_void_p()
+    _scheck(library().lbm_split_create(C.byref(desc), int(parts), C.byref(s)))
+    return s
+
+
+def lbm_split_step(s, n):
+    _scheck(library().lbm_split_step(s, int(n)), s)
+
+
+def lbm_split_check_device(s, out_ptr):
+    _scheck(library().lbm_split_check_device(s, C.c_void_p(out_ptr)), s)
+
+
+def lbm_split_moments(s, rho, u, totals):
+    _scheck(library().lbm_split_moments(s, _dptr(rho), _dptr(u), _dptr(totals)), s)
+
+
+def lbm_split_state_bytes(s):
+    return int(library().lbm_split_state_bytes(s))
+
+
+def lbm_split_get_state(s, buf):
+    step = C.c_int64()
+    _scheck(library().lbm_split_get_state(s, buf.ctypes.data_as(C.c_void_p), buf.nbytes, C.byref(step)), s)
+    return step.value
+
+
+def lbm_split_get_populations(s, f):
+    _scheck(library().lbm_split_get_populations(s, _dptr(f)), s)
+
+
+def lbm_split_set_launch_layout(s, block_x, nodes_per_thread, layout):
+    _scheck(library().lbm_split_set_launch_layout(s, int(block_x), int(nodes_per_thread),
+                                                  _enum("layout", layout)), s)
+
+
+def lbm_split_last_error(s):
+    m = library().lbm_split_last_error(s)
+    return m.decode() if m else ""
+
+
+def lbm_split_destroy(s):
+    library().lbm_split_destroy(s)
+
+
+class Split:
+    """A domain split into `parts` slabs along its outermost axis, each slab
+    in its own buffers, with the halo exchange after every step (see
+    lbm_split_create).  Arguments as Lattice."""
+
+    def __init__(self, parts, lattice, collision, shape, tau, storage="F32", periodic=(1, 1, 1), g=None,
+                 force_kind=None, solid=None, rho0=None, u0=None, tau_bulk=0.0):
+        self.lattice = _enum("lattice", lattice)
+        self.D, self.Q = _DQ[self.lattice]
+        nx, ny, nz = (list(shape) + [1, 1])[:3]
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        desc, keep = make_desc(lattice, collision, shape, tau, storage, periodic, g, force_kind, solid, rho0, u0,
+                               None, None, None, tau_bulk)
+        self.s = lbm_split_create(desc, parts)
+        del keep
+
+    def step(self, n=1):
+        lbm_split_step(self.s, n)
+
+    def check_device(self, out_ptr):
+        lbm_split_check_device(self.s, out_ptr)
+
+    def moments(self):
+        rho = np.empty(self.N)
+        u = np.empty(self.D * self.N)
+        tot = np.empty(4)
+        lbm_split_moments(self.s, rho, u, tot)
+        return rho.reshape(self.shape), u.reshape((self.D,) + self.shape), tot
+
+    def state(self):
+        buf = np.empty(lbm_split_state_bytes(self.s), np.uint8)
+        step = lbm_split_get_state(self.s, buf)
+        return buf, step
+
+    def populations(self):
+        f = np.empty(self.Q * self.N)
+        lbm_split_get_populations(self.s, f)
+        return f.reshape((self.Q,) + self.shape)
+
+    def set_launch(self, block_x, nodes_per_thread, layout=0):
+        lbm_split_set_launch_layout(self.s, block_x, nodes_per_thread, layout)
+
+    def close(self):
+        if getattr(self, "s", None) is not None:
+            lbm_split_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------------- batches

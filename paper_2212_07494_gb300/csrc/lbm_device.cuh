@@ -171,6 +171,14 @@ struct KParams {
     float om32[5];
     double omb;                    // 1 / tau of the trace (bulk) part of order 2; om[2] unless split
     float omb32;
+    // A slab of a domain split along its outermost axis (halo_ax = 1: y in
+    // 2-D, 2: z in 3-D; 0: a whole domain).  That axis then holds one halo
+    // layer at each end, which the caller fills with the neighbouring slabs'
+    // layers; the step and moments kernels work on layers 1 .. n - 2, and
+    // the pull reads the halo layers without wrapping.  hg0 is the global
+    // index of layer 1 and hgn the global extent, which place the domain's
+    // walls on that axis.
+    int halo_ax, hg0, hgn;
     // per population i, relative to a node's element index:
     long long doff[27];            // i*plane - (cx + cy*nxp + cz*nxp*ny): pull source
     long long poff[27];            // i*plane: the node's own entry
@@ -718,10 +726,36 @@ __device__ __forceinline__ void axis_src(int x, int n, int per, int *s, bool *w)
     }
 }
 
+// the same along the split axis of a slab: the source layer is always in
+// the buffer (halo layers at both ends), and a wall only where the global
+// layer leaves a domain that is not periodic on that axis
+__device__ __forceinline__ void axis_src_halo(int v, int per, int g0, int gn, int *s, bool *w) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int t = v - (k - 1);
+        const int g = g0 + t - 1;
+        const bool wall = !per && (g < 0 || g >= gn);
+        s[k] = wall ? v : t;
+        w[k] = wall;
+    }
+}
+
 __device__ __forceinline__ void node_nbr(const KParams &p, int x, int y, int z, NodeNbr &nb) {
     axis_src(x, p.nx, p.per[0], nb.xs, nb.xw);
-    axis_src(y, p.ny, p.per[1], nb.ys, nb.yw);
-    axis_src(z, p.nz, p.per[2], nb.zs, nb.zw);
+    if (p.halo_ax == 1) axis_src_halo(y, p.per[1], p.hg0, p.hgn, nb.ys, nb.yw);
+    else axis_src(y, p.ny, p.per[1], nb.ys, nb.yw);
+    if (p.halo_ax == 2) axis_src_halo(z, p.per[2], p.hg0, p.hgn, nb.zs, nb.zw);
+    else axis_src(z, p.nz, p.per[2], nb.zs, nb.zw);
+}
+
+// v is not at a face of axis ax (1: y, 2: z) of extent n: all three sources
+// along it lie inside the buffer without wrap or wall
+__device__ __forceinline__ bool inner(const KParams &p, int ax, int v, int n) {
+    if (p.halo_ax == ax) {
+        const int g = p.hg0 + v - 1;
+        return p.per[ax] || (g > 0 && g < p.hgn - 1);
+    }
+    return v > 0 && v < n - 1;
 }
 
 __device__ __forceinline__ long long node_index(const KParams &p, int x, int y, int z) {
@@ -740,7 +774,7 @@ __device__ __forceinline__ void gather(const KParams &p, const typename Store<ST
     const long long own = node_index(p, x, y, z);
 #pragma unroll
     for (int g = 0; g < Grid<D>::N; ++g) G[g] = R(0);
-    const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && (D == 2 || (z > 0 && z < p.nz - 1));
+    const bool interior = x > 0 && x < p.nx - 1 && inner(p, 1, y, p.ny) && (D == 2 || inner(p, 2, z, p.nz));
     if (interior) {
         const typename Store<ST>::T *base = f + own;
 #pragma unroll

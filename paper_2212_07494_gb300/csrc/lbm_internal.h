@@ -19,8 +19,44 @@ constexpr int kMomGridMax = 1216;   // 8 blocks per SM on 152 SMs: one wave
 
 struct StepCfg {
     int bdx;  // threads per block along x
-    int npt;  // nodes per thread (strided by bdx)
+    int npt;  // nodes per thread: strided by bdx (vec = 0), or consecutive (vec = 1)
+    int vec;  // 1: k_step_vec, each population of a thread's npt nodes moved as one vector
 };
+
+// vector widths (nodes per thread) k_step_vec is built for, per lattice and
+// storage: D2Q9 moves 16 bytes per population and thread at the upper width;
+// the 3-D lattices, with 19 or 27 populations in registers, 4 or 8 bytes
+__host__ __device__ constexpr int vec_width_lo(int L, int ST) {
+    return L == D2Q9 ? (ST == ST_F64 ? 1 : (ST == ST_F32 ? 2 : 4)) : (ST == ST_F64 || ST == ST_F32 ? 1 : 2);
+}
+__host__ __device__ constexpr int vec_width_hi(int L, int ST) {
+    return L == D2Q9 ? (ST == ST_F64 ? 2 : (ST == ST_F32 ? 4 : 8)) : (ST == ST_F64 ? 1 : (ST == ST_F32 ? 2 : 4));
+}
+
+// k_step_vec launcher of one lattice and storage (collision and width from
+// the arguments); cudaErrorInvalidValue for a width it is not built for
+typedef cudaError_t (*StepVecFn)(int coll, StepCfg cfg, const KParams &p, const void *fin, void *fout,
+                                 cudaStream_t s);
+cudaError_t step_vec_d2q9_f64(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d2q9_f32(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d2q9_f16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d2q9_bf16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q19_f64(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q19_f32(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q19_f16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q19_bf16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q27_f64(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q27_f32(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q27_f16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+cudaError_t step_vec_d3q27_bf16(int, StepCfg, const KParams &, const void *, void *, cudaStream_t);
+
+inline StepVecFn step_vec_fn(int lattice, int storage) {
+    static const StepVecFn t[3][4] = {
+        {step_vec_d2q9_f64, step_vec_d2q9_f32, step_vec_d2q9_f16, step_vec_d2q9_bf16},
+        {step_vec_d3q19_f64, step_vec_d3q19_f32, step_vec_d3q19_f16, step_vec_d3q19_bf16},
+        {step_vec_d3q27_f64, step_vec_d3q27_f32, step_vec_d3q27_f16, step_vec_d3q27_bf16}};
+    return t[lattice][storage];
+}
 
 struct Launchers {
     cudaError_t (*step)(int coll, int st, bool mask, StepCfg cfg, const KParams &p, const void *fin,
@@ -49,7 +85,8 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
 void set_thread_error(const char *msg);
 
 inline int moments_grid(const KParams &p, int resident) {
-    const long long items = (long long)((p.nx + kMomBlock * kMomNpt - 1) / (kMomBlock * kMomNpt)) * p.ny * p.nz;
+    const long long items = (long long)((p.nx + kMomBlock * kMomNpt - 1) / (kMomBlock * kMomNpt)) *
+                            (p.ny - (p.halo_ax == 1 ? 2 : 0)) * (p.nz - (p.halo_ax == 2 ? 2 : 0));
     long long g = items < kMomGridMax ? items : kMomGridMax;
     if (resident > 0 && g > resident) g = resident;
     return (int)g;
@@ -59,6 +96,11 @@ inline int moments_grid(const KParams &p, int resident) {
 // from per-block partials in a fixed order
 inline dim3 node_grid(const KParams &p, int bdx, int npt) {
     return dim3((unsigned)((p.nx + bdx * npt - 1) / (bdx * npt)), (unsigned)p.ny, (unsigned)p.nz);
+}
+// the step kernels' grid: the layers they update (a slab's halo layers excluded)
+inline dim3 step_grid(const KParams &p, int bdx, int npt) {
+    return dim3((unsigned)((p.nx + bdx * npt - 1) / (bdx * npt)), (unsigned)(p.ny - (p.halo_ax == 1 ? 2 : 0)),
+                (unsigned)(p.nz - (p.halo_ax == 2 ? 2 : 0)));
 }
 
 }  // namespace lbm

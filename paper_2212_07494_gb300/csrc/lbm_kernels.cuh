@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
                                               typename Store<ST>::T *__restrict__ fout) {
     typedef typename Store<ST>::R R;
     constexpr int NG = Grid<Lat<L>::D>::N;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y + (p.halo_ax == 1), z = blockIdx.z + (p.halo_ax == 2);
     const int x0 = blockIdx.x * blockDim.x * NPT + threadIdx.x;
     R G[NPT][NG];
     bool act[NPT];
@@ -116,7 +116,10 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
     // work items (row segment, row) walked with 32-bit counters: a row is
     // (y, z), at most 65535^2 of them, and segments per row are few
     const int segs = (p.nx + SEG - 1) / SEG;
-    const unsigned rows = (unsigned)p.ny * (unsigned)p.nz;
+    // a slab's halo layers are not its nodes
+    const int ylo = p.halo_ax == 1 ? 1 : 0, zlo = p.halo_ax == 2 ? 1 : 0;
+    const unsigned nyc = (unsigned)(p.ny - 2 * ylo);
+    const unsigned rows = nyc * (unsigned)(p.nz - 2 * zlo);
     const long long N = (long long)p.nx * p.ny * p.nz;
     Acc<R> a_drho, a_j[3], a_dd, a_uu;
     int fluid = 0, nonfinite = 0;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const KParams p, const ty
             ++row;
             if (row >= rows) break;
         }
-        const int y = (int)(row % (unsigned)p.ny), z = (int)(row / (unsigned)p.ny);
+        const int y = ylo + (int)(row % nyc), z = zlo + (int)(row / nyc);
         R G[kMomNpt][NG];
         bool on[kMomNpt], fl[kMomNpt];
         R up[kMomNpt][3];
@@ -316,7 +319,7 @@ template <int L> struct Dispatch {
     template <int COLL, int ST, bool MASK, int NPT>
     static cudaError_t step_t(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
         typedef typename Store<ST>::T T;
-        k_step<L, COLL, ST, MASK, NPT><<<node_grid(p, cfg.bdx, NPT), cfg.bdx, 0, s>>>(
+        k_step<L, COLL, ST, MASK, NPT><<<step_grid(p, cfg.bdx, NPT), cfg.bdx, 0, s>>>(
             p, (const T *)fin, (T *)fout);
         return cudaGetLastError();
     }

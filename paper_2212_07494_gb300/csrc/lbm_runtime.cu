@@ -100,7 +100,7 @@ struct lbm_handle {
     int force_kind = 0;
     bool mask = false;
     KParams kp{};
-    StepCfg cfg{128, 1};
+    StepCfg cfg{128, 1, 0};
     size_t state_bytes = 0;   // one population buffer
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;              // buffer holding the state
@@ -223,12 +223,28 @@ lbm_status sched_apply(lbm_handle *h, int off) {
     return LBM_OK;
 }
 
+// k_step_vec takes 32-bit element offsets and no obstacle mask
+bool vec_ok(const lbm_handle *h) { return !h->mask && (long long)h->Q * h->kp.plane < (1LL << 32); }
+
+// one step from fin to fout with launch shape c
+cudaError_t launch_step(lbm_handle *h, StepCfg c, const void *fin, void *fout) {
+    if (c.vec) return step_vec_fn(h->lattice, h->storage)(h->collision, c, h->kp, fin, fout, h->stream);
+    return launchers_for(h->lattice).step(h->collision, h->storage, h->mask, c, h->kp, fin, fout, h->stream);
+}
+
+// launch shape check: strided 1 or 2 nodes, or a vector width built for
+// this lattice and storage
+bool shape_ok(const lbm_handle *h, StepCfg c) {
+    if (!(c.bdx == 32 || c.bdx == 64 || c.bdx == 128 || c.bdx == 256)) return false;
+    if (!c.vec) return c.npt == 1 || c.npt == 2;
+    if (!vec_ok(h)) return false;
+    return c.npt == vec_width_lo(h->lattice, h->storage) || c.npt == vec_width_hi(h->lattice, h->storage);
+}
+
 lbm_status launch_steps(lbm_handle *h, int64_t n) {
-    const Launchers &L = launchers_for(h->lattice);
     int since = 0;   // with a force schedule: steps since the counter last advanced (< 64)
     for (int64_t s = 0; s < n; ++s) {
-        cudaError_t e = L.step(h->collision, h->storage, h->mask, h->cfg, h->kp, h->buf[h->cur],
-                               h->buf[1 - h->cur], h->stream);
+        cudaError_t e = launch_step(h, h->cfg, h->buf[h->cur], h->buf[1 - h->cur]);
         if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
         h->cur = 1 - h->cur;
         if (h->gs_dev) {
@@ -406,6 +422,26 @@ lbm_status handle_export_state(lbm_handle *h, void *state_dev) {
 
 cudaStream_t handle_stream(const lbm_handle *h) { return h->stream; }
 
+// Library-internal entry points of split domains (lbm_split.cu): a handle
+// created for one slab of a domain split along its outermost axis becomes a
+// slab (halo layers at both ends of that axis, see KParams), and the split
+// reaches its two population buffers and which of them holds the state.
+lbm_status handle_make_slab(lbm_handle *h, int ax, int g0, int gn) {
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->kp.halo_ax = ax;
+    h->kp.hg0 = g0;
+    h->kp.hgn = gn;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+void handle_buffers(const lbm_handle *h, void **b0, void **b1, int *cur, size_t *bytes) {
+    *b0 = h->buf[0];
+    *b1 = h->buf[1];
+    *cur = h->cur;
+    *bytes = h->state_bytes;
+}
+
 }  // namespace lbm
 
 extern "C" {
@@ -498,10 +534,19 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
     else fill_offsets<D3Q27>(kp);
 
-    // launch shape: 3-D and wide rows use two nodes per thread
+    // launch shape: without an obstacle mask the vector kernel (D2Q9 at its
+    // 16-byte width, the 3-D lattices at the narrower one); with a mask the
+    // strided kernel, wide rows with two nodes per thread
     h->cfg.bdx = 128;
     h->cfg.npt = (d->nx >= 512) ? 2 : 1;
+    h->cfg.vec = 0;
     if (d->nx <= 64) h->cfg.bdx = 64;
+    if (!h->mask && (long long)Q * plane < (1LL << 32)) {
+        h->cfg.vec = 1;
+        h->cfg.npt = D == 2 ? vec_width_hi(d->lattice, d->storage) : vec_width_lo(d->lattice, d->storage);
+        if ((long long)d->nx < 128LL * h->cfg.npt) h->cfg.bdx = 64;
+        if ((long long)d->nx < 64LL * h->cfg.npt) h->cfg.bdx = 32;
+    }
     h->graph_steps = 64;
 
     lbm_status st;
@@ -801,27 +846,57 @@ lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t 
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread) {
+lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-    if (!(block_x == 32 || block_x == 64 || block_x == 128 || block_x == 256))
-        return fail(h, LBM_ERR_ARG, "block_x must be 32, 64, 128 or 256");
-    if (nodes_per_thread != 1 && nodes_per_thread != 2) return fail(h, LBM_ERR_ARG, "nodes_per_thread must be 1 or 2");
+    if (layout != LBM_LAYOUT_STRIDED && layout != LBM_LAYOUT_VECTOR) return fail(h, LBM_ERR_ARG, "bad layout");
+    const StepCfg c{block_x, nodes_per_thread, layout == LBM_LAYOUT_VECTOR ? 1 : 0};
+    if (!shape_ok(h, c)) {
+        if (layout == LBM_LAYOUT_VECTOR && !vec_ok(h))
+            return fail(h, LBM_ERR_ARG, "the vector layout takes no obstacle mask and Q * plane < 2^32");
+        return fail(h, LBM_ERR_ARG,
+                    layout == LBM_LAYOUT_VECTOR
+                        ? "block_x must be 32, 64, 128 or 256 and nodes_per_thread a vector width built for this "
+                          "lattice and storage (lbm_launch_widths)"
+                        : "block_x must be 32, 64, 128 or 256 and nodes_per_thread 1 or 2");
+    }
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->cfg.bdx = block_x;
-    h->cfg.npt = nodes_per_thread;
-    for (cudaGraphExec_t &ge : h->graph)
-        if (ge) {
-            cudaGraphExecDestroy(ge);
-            ge = nullptr;
-        }
+    h->cfg = c;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread) {
+    return lbm_set_launch_layout(h, block_x, nodes_per_thread, LBM_LAYOUT_STRIDED);
+}
+
+lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (block_x) *block_x = h->cfg.bdx;
+    if (nodes_per_thread) *nodes_per_thread = h->cfg.npt;
+    if (layout) *layout = h->cfg.vec ? LBM_LAYOUT_VECTOR : LBM_LAYOUT_STRIDED;
+    return LBM_OK;
+}
+
+lbm_status lbm_launch_widths(int lattice, int storage, int *lo, int *hi) {
+    if (lattice < LBM_D2Q9 || lattice > LBM_D3Q27 || storage < LBM_F64 || storage > LBM_BF16_SHIFT)
+        return fail(nullptr, LBM_ERR_ARG, "bad lattice or storage");
+    if (lo) *lo = vec_width_lo(lattice, storage);
+    if (hi) *hi = vec_width_hi(lattice, storage);
     return LBM_OK;
 }
 
 lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (trials < 1) return fail(h, LBM_ERR_ARG, "trials must be >= 1");
-    const Launchers &L = launchers_for(h->lattice);
-    static const int shapes[][2] = {{32, 1}, {64, 1}, {64, 2}, {128, 1}, {128, 2}, {256, 1}, {256, 2}};
+    // strided shapes, then (without a mask) the vector widths
+    std::vector<StepCfg> shapes = {{32, 1, 0}, {64, 1, 0}, {64, 2, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {256, 2, 0}};
+    if (vec_ok(h)) {
+        const int wl = vec_width_lo(h->lattice, h->storage), wh = vec_width_hi(h->lattice, h->storage);
+        for (int bx : {64, 128, 256}) {
+            shapes.push_back({bx, wl, 1});
+            if (wh != wl) shapes.push_back({bx, wh, 1});
+        }
+    }
     cudaEvent_t e0, e1;
     LBM_CUDA(h, cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
@@ -831,14 +906,12 @@ lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_
     }
     double best = 1e300;
     StepCfg best_cfg = h->cfg;
-    for (const auto &sh : shapes) {
-        StepCfg c{sh[0], sh[1]};
+    for (const StepCfg &c : shapes) {
         // one untimed launch, then the timed ones; all read the state and
         // write the spare buffer
-        e = L.step(h->collision, h->storage, h->mask, c, h->kp, h->buf[h->cur], h->buf[1 - h->cur], h->stream);
+        e = launch_step(h, c, h->buf[h->cur], h->buf[1 - h->cur]);
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        for (int t = 0; t < trials && e == cudaSuccess; ++t)
-            e = L.step(h->collision, h->storage, h->mask, c, h->kp, h->buf[h->cur], h->buf[1 - h->cur], h->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) e = launch_step(h, c, h->buf[h->cur], h->buf[1 - h->cur]);
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float t_ms = 0.f;
@@ -853,7 +926,8 @@ lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
-    lbm_status st = lbm_set_launch(h, best_cfg.bdx, best_cfg.npt);
+    lbm_status st = lbm_set_launch_layout(h, best_cfg.bdx, best_cfg.npt,
+                                          best_cfg.vec ? LBM_LAYOUT_VECTOR : LBM_LAYOUT_STRIDED);
     if (st != LBM_OK) return st;
     if (block_x) *block_x = best_cfg.bdx;
     if (nodes_per_thread) *nodes_per_thread = best_cfg.npt;

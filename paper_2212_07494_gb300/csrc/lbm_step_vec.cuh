@@ -1,0 +1,295 @@
+// lbm_step_vec.cuh -- the fused pull-stream + collide + store kernel with
+// vector loads: each thread takes V consecutive nodes of a row and moves each
+// population of them as one aligned vector of V storage elements (16 bytes
+// for D2Q9 in every storage type, 4 or 8 bytes on the 3-D lattices).
+//
+// The pull f_i(x) <- f_i,p(x - c_i) reads, for the V nodes of a thread, the
+// elements x0 - cx .. x0 + V - 1 - cx of population i's row y - cy (z - cz).
+// For cx = 0 that is the thread's own aligned vector of the source row; for
+// cx = +1 it is that vector shifted by one element, whose first element is
+// the last element of the neighbouring lane's vector (one warp shuffle), and
+// for cx = -1 the last element is the next lane's first.  Only the first and
+// last lane of a warp load that edge element themselves.  Decoding picks the
+// element out of its 32-bit word (the 2-byte types hold two per word), so
+// the shift costs no extra instruction per node.
+//
+// Rows are resolved once per block: a source row across a periodic face
+// wraps; a row next to a wall takes the per-node path (gather of
+// lbm_device.cuh with halfway bounce-back), as do the threads whose nodes
+// touch the row's ends (x = 0 or x = nx - 1, where the pull wraps or
+// bounces back).  Obstacle masks use the strided kernel k_step.
+//
+// Element offsets are 32-bit: the host launches this kernel only when
+// Q * plane < 2^32.
+#pragma once
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int ST> struct Bits;
+template <> struct Bits<ST_F64> { typedef unsigned long long E; };
+template <> struct Bits<ST_F32> { typedef unsigned int E; };
+template <> struct Bits<ST_F16> { typedef unsigned int E; };    // element in the low 16 bits
+template <> struct Bits<ST_BF16> { typedef unsigned int E; };   // element in the low 16 bits
+
+// storage element bits -> arithmetic type
+template <int ST> __device__ __forceinline__ typename Store<ST>::R dec(typename Bits<ST>::E e);
+template <> __device__ __forceinline__ double dec<ST_F64>(unsigned long long e) { return __longlong_as_double((long long)e); }
+template <> __device__ __forceinline__ float dec<ST_F32>(unsigned int e) { return __uint_as_float(e); }
+template <> __device__ __forceinline__ float dec<ST_F16>(unsigned int e) {
+    return __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+}
+template <> __device__ __forceinline__ float dec<ST_BF16>(unsigned int e) { return __uint_as_float(e << 16); }
+
+// one vector of V elements as NW 32-bit words
+template <int ST, int V> struct Vec {
+    typedef typename Store<ST>::T T;
+    typedef typename Store<ST>::R R;
+    typedef typename Bits<ST>::E E;
+    static constexpr int BYTES = V * (int)sizeof(T);
+    static constexpr int NW = BYTES / 4;
+    static_assert(BYTES % 4 == 0 && BYTES >= 4 && BYTES <= 32, "vector of 4 to 32 bytes");
+
+    // element e (0 <= e < V) of the words
+    __device__ __forceinline__ static E elem(const unsigned (&w)[NW], int e) {
+        if constexpr (sizeof(T) == 2) return (e & 1) ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xffffu);
+        else if constexpr (sizeof(T) == 4) return w[e];
+        else return (unsigned long long)w[2 * e] | ((unsigned long long)w[2 * e + 1] << 32);
+    }
+    // BF16 decodes straight from either half of a word
+    __device__ __forceinline__ static R delem(const unsigned (&w)[NW], int e) {
+        if constexpr (ST == ST_BF16) return __uint_as_float((e & 1) ? (w[e >> 1] & 0xffff0000u) : (w[e >> 1] << 16));
+        else return dec<ST>(elem(w, e));
+    }
+    __device__ __forceinline__ static void load(const T *p, unsigned (&w)[NW]) {
+        if constexpr (NW >= 4) {
+#pragma unroll
+            for (int k = 0; k < NW / 4; ++k) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + k);
+                w[4 * k] = v.x;
+                w[4 * k + 1] = v.y;
+                w[4 * k + 2] = v.z;
+                w[4 * k + 3] = v.w;
+            }
+        } else if constexpr (NW == 2) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+            w[0] = v.x;
+            w[1] = v.y;
+        } else {
+            w[0] = __ldg(reinterpret_cast<const unsigned *>(p));
+        }
+    }
+    __device__ __forceinline__ static void store(T *p, const unsigned (&w)[NW]) {
+        if constexpr (NW >= 4) {
+#pragma unroll
+            for (int k = 0; k < NW / 4; ++k)
+                reinterpret_cast<uint4 *>(p)[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        } else if constexpr (NW == 2) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+        } else {
+            *reinterpret_cast<unsigned *>(p) = w[0];
+        }
+    }
+    // one element loaded on its own (the lane at a warp's edge)
+    __device__ __forceinline__ static E load1(const T *p) {
+        if constexpr (sizeof(T) == 2) return (unsigned)__ldg(reinterpret_cast<const unsigned short *>(p));
+        else if constexpr (sizeof(T) == 4) return __ldg(reinterpret_cast<const unsigned *>(p));
+        else return __ldg(reinterpret_cast<const unsigned long long *>(p));
+    }
+    // the last element of the previous lane, the first of the next lane
+    __device__ __forceinline__ static E from_prev_lane(const unsigned (&w)[NW]) {
+        if constexpr (sizeof(T) == 2) return __shfl_up_sync(0xffffffffu, w[NW - 1], 1) >> 16;
+        else if constexpr (sizeof(T) == 4) return __shfl_up_sync(0xffffffffu, w[NW - 1], 1);
+        else
+            return (unsigned long long)__shfl_up_sync(0xffffffffu, w[NW - 2], 1) |
+                   ((unsigned long long)__shfl_up_sync(0xffffffffu, w[NW - 1], 1) << 32);
+    }
+    __device__ __forceinline__ static E from_next_lane(const unsigned (&w)[NW]) {
+        if constexpr (sizeof(T) == 2) return __shfl_down_sync(0xffffffffu, w[0], 1) & 0xffffu;
+        else if constexpr (sizeof(T) == 4) return __shfl_down_sync(0xffffffffu, w[0], 1);
+        else
+            return (unsigned long long)__shfl_down_sync(0xffffffffu, w[0], 1) |
+                   ((unsigned long long)__shfl_down_sync(0xffffffffu, w[1], 1) << 32);
+    }
+    // put the result of node k into the output words; the 2-byte types pack
+    // the results of nodes k - 1 and k (round to nearest even) at odd k
+    __device__ __forceinline__ static void put(unsigned (&o)[NW], int k, R v, R &held) {
+        if constexpr (ST == ST_F16) {
+            if (k & 1) {
+                const __half2 h = __floats2half2_rn(held, v);
+                o[k >> 1] = *reinterpret_cast<const unsigned *>(&h);
+            } else {
+                held = v;
+            }
+        } else if constexpr (ST == ST_BF16) {
+            if (k & 1) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(held, v);
+                o[k >> 1] = *reinterpret_cast<const unsigned *>(&h);
+            } else {
+                held = v;
+            }
+        } else if constexpr (ST == ST_F32) {
+            o[k] = __float_as_uint(v);
+        } else {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            o[2 * k] = (unsigned)b;
+            o[2 * k + 1] = (unsigned)(b >> 32);
+        }
+    }
+};
+
+template <int L, int COLL, typename R>
+__device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
+    if constexpr (COLL == SMRT) collide_smrt<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<L>(G, gx, gy, gz, om2);
+    else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<L>(G, gx, gy, gz, om2, om3, om4);
+    else collide_bgk<L>(G, gx, gy, gz, om2);
+}
+
+// source row index along one axis for c = -1, 0, +1 (entry c + 1): the
+// coordinate minus c, wrapped on a periodic axis; false if it lies beyond a
+// wall
+__device__ __forceinline__ bool row_src(int v, int n, int per, int (&s)[3]) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int t = v - (k - 1);
+        if (t < 0) { if (per) t += n; else { ok = false; t = 0; } }
+        else if (t >= n) { if (per) t -= n; else { ok = false; t = n - 1; } }
+        s[k] = t;
+    }
+    return ok;
+}
+
+// the same along the split axis of a slab (axis_src_halo): the source layer
+// is in the buffer unless it lies beyond a wall of the whole domain
+__device__ __forceinline__ bool row_src_halo(const KParams &p, int ax, int v, int (&s)[3]) {
+    int t[3];
+    bool w[3];
+    axis_src_halo(v, p.per[ax], p.hg0, p.hgn, t, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s[k] = t[k];
+    return !(w[0] || w[1] || w[2]);
+}
+
+template <int L, int COLL, int ST, int V>
+__global__ void __launch_bounds__(256) k_step_vec(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+                                                  typename Store<ST>::T *__restrict__ fout) {
+    typedef Vec<ST, V> VT;
+    typedef typename Store<ST>::R R;
+    typedef typename Bits<ST>::E E;
+    constexpr int D = Lat<L>::D, Q = Lat<L>::Q, NG = Grid<D>::N, NW = VT::NW;
+    const int y = blockIdx.y + (p.halo_ax == 1), z = blockIdx.z + (p.halo_ax == 2);
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4), omb = omega_bulk<R>(p);
+    const bool per_node_force = p.force_kind == G_FIELD;
+    R gx, gy, gz;
+    if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
+
+    int ys[3], zs[3] = {0, 0, 0};
+    bool row_ok = p.halo_ax == 1 ? row_src_halo(p, 1, y, ys) : row_src(y, p.ny, p.per[1], ys);
+    if (D == 3) row_ok = (p.halo_ax == 2 ? row_src_halo(p, 2, z, zs) : row_src(z, p.nz, p.per[2], zs)) && row_ok;
+    // fast: every source of the thread's V nodes is in this row band's
+    // interior or wraps across a periodic face of y or z
+    const bool fast = row_ok && x0 >= 1 && x0 + V <= p.nx - 1;
+
+    if (row_ok) {
+        // the whole block is one row band: every lane takes part in the loads
+        // and shuffles; threads past the row's end load nothing
+        const bool on = x0 < p.nx;
+        const int lane = threadIdx.x & 31;
+        unsigned w[Q][NW];
+        E edge[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = Lat<L>::cx(i), cy = Lat<L>::cy(i), cz = Lat<L>::cz(i);
+            const unsigned src = (unsigned)i * (unsigned)p.plane +
+                                 ((unsigned)(D == 3 ? zs[cz + 1] : 0) * (unsigned)p.ny + (unsigned)ys[cy + 1]) *
+                                     (unsigned)p.nxp + (unsigned)x0;
+            if (on) VT::load(fin + src, w[i]);
+            else
+#pragma unroll
+                for (int k = 0; k < NW; ++k) w[i][k] = 0u;
+            if (cx == 1) {
+                edge[i] = VT::from_prev_lane(w[i]);
+                if (lane == 0 && fast) edge[i] = VT::load1(fin + (src - 1u));
+            } else if (cx == -1) {
+                edge[i] = VT::from_next_lane(w[i]);
+                if (lane == 31 && fast) edge[i] = VT::load1(fin + (src + (unsigned)V));
+            } else {
+                edge[i] = 0;
+            }
+        }
+        if (fast) {
+            const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.nxp + (unsigned)x0;
+            unsigned o[Q][NW];
+            R held[Q];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                R G[NG];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) G[g] = R(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int e = k - Lat<L>::cx(i);   // element of the source vector
+                    G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e);
+                }
+                if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
+                collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) VT::store(fout + ((unsigned)i * (unsigned)p.plane + own), o[i]);
+            return;
+        }
+    }
+    // the per-node path: rows next to a wall, and the row ends
+    if (x0 >= p.nx) return;
+#pragma unroll 1
+    for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        if (x >= p.nx) break;
+        R G[NG];
+        gather<L, ST, false>(p, fin, x, y, z, G);
+        const long long own = node_index(p, x, y, z);
+        if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
+        collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+        typename Store<ST>::T *dst = fout + own;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<ST>::st(dst + p.poff[i], G[gpos<L>(i)]);
+    }
+}
+
+// host launcher of one (lattice, storage) pair: the collision and vector
+// width are template arguments, the supported widths listed by vec_widths
+template <int L, int ST> struct VecDispatch {
+    template <int COLL, int V>
+    static cudaError_t go(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        typedef typename Store<ST>::T T;
+        k_step_vec<L, COLL, ST, V><<<step_grid(p, cfg.bdx, V), cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout);
+        return cudaGetLastError();
+    }
+    template <int COLL>
+    static cudaError_t by_width(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        constexpr int W0 = vec_width_lo(L, ST), W1 = vec_width_hi(L, ST);
+        if (cfg.npt == W0) return go<COLL, W0>(cfg, p, fin, fout, s);
+        if constexpr (W1 != W0)
+            if (cfg.npt == W1) return go<COLL, W1>(cfg, p, fin, fout, s);
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t step(int coll, StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
+        if (coll == SMRT && p.om[3] == 1.0 && p.om[4] == 1.0 && p.omb == p.om[2])
+            return by_width<SMRT_TRIM>(cfg, p, fin, fout, s);
+        switch (coll) {
+        case SMRT: return by_width<SMRT>(cfg, p, fin, fout, s);
+        case SMRT_FNEQ: return by_width<SMRT_FNEQ>(cfg, p, fin, fout, s);
+        case MRT_RAW: return by_width<MRT_RAW>(cfg, p, fin, fout, s);
+        case BGK: return by_width<BGK>(cfg, p, fin, fout, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+};
+
+}  // namespace lbm

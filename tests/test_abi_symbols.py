@@ -176,3 +176,17 @@ def test_null_handles_are_rejected(lib):
     r = ctypes.c_double()
     assert lib.lbm_residual(None, 10, ctypes.byref(r)) == -1
     assert lib.lbm_set_force(None, None) == -1
+
+
+def test_vector_widths_without_a_gpu(lib):
+    """lbm_launch_widths is host-only: D2Q9 moves 16 bytes per population and
+    thread at its wider width in every storage type."""
+    import paper_2212_07494_gb300 as P
+    for st, size in (("F64", 8), ("F32", 4), ("F16", 2), ("BF16", 2)):
+        lo, hi = P.lbm_launch_widths("D2Q9", st)
+        assert hi * size == 16 and lo <= hi
+        for lat in ("D3Q19", "D3Q27"):
+            lo3, hi3 = P.lbm_launch_widths(lat, st)
+            assert 4 <= lo3 * size <= hi3 * size <= 8
+    with pytest.raises(P.LbmError):
+        P.lbm_launch_widths(5, "F32")
