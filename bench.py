@@ -60,11 +60,13 @@ def parse():
     ap.add_argument("--max-repeats", type=int, default=1000)
     ap.add_argument("--repeats", type=int, default=0, help="kolmogorov: fixed number of timed regions (0: from --min-seconds)")
     ap.add_argument("--workload", default="kolmogorov",
-                    choices=["kolmogorov", "batch", "surrogate", "precision", "unet", "womersley"],
+                    choices=["kolmogorov", "tgv", "batch", "surrogate", "precision", "unet", "womersley", "peaks"],
                     help="kolmogorov: the 4096^2 MLUPS line (default); batch: 512 channels to steady "
                          "state; surrogate: learned warm start of obstacle channels vs cold start; "
                          "precision: every storage mode on the Kolmogorov and TGV workloads vs FP64")
-    ap.add_argument("--storage", default="F32", choices=["F32", "F16", "BF16"],
+    ap.add_argument("--lattice", default="D2Q9", choices=["D2Q9", "D3Q19", "D3Q27"],
+                    help="tgv: the 3-D lattice (D2Q9 selects D3Q27)")
+    ap.add_argument("--storage", default="F32", choices=["F64", "F32", "F16", "BF16"],
                     help="kolmogorov: storage of the populations (F32 is the benchmark configuration)")
     ap.add_argument("--collision", default="SMRT", choices=["SMRT", "SMRT_FNEQ", "MRT_RAW"],
                     help="kolmogorov: SMRT (the benchmark configuration), SMRT with the force's "
@@ -289,6 +291,31 @@ def run_reference(args, ws, rank):
 
 
 # ------------------------------------------------------------------- GPU arm
+def workload_spec(args):
+    """The workload of the MLUPS line: the 4096^2 Kolmogorov flow on D2Q9
+    (configuration 2), or --workload tgv: the 256^3 Taylor-Green vortex at
+    Re 1600 plus g_x = 1e-6 on --lattice D3Q27 or D3Q19 (configuration 3)."""
+    if args.workload == "tgv":
+        lat = args.lattice if args.lattice != "D2Q9" else "D3Q27"
+        wl = W.taylor_green_3d(n=args.tgv_n, steps=args.tgv_steps, lattice=lat)
+        n = args.tgv_n
+        return wl, {"lattice": lat, "shape": (n, n, n), "N": n ** 3, "kind": "uniform",
+                    "name": f"tgv3d_{lat.lower()}_{{coll}}_{{st}}_{n}x{n}x{n}",
+                    "config": {"nx": n, "ny": n, "nz": n, "Re": 1600, "U0": 0.05, "tau": list(wl.tau),
+                               "force": "uniform g_x = 1e-6", "length": "N / 2 pi"}}
+    n = args.n
+    wl = W.kolmogorov(n=n)
+    return wl, {"lattice": "D2Q9", "shape": (n, n, 1), "N": n * n, "kind": "rows",
+                "name": "kolmogorov_d2q9_{coll}_{st}_" + f"{n}x{n}",
+                "config": {"nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)"}}
+
+
+def make_lattice(P, wl, spec, st, coll, tau_bulk=0.0, torch_stream=None, host_inputs=None):
+    g, u0, rho0 = (wl.g, wl.u0, wl.rho0) if host_inputs is None else host_inputs
+    return P.Lattice(spec["lattice"], coll, spec["shape"], wl.tau, st, (1, 1, 1), g=g, force_kind=spec["kind"],
+                     rho0=rho0, u0=u0, torch_stream=torch_stream, tau_bulk=tau_bulk)
+
+
 def run_gpu(args, ws, rank, local):
     import torch
 
@@ -299,15 +326,13 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    n = args.n
-    t_gen = time.perf_counter()
-    wl = W.kolmogorov(n=n)
     stream = torch.cuda.Stream(device=local)
-    N = n * n
     st = args.storage
     coll = args.collision
-    lat = P.Lattice("D2Q9", coll, (n, n, 1), wl.tau, st, (1, 1, 1), g=wl.g, force_kind="rows",
-                    u0=wl.u0, torch_stream=stream, tau_bulk=args.tau_bulk)
+    wl, spec = workload_spec(args)
+    n = args.n
+    N = spec["N"]
+    lat = make_lattice(P, wl, spec, st, coll, args.tau_bulk, torch_stream=stream)
     D, Q, _, bytes_per_node = lat.info()
     steps = max(1, args.steps)
     C = max(1, args.check_every)
@@ -372,6 +397,7 @@ def run_gpu(args, ws, rank, local):
     total_ms = sum(region_ms)
     kern_ms = sum(es.elapsed_time(ee) for es, ee, _ in chunk_ev) / sum(n for _, _, n in chunk_ev)
     bx, npt, layout = lat.launch()
+    u_stall = lat.force_resolution()
     ck = checks[:max(1, k)].cpu().numpy()
     finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
     res = float(math.sqrt(ck[-1, 4]) / (C * math.sqrt(ck[-1, 5]))) if k > 1 and ck[-1, 5] > 0 else None
@@ -383,7 +409,8 @@ def run_gpu(args, ws, rank, local):
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_node * N
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = traffic_per_launch(N, coll) if st == "F32" and not args.tau_bulk else None
+    traffic = (traffic_per_launch(N, coll) if st == "F32" and not args.tau_bulk and spec["lattice"] == "D2Q9"
+               else None)
     clocks = sampler.summary()
     launches = all_steps + 2 * k   # step kernels, and the moments and finalize kernels per check
 
@@ -392,10 +419,13 @@ def run_gpu(args, ws, rank, local):
         # the configuration's whole job (its full step count), through the
         # public API from host buffers: creation and the final read-back are
         # part of every real run, so they are timed, not amortised away
-        e2e_steps = max(args.kol_steps, steps)
-        e2e = run_e2e(P, torch, wl, n, e2e_steps, min(args.check_every, e2e_steps), local, ws, dist, st, coll,
+        e2e_steps = max(args.kol_steps if spec["lattice"] == "D2Q9" else args.tgv_steps, steps)
+        e2e = run_e2e(P, torch, wl, spec, e2e_steps, min(args.check_every, e2e_steps), local, ws, dist, st, coll,
                       args.tau_bulk)
 
+    L = spec["lattice"]
+    kname = "SMRT_TRIM" if coll == "SMRT" else coll
+    q_bytes = N * Q * {"F64": 8, "F32": 4}.get(st, 2)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
             "warmup": args.warmup, "ms_per_step": total_ms / all_steps, "higher_is_better": True,
             "repeats": repeats,
@@ -403,53 +433,59 @@ def run_gpu(args, ws, rank, local):
                       f"device synchronisation; value and ms_per_step over all of them (per region: median "
                       f"{statistics.median(region_ms) / steps:.5f}, min {min(region_ms) / steps:.5f}, max "
                       f"{max(region_ms) / steps:.5f} ms per step)",
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if st == "F32" else f"{st.lower()} storage, f32 arithmetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if st == "F32" else (f"{st.lower()} storage, f32 arithmetic" if st != "F64" else "f64"),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("_smrt_f32_", f"_{coll.lower()}_{st.lower()}_") +
-                                   (f"_bulk{args.tau_bulk:g}" if args.tau_bulk else ""),
-                       "lattice": "D2Q9", "collision": coll, "storage": st, "tau_bulk": args.tau_bulk or None,
-                       "nx": n, "ny": n, "tau": list(wl.tau), "force": "rows g_x = 1e-5 sin(2 pi y / n)",
-                       "check_every": C, "checks_timed": k,
-                       "l2": (f"inputs larger than L2 (two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers)"
-                              if N * Q * (4 if st == 'F32' else 2) > 129e6 else
-                              f"two {N * Q * (4 if st == 'F32' else 2) / 1e6:.0f} MB population buffers fit in L2: "
-                              "a small case for profilers, not a bench line"),
-                       "replicas": ws},
+            "config": dict({"workload": spec["name"].format(coll=coll.lower(), st=st.lower()) +
+                                        (f"_bulk{args.tau_bulk:g}" if args.tau_bulk else ""),
+                            "lattice": L, "collision": coll, "storage": st, "tau_bulk": args.tau_bulk or None},
+                           **spec["config"],
+                           **{"check_every": C, "checks_timed": k,
+                              "l2": (f"inputs larger than L2 (two {q_bytes / 1e6:.0f} MB population buffers)"
+                                     if q_bytes > 129e6 else
+                                     f"two {q_bytes / 1e6:.0f} MB population buffers fit in L2: "
+                                     "a small case for profilers, not a bench line"),
+                              "replicas": ws}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": (f"k_step_vec<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st},{npt}>" if layout
-                                    else f"k_step<D2Q9,{'SMRT_TRIM' if coll == 'SMRT' else coll},{st},{npt}>"),
+                         "kernel": (f"k_step_vec<{L},{kname},{st},{npt}>" if layout
+                                    else f"k_step<{L},{kname},{st},{npt}>"),
                          "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided"},
                          "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,
-            "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res}}
+            "check": {"finite": finite, "mass_drift": mass_drift, "residual_K": res},
+            "storage_resolution": {"u_stall": u_stall,
+                                   "what": "speed above which one step of the body force rounds away in this "
+                                           "storage (lbm_force_resolution)"}}
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds, coll)
+        line["cpu_baseline"] = (cpu_baseline(n, args.cpu_seconds, coll) if L == "D2Q9"
+                                else cpu_baseline_3d(wl, L, args.tgv_n))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32", collision="SMRT", tau_bulk=0.0):
+def run_e2e(P, torch, wl, spec, steps, C, local, ws, dist, storage="F32", collision="SMRT", tau_bulk=0.0):
     """Whole job through the public API from pinned host memory: create (H2D of
-    the initial velocity and force), run with a host-read residual every C
+    the initial fields and the force), run with a host-read residual every C
     steps, read rho and u back (D2H)."""
-    u0 = torch.from_numpy(np.ascontiguousarray(wl.u0)).pin_memory()
-    g = torch.from_numpy(np.ascontiguousarray(wl.g)).pin_memory()
-    N = n * n
+    pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    u0, g, rho0 = pin(wl.u0), pin(wl.g), pin(wl.rho0)
+    N = spec["N"]
+    D = 2 if spec["lattice"] == "D2Q9" else 3
     rho = torch.empty(N, dtype=torch.float64).pin_memory()
-    u = torch.empty(2 * N, dtype=torch.float64).pin_memory()
+    u = torch.empty(D * N, dtype=torch.float64).pin_memory()
     tot = np.empty(4)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat = P.Lattice("D2Q9", collision, (n, n, 1), wl.tau, storage, (1, 1, 1), g=g.numpy(), force_kind="rows",
-                    u0=u0.numpy(), tau_bulk=tau_bulk)
+    lat = make_lattice(P, wl, spec, storage, collision, tau_bulk,
+                       host_inputs=(g.numpy(), u0.numpy(), None if rho0 is None else rho0.numpy()))
     r = None
     for _ in range(steps // C):
         r = lat.residual(C)
@@ -457,12 +493,27 @@ def run_e2e(P, torch, wl, n, steps, C, local, ws, dist, storage="F32", collision
     dt = time.perf_counter() - t0
     lat.close()
     dt = reduce_max(dt, dist, f"cuda:{local}")
-    h2d = u0.numel() * 8 + g.numel() * 8
+    h2d = sum(a.numel() * 8 for a in (u0, g, rho0) if a is not None)
     d2h = (rho.numel() + u.numel()) * 8 + (steps // C) * 7 * 8
     return {"value": job_rate(ws, N * steps, dt) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps, "residual_last": r, "steps": steps,
-            "what": f"the whole {steps}-step job: lbm_create from host u0/g, lbm_residual every {C} steps, "
-                    "lbm_moments to host"}
+            "what": f"the whole {steps}-step job: lbm_create from host initial fields and force, lbm_residual "
+                    f"every {C} steps, lbm_moments to host"}
+
+
+def cpu_baseline_3d(wl, lattice, n, steps=3):
+    """The FP64 oracle on the host cores: `steps` steps of an n x n x 4
+    periodic slab of the Taylor-Green vortex."""
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    sl = (slice(0, 4), slice(None), slice(None))
+    orc = O.Sim(getattr(O, lattice), O.SMRT, (n, n, 4), (1, 1, 1), wl.tau, g=wl.g,
+                rho0=np.ascontiguousarray(wl.rho0[sl]), u0=np.ascontiguousarray(wl.u0[(slice(None),) + sl]))
+    t0 = time.perf_counter()
+    orc.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * 4 * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps on a {n} x {n} x 4 periodic slab of the {n}^3 vortex ({dt:.1f} s)"}
 
 
 def run_batch(args, ws, rank, local):
@@ -807,6 +858,43 @@ def run_precision(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_peaks(args, ws, rank, local):
+    """The CUDA-core FMA peaks (FP32, FP64) of this GPU with sampled clocks:
+    the ceilings of the 2-byte and FP64 step kernels (lbm_alu_peak)."""
+    import torch
+
+    import paper_2212_07494_gb300 as P
+
+    torch.cuda.set_device(local)
+    out = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    sampler.mark(0)
+    for prec, iters in (("F32", 1 << 21), ("F64", 1 << 15)):
+        runs = [P.lbm_alu_peak(prec, iters) for _ in range(5)]
+        best = max(r[0] for r in runs)
+        out[prec] = {"tflops": best, "tflops_median": statistics.median(r[0] for r in runs),
+                     "ms_per_launch": statistics.median(r[1] for r in runs), "launches": len(runs),
+                     "fmas_per_launch": 8 * iters * 256 * 8 * torch.cuda.get_device_properties(local).multi_processor_count}
+    sampler.mark(1)
+    sampler.stop()
+    clocks = sampler.summary()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    nominal32 = sms * 128 * 2 * mhz * 1e6 / 1e12
+    line = {"metric": "CUDA-core FMA peak", "value": out["F32"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": 5, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 and f64", "data": "synthetic",
+            "config": {"workload": "fma_chains", "chains_per_thread": 8, "threads": f"{sms} SMs x 8 x 256"},
+            "fp32": out["F32"], "fp64": out["F64"], "clocks": clocks, "sms": sms,
+            "fp32_nominal_at_clock": nominal32,
+            "issue_rate_warp_instr_per_s": out["F32"]["tflops"] * 1e12 / 2 / 32,
+            "what": "FP32 FMAs per second / 32 = warp instructions issued per second at one FFMA per lane"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def womersley_analytic(y, t, A, om, nu, Lh, nmax=200):
     """Sec. III.B: the periodic Womersley profile plus the start-up transient
     of the diffusion equation from rest (even no-slip modes)."""
@@ -919,6 +1007,8 @@ def main():
         run_unet(args, ws, rank, local)
     elif args.workload == "womersley":
         run_womersley(args, ws, rank, local)
+    elif args.workload == "peaks":
+        run_peaks(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
 

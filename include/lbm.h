@@ -215,9 +215,9 @@ typedef enum { LBM_LAYOUT_STRIDED = 0, LBM_LAYOUT_VECTOR = 1 } lbm_layout;
  * (block_x: 32, 64, 128 or 256), nodes per thread along x and their layout.
  * Drops the captured step graphs; synchronises the handle's stream.  Results
  * do not depend on the shape.  A new handle starts with the vector layout at
- * the wider width for D2Q9 and the narrower one on the 3-D lattices when the
- * layout applies, else the strided layout.  LBM_ERR_ARG for a shape not
- * listed. */
+ * its wider width for D2Q9 in FP16 or BF16 storage when the layout applies,
+ * else with the strided layout (the faster ones on GB300).  LBM_ERR_ARG for
+ * a shape not listed. */
 lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout);
 /* lbm_set_launch_layout with LBM_LAYOUT_STRIDED (nodes_per_thread 1 or 2). */
 lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread);
@@ -235,9 +235,29 @@ lbm_status lbm_launch_widths(int lattice, int storage, int *lo, int *hi);
  * layout) with its mean launch time in milliseconds.  Synchronises. */
 lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms);
 
-/* Information: D, Q, the step counter, and the device population buffer
- * currently holding the state (for profiling tools; do not free). */
+/* Information (outputs nullable): D, Q, the step counter, and the
+ * algorithmic bytes of one node update, 2 Q times the storage size (the
+ * populations read and written by one step). */
 lbm_status lbm_info(const lbm_handle *h, int *D, int *Q, int64_t *step, size_t *bytes_per_node);
+
+/* Speed above which one time step of the body force is lost to the rounding
+ * of the stored deviations: the regime in which a reduced storage format
+ * can carry a forced flow.  Each step adds the force to the first moment of
+ * the populations (Sec. II.C: after the collision the first central moment
+ * is F/2, before it the pull brought -F/2), so the stored deviation
+ * delta_i of a population changes by about 3 w_i c_i . g, while a fluid
+ * moving at u holds delta_i ~ 3 w_i c_i . u.  Rounding to nearest with a
+ * p-bit significand drops every change below half an ulp of the stored
+ * value, which is at least 2^-(p+1) of it; so once |u| exceeds
+ *   u_stall = 2^(p+1) max|g|     (p = 53, 24, 11, 8 for F64, F32, F16, BF16)
+ * the force increments round away and the flow stops gaining speed from the
+ * force (the stored state stagnates).  A flow accelerated from rest, u ~ g t,
+ * gets there after about 2^(p+1) steps: 512 in BF16, 4096 in FP16, 3.4e7 in
+ * FP32.  +inf without a force (or a zero one).  The maximum is over the
+ * force given at creation, by lbm_set_force, or by a schedule.  lbm_create
+ * leaves a note in lbm_last_error(h) when the initial velocity already
+ * exceeds u_stall. */
+lbm_status lbm_force_resolution(const lbm_handle *h, double *u_stall);
 
 void lbm_destroy(lbm_handle *h);
 const char *lbm_last_error(const lbm_handle *h);
@@ -354,6 +374,18 @@ enum { LBM_UNET_WGRAD_AUTO = 0, LBM_UNET_WGRAD_MMA_SYNC = 1 };
 lbm_status lbm_unet_set_wgrad(lbm_unet *u, int kind);
 const char *lbm_unet_last_error(const lbm_unet *u);
 void lbm_unet_destroy(lbm_unet *u);
+
+/* Arithmetic peak of the current device's CUDA cores, measured: one launch
+ * of a full wave of threads (8 blocks of 256 per SM), each running 8
+ * independent chains of `iters` fused multiply-adds, timed with CUDA events
+ * after one untimed launch.  precision: LBM_F32 or LBM_F64.  Outputs
+ * (nullable): TFLOP/s (2 flops per FMA) and the timed launch's duration.
+ * The ceilings of the step kernels that HBM does not bound: FP32 FMA for
+ * the collision arithmetic of the FP32, FP16 and BF16 modes (an FP32 FMA
+ * per lane per clock is also one warp instruction issued per scheduler per
+ * clock), FP64 FMA for the FP64 mode.  Measurement only; allocates and frees
+ * its own output buffer, synchronises. */
+lbm_status lbm_alu_peak(int precision, int64_t iters, double *tflops, double *ms);
 
 /* ------------------------------------------------------------------------
  * Split domains: the domain decomposition of the stream step (Sec. II.C).

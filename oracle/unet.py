@@ -193,37 +193,50 @@ def loss(y, t, m):
 
 def backward(params, cache, y, t, m, storage="fp64", periodic_x=False):
     """Gradient of loss(forward(params, x), t, m) with respect to params (the
-    exact derivative of the forward pass; with storage="bf16" the weights
-    are the rounded ones the forward pass used)."""
+    exact derivative of the forward pass).  With storage="bf16" the weights
+    are the rounded ones the forward pass used, and every gradient the GPU
+    stores in bfloat16 is rounded where it is stored (the arithmetic stays
+    FP64): the loss gradient at the head's output; each layer's dz (the
+    gradient at its pre-activation, after its ReLU's gate); the input
+    gradient of a layer whose input is pooled or upsampled, before the
+    pooling or upsampling adjoint; and the skip part of a concatenation,
+    gated by the encoder's ReLU, before the pooling path is added to it."""
     cin = cache["enc1a"][0].shape[-1]
     P = unpack(params, cin)
+    rnd = bf16 if storage == "bf16" else (lambda a: a)
     if storage == "bf16":
         P = {k: (bf16(W), b) for k, (W, b) in P.items()}
     relu_of = dict((l[0], l[3]) for l in LAYERS)
     grads = {}
-    dy = 2.0 * m[..., None] * (y - t) / (3.0 * m.sum())
+    dy = rnd(2.0 * m[..., None] * (y - t) / (3.0 * m.sum()))
+
+    def gate(name, d):
+        """d times the derivative of layer `name`'s ReLU at its pre-activation"""
+        return d * (cache[name][1] > 0) if relu_of[name] else d
 
     def back(name, dout):
+        """the layer's dz (dout gated, as stored), its weight and bias
+        gradients, and the gradient at its input (not gated, not rounded)"""
         inp, z = cache[name]
-        dz = dout * (z > 0) if relu_of[name] else dout
+        dz = rnd(gate(name, dout))
         dx, dW, db = conv_backward(inp, P[name][0], dz, periodic_x)
         grads[name] = (dW, db)
         return dx
 
     dd1 = back("dec1a", back("dec1b", back("head", dy)))
-    du1, de1 = dd1[..., :32], dd1[..., 32:]
-    dd2 = up_backward(back("up1", du1))
+    du1, de1 = dd1[..., :32], rnd(gate("enc1b", dd1[..., 32:]))
+    dd2 = up_backward(rnd(back("up1", du1)))
     dd2 = back("dec2a", back("dec2b", dd2))
-    du2, de2 = dd2[..., :64], dd2[..., 64:]
-    dd3 = up_backward(back("up2", du2))
+    du2, de2 = dd2[..., :64], rnd(gate("enc2b", dd2[..., 64:]))
+    dd3 = up_backward(rnd(back("up2", du2)))
     dd3 = back("dec3a", back("dec3b", dd3))
-    du3, de3 = dd3[..., :128], dd3[..., 128:]
-    dbb = up_backward(back("up3", du3))
-    dp3 = back("bota", back("botb", dbb))
+    du3, de3 = dd3[..., :128], rnd(gate("enc3b", dd3[..., 128:]))
+    dbb = up_backward(rnd(back("up3", du3)))
+    dp3 = rnd(back("bota", back("botb", dbb)))
     de3 = de3 + pool_backward(dp3)
-    dp2 = back("enc3a", back("enc3b", de3))
+    dp2 = rnd(back("enc3a", back("enc3b", de3)))
     de2 = de2 + pool_backward(dp2)
-    dp1 = back("enc2a", back("enc2b", de2))
+    dp1 = rnd(back("enc2a", back("enc2b", de2)))
     de1 = de1 + pool_backward(dp1)
     back("enc1a", back("enc1b", de1))
     return pack(grads, cin)

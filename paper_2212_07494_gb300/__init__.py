@@ -18,7 +18,7 @@ from ._binding import (  # noqa: F401
     lbm_check_device,
     lbm_set_force, lbm_set_force_schedule, lbm_set_force_scale_schedule, lbm_get_populations, lbm_set_populations, lbm_state_bytes, lbm_get_state,
     lbm_set_state, lbm_info, lbm_last_error, lbm_set_launch, lbm_set_launch_layout, lbm_get_launch,
-    lbm_launch_widths, LBM_LAYOUT_STRIDED, LBM_LAYOUT_VECTOR, lbm_autotune, lbm_check_noalloc, library, library_path,
+    lbm_launch_widths, LBM_LAYOUT_STRIDED, LBM_LAYOUT_VECTOR, lbm_force_resolution, lbm_alu_peak, lbm_autotune, lbm_check_noalloc, library, library_path,
     make_desc, Batch, lbm_batch_create, lbm_batch_run_to_steady, lbm_batch_step, lbm_batch_reset,
     lbm_batch_moments, lbm_batch_get_populations, lbm_batch_set_tiles, lbm_batch_autotune,
     lbm_batch_set_spin_limit, lbm_batch_set_handoff, lbm_batch_info, lbm_batch_last_error, lbm_batch_destroy, LBM_NOT_CONVERGED,

@@ -84,6 +84,8 @@ def library():
     L.lbm_set_launch_layout.argtypes = [H, C.c_int, C.c_int, C.c_int]
     L.lbm_get_launch.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_launch_widths.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_force_resolution.argtypes = [H, dp]
+    L.lbm_alu_peak.argtypes = [C.c_int, C.c_int64, dp, dp]
     L.lbm_autotune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.lbm_check_noalloc.argtypes = [C.POINTER(lbm_desc), C.c_void_p, C.c_void_p, C.c_void_p]
     S = C.c_void_p
@@ -127,7 +129,7 @@ def library():
               "lbm_check_device",
               "lbm_set_force", "lbm_set_force_schedule", "lbm_set_force_scale_schedule", "lbm_get_populations", "lbm_set_populations", "lbm_get_state",
               "lbm_set_state", "lbm_info", "lbm_set_launch", "lbm_set_launch_layout", "lbm_get_launch",
-              "lbm_launch_widths", "lbm_autotune", "lbm_check_noalloc", "lbm_split_schedule", "lbm_split_create",
+              "lbm_launch_widths", "lbm_force_resolution", "lbm_alu_peak", "lbm_autotune", "lbm_check_noalloc", "lbm_split_schedule", "lbm_split_create",
               "lbm_split_step", "lbm_split_check_device", "lbm_split_moments", "lbm_split_get_state",
               "lbm_split_get_populations", "lbm_split_set_launch_layout",
               "lbm_batch_create", "lbm_batch_run_to_steady", "lbm_batch_step", "lbm_batch_reset",
@@ -306,6 +308,19 @@ def lbm_launch_widths(lattice, storage):
     return lo.value, hi.value
 
 
+def lbm_force_resolution(h):
+    u = C.c_double()
+    _check(library().lbm_force_resolution(h, C.byref(u)), h)
+    return u.value
+
+
+def lbm_alu_peak(precision, iters):
+    """(TFLOP/s, ms) of the FMA microbenchmark (see lbm_alu_peak)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(library().lbm_alu_peak(_enum("storage", precision), int(iters), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
+
+
 def lbm_autotune(h, trials=20):
     bx, npt, ms = C.c_int(), C.c_int(), C.c_double()
     _check(library().lbm_autotune(h, int(trials), C.byref(bx), C.byref(npt), C.byref(ms)), h)
@@ -431,6 +446,15 @@ class Lattice:
     def launch(self):
         """(block_x, nodes_per_thread, layout) of the step kernel."""
         return lbm_get_launch(self.h)
+
+    def force_resolution(self):
+        """Speed above which one step of the force rounds away in the storage
+        format (see lbm_force_resolution); inf without a force."""
+        return lbm_force_resolution(self.h)
+
+    def note(self):
+        """lbm_last_error of the handle (a note lbm_create may leave)."""
+        return lbm_last_error(self.h)
 
     def autotune(self, trials=20, cache=None):
         """Pick the fastest launch shape (see lbm_autotune).  With a cache path,

@@ -25,6 +25,13 @@ int lattice_Q(int lat) { return lat == LBM_D2Q9 ? 9 : (lat == LBM_D3Q19 ? 19 : 2
 size_t storage_bytes(int st) { return st == LBM_F64 ? 8 : (st == LBM_F32 ? 4 : 2); }
 size_t arith_bytes(int st) { return st == LBM_F64 ? 8 : 4; }
 
+// 2^(p+1) max|g|, p the significand bits of the storage format (see
+// lbm_force_resolution)
+double stall_speed(int st, double gmax) {
+    const int p = st == LBM_F64 ? 53 : (st == LBM_F32 ? 24 : (st == LBM_F16_SHIFT ? 11 : 8));
+    return gmax > 0.0 ? std::ldexp(gmax, p + 1) : INFINITY;
+}
+
 const Launchers &launchers_for(int lat) {
     return lat == LBM_D2Q9 ? launchers_d2q9() : (lat == LBM_D3Q19 ? launchers_d3q19() : launchers_d3q27());
 }
@@ -114,6 +121,8 @@ struct lbm_handle {
     float *g32_dev = nullptr;    // FP32 copy of the force
     int64_t uprev_step = -1;
     double *fields = nullptr;    // (1 + D) * N doubles for lbm_moments
+    double gmax = 0.0;           // largest |g| component of the constant force (lbm_force_resolution)
+    double gmax_sched = 0.0;     // the same over a force schedule, while one is set
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // graph_steps steps starting from buf[0] / buf[1]
@@ -203,8 +212,12 @@ lbm_status upload_force(lbm_handle *h, const double *g) {
                 std::memcpy(&tmp[a * plane + zy * h->kp.nxp], &g[a * h->N() + zy * h->nx],
                             sizeof(double) * h->nx);
     }
-    for (double v : tmp)
+    double gmax = 0.0;
+    for (double v : tmp) {
         if (!std::isfinite(v)) return fail(h, LBM_ERR_ARG, "force contains a non-finite value");
+        gmax = std::max(gmax, std::fabs(v));
+    }
+    h->gmax = gmax;
     std::vector<float> tmp32(tmp.begin(), tmp.end());
     LBM_CUDA(h, cudaMemcpyAsync(h->g_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice,
                                 h->stream));
@@ -352,6 +365,9 @@ lbm_status set_schedule(lbm_handle *h, const std::vector<double> &table, int64_t
     drop_graphs(h);
     free_schedule(h);
     if (period == 0) return LBM_OK;
+    double m = 0.0;
+    for (double v : table) m = std::max(m, std::fabs(v));
+    h->gmax_sched = scale ? m * h->gmax : m;
     // extended by 64 wrapped entries: the kernels index it at counter + offset
     const size_t width = scale ? 1 : 3;
     std::vector<double> tmp(width * (size_t)(period + 64));
@@ -534,16 +550,17 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
     else fill_offsets<D3Q27>(kp);
 
-    // launch shape: without an obstacle mask the vector kernel (D2Q9 at its
-    // 16-byte width, the 3-D lattices at the narrower one); with a mask the
-    // strided kernel, wide rows with two nodes per thread
-    h->cfg.bdx = 128;
-    h->cfg.npt = (d->nx >= 512) ? 2 : 1;
+    // launch shape, from the measured rates on GB300: D2Q9 in 2-byte storage
+    // without an obstacle mask takes the vector kernel at its 16-byte width
+    // (where the strided kernel is bound by instruction issue); everything
+    // else the strided kernel, wide 2-D rows with two nodes per thread
+    h->cfg.bdx = D == 2 ? 128 : 64;
+    h->cfg.npt = (D == 2 && d->nx >= 512) ? 2 : 1;
     h->cfg.vec = 0;
     if (d->nx <= 64) h->cfg.bdx = 64;
-    if (!h->mask && (long long)Q * plane < (1LL << 32)) {
+    if (D == 2 && storage_bytes(d->storage) == 2 && !h->mask && (long long)Q * plane < (1LL << 32)) {
         h->cfg.vec = 1;
-        h->cfg.npt = D == 2 ? vec_width_hi(d->lattice, d->storage) : vec_width_lo(d->lattice, d->storage);
+        h->cfg.npt = vec_width_hi(d->lattice, d->storage);
         if ((long long)d->nx < 128LL * h->cfg.npt) h->cfg.bdx = 64;
         if ((long long)d->nx < 64LL * h->cfg.npt) h->cfg.bdx = 32;
     }
@@ -650,6 +667,15 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
         return s2;
     }
     h->cur = 0;
+    if (d->u0 && h->gmax > 0.0) {
+        double umax = 0.0;
+        for (size_t k = 0; k < (size_t)D * N; ++k) umax = std::max(umax, std::fabs(d->u0[k]));
+        const double us = stall_speed(h->storage, h->gmax);
+        if (umax > us)
+            h->err = "note: the initial speed " + std::to_string(umax) + " exceeds " + std::to_string(us) +
+                     ", above which one step of the body force rounds away in this storage format "
+                     "(lbm_force_resolution)";
+    }
     *out = h;
     return LBM_OK;
 }
@@ -932,6 +958,12 @@ lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_
     if (block_x) *block_x = best_cfg.bdx;
     if (nodes_per_thread) *nodes_per_thread = best_cfg.npt;
     if (ms) *ms = best;
+    return LBM_OK;
+}
+
+lbm_status lbm_force_resolution(const lbm_handle *h, double *u_stall) {
+    if (!h || !u_stall) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    *u_stall = stall_speed(h->storage, h->gs_dev ? h->gmax_sched : h->gmax);
     return LBM_OK;
 }
 

@@ -128,7 +128,8 @@ def test_vector_layout_field_force_and_autotune(lat):
     g = 1e-5 * rng.normal(D * nx * ny * nz).reshape(D, nz, ny, nx)
     rho0, u0 = W.random_near_equilibrium(lat, shape, seed=8, du=0.02)
     gl, orc = make_pair(lat, "SMRT", shape, TAU["SMRT"], "F64", periodic, g=g, force_kind="field", rho0=rho0, u0=u0)
-    assert gl.launch()[2] == 1            # the default layout without a mask
+    assert gl.launch()[2] == 0            # FP64 starts strided
+    gl.set_launch(32, _widths(lat, "F64")[-1], "vector")
     gl.step(40)
     orc.step(40)
     before = gl.populations()
@@ -140,6 +141,17 @@ def test_vector_layout_field_force_and_autotune(lat):
     ug, uo = gl.moments()[1], orc.moments()[1]
     assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-12
     gl.close()
+
+
+def test_default_layouts():
+    """A new handle starts with the layout measured faster on GB300: the
+    vector one for D2Q9 in 2-byte storage without a mask, else strided."""
+    import paper_2212_07494_gb300 as P
+    for lat, st, vec in (("D2Q9", "F16", 1), ("D2Q9", "BF16", 1), ("D2Q9", "F32", 0), ("D3Q27", "F16", 0)):
+        shape = (256, 8, 1) if lat == "D2Q9" else (64, 4, 4)
+        gl = P.Lattice(lat, "SMRT", shape, TAU["SMRT_TRIM"], st, (1, 1, 1))
+        assert gl.launch()[2] == vec, (lat, st, gl.launch())
+        gl.close()
 
 
 def test_vector_layout_rejected_with_a_mask():
