@@ -268,18 +268,27 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
             const R om2 = R(C.om2), om3 = R(C.om3), om4 = R(C.om4), gx = R(C.gx), gy = R(C.gy);
             const bool trim = C.om3 == 1.0 && C.om4 == 1.0;
             double v[2] = {0.0, 0.0};
-            // two nodes per thread per pass, all loads issued first
-            for (int base = threadIdx.x; base < nn; base += 2 * blockDim.x) {
+            // two nodes per thread per pass, all loads issued first.  The
+            // tile's nodes are numbered row by row; a thread's two nodes
+            // (numbers base and base + blockDim.x) advance by 2 blockDim.x a
+            // pass, i.e. by (dy, dx) rows and columns with one carry, so no
+            // node needs a division
+            const int stride = 2 * (int)blockDim.x;
+            const int dy = stride / C.nx, dx = stride - dy * C.nx;
+            int xs[2], ys[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int idx = (int)threadIdx.x + k * (int)blockDim.x;
+                const int yy = idx / C.nx;
+                xs[k] = idx - yy * C.nx;
+                ys[k] = y0 + yy;
+            }
+            for (int base = threadIdx.x; base < nn; base += stride) {
                 R G[2][9];
-                int xs[2], ys[2];
                 bool on[2];
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    const int idx = base + k * blockDim.x;
-                    on[k] = idx < nn;
-                    const int yy = (int)((unsigned)idx / (unsigned)C.nx);
-                    xs[k] = idx - yy * C.nx;
-                    ys[k] = y0 + yy;
+                    on[k] = base + k * (int)blockDim.x < nn;
                     if (on[k] && solid) on[k] = solid[ys[k] * C.nxp + xs[k]] == 0;
                     if (on[k]) gather_chan<ST>(C, fin, solid, xs[k], ys[k], G[k]);
                 }
@@ -313,6 +322,15 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                     T *dst = fout + (y * C.nxp + x);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[k][gpos<D2Q9>(i)]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    xs[k] += dx;
+                    ys[k] += dy;
+                    if (xs[k] >= C.nx) {
+                        xs[k] -= C.nx;
+                        ++ys[k];
+                    }
                 }
             }
             if (check) {

@@ -528,7 +528,7 @@ __host__ __device__ __forceinline__ void collide_smrt_fneq(R *G, R gx, R gy, R g
     R d2[N], F3[N], d3[N];                // second- and third-order central moments of f, d_F^(3)
 #pragma unroll
     for (int g = 0; g < N; ++g) d2[g] = morder<D>(g) == 2 ? G[g] : R(0);
-    relax_order2<D>(d2, R(0.5) * om2, R(0.5) * omb);   // d^(2) = (1 - om/2) dbar_1^(2) per part
+    relax_order2<D>(d2, R(R(0.5) * om2), R(R(0.5) * omb));   // d^(2) = (1 - om/2) dbar_1^(2) per part
 #pragma unroll
     for (int g = 0; g < N; ++g) {
         F3[g] = R(0);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "lbm_device.cuh"
+#include "lbm_f32x2.cuh"
 
 namespace lbm {
 

@@ -7,6 +7,15 @@
 
 namespace lbm {
 
+template <int L, int COLL, typename R>
+__device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
+    if constexpr (COLL == SMRT) collide_smrt<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<L>(G, gx, gy, gz, om2);
+    else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<L>(G, gx, gy, gz, om2, om3, om4);
+    else collide_bgk<L>(G, gx, gy, gz, om2);
+}
+
 // Fused pull-stream + collide + store for NPT nodes per thread along x
 // (strided by blockDim.x so every load instruction of a warp is a contiguous
 // row segment).  Loads for all NPT nodes are issued before any arithmetic.
@@ -30,6 +39,32 @@ __global__ void __launch_bounds__(256) k_step(const KParams p, const typename St
     R gx, gy, gz;
     const bool per_node_force = p.force_kind == G_FIELD;
     if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
+    if constexpr (NPT == 2 && sizeof(R) == 4) {
+        // both nodes present: one collision for the pair in packed FP32
+        if (act[0] && act[1]) {
+            const long long own0 = node_index(p, x0, y, z), own1 = own0 + blockDim.x;
+            F2 G2[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) G2[g] = F2::pair(G[0][g], G[1][g]);
+            F2 gx2 = F2(gx), gy2 = F2(gy), gz2 = F2(gz);
+            if (per_node_force) {
+                R ax, ay, az, bx, by, bz;
+                load_force<L>(p, y, own0, ax, ay, az);
+                load_force<L>(p, y, own1, bx, by, bz);
+                gx2 = F2::pair(ax, bx);
+                gy2 = F2::pair(ay, by);
+                gz2 = F2::pair(az, bz);
+            }
+            collide_any<L, COLL>(G2, gx2, gy2, gz2, F2(om2), F2(om3), F2(om4), F2(omb));
+            typename Store<ST>::T *d0 = fout + own0, *d1 = fout + own1;
+#pragma unroll
+            for (int i = 0; i < Lat<L>::Q; ++i) {
+                Store<ST>::st(d0 + p.poff[i], G2[gpos<L>(i)].lo());
+                Store<ST>::st(d1 + p.poff[i], G2[gpos<L>(i)].hi());
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         if (!act[k]) continue;

@@ -22,7 +22,7 @@
 // Element offsets are 32-bit: the host launches this kernel only when
 // Q * plane < 2^32.
 #pragma once
-#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
 
 namespace lbm {
 
@@ -138,14 +138,6 @@ template <int ST, int V> struct Vec {
     }
 };
 
-template <int L, int COLL, typename R>
-__device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
-    if constexpr (COLL == SMRT) collide_smrt<L>(G, gx, gy, gz, om2, om3, om4, omb);
-    else if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<L>(G, gx, gy, gz, om2);
-    else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G, gx, gy, gz, om2, om3, om4, omb);
-    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<L>(G, gx, gy, gz, om2, om3, om4);
-    else collide_bgk<L>(G, gx, gy, gz, om2);
-}
 
 // source row index along one axis for c = -1, 0, +1 (entry c + 1): the
 // coordinate minus c, wrapped on a periodic axis; false if it lies beyond a
@@ -225,20 +217,52 @@ __global__ void __launch_bounds__(256) k_step_vec(const KParams p, const typenam
             const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.nxp + (unsigned)x0;
             unsigned o[Q][NW];
             R held[Q];
+            if constexpr (sizeof(R) == 4 && V % 2 == 0) {
+                // nodes k and k + 1 collide together in packed FP32
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                R G[NG];
+                for (int k = 0; k < V; k += 2) {
+                    F2 G2[NG];
 #pragma unroll
-                for (int g = 0; g < NG; ++g) G[g] = R(0);
+                    for (int g = 0; g < NG; ++g) G2[g] = F2(0.0f);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const int e = k - Lat<L>::cx(i);   // element of the source vector
-                    G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e);
+                    for (int i = 0; i < Q; ++i) {
+                        const int e0 = k - Lat<L>::cx(i), e1 = e0 + 1;
+                        const R v0 = (e0 < 0 || e0 >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e0);
+                        const R v1 = (e1 < 0 || e1 >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e1);
+                        G2[gpos<L>(i)] = F2::pair(v0, v1);
+                    }
+                    F2 gx2 = F2(gx), gy2 = F2(gy), gz2 = F2(gz);
+                    if (per_node_force) {
+                        R ax, ay, az, bx, by, bz;
+                        load_force<L>(p, y, (long long)own + k, ax, ay, az);
+                        load_force<L>(p, y, (long long)own + k + 1, bx, by, bz);
+                        gx2 = F2::pair(ax, bx);
+                        gy2 = F2::pair(ay, by);
+                        gz2 = F2::pair(az, bz);
+                    }
+                    collide_any<L, COLL>(G2, gx2, gy2, gz2, F2(om2), F2(om3), F2(om4), F2(omb));
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        VT::put(o[i], k, G2[gpos<L>(i)].lo(), held[i]);
+                        VT::put(o[i], k + 1, G2[gpos<L>(i)].hi(), held[i]);
+                    }
                 }
-                if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
-                collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+            } else {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
+                for (int k = 0; k < V; ++k) {
+                    R G[NG];
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) G[g] = R(0);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int e = k - Lat<L>::cx(i);   // element of the source vector
+                        G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e);
+                    }
+                    if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
+                    collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
+                }
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) VT::store(fout + ((unsigned)i * (unsigned)p.plane + own), o[i]);

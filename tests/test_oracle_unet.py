@@ -92,3 +92,65 @@ def test_gradient_matches_finite_differences(cin, periodic_x):
         tol = 1e-5 * max(1e-3, abs(g[k])) + 1e-9
         errs = [abs((f1 - f2) / (2 * h) - g[k]), abs((f1 - f0) / h - g[k]), abs((f0 - f2) / h - g[k])]
         assert min(errs) <= tol, (k, errs, g[k])
+
+
+def _small_problem(seed=4, H=16, W=24, n=2, cin=3):
+    rng = np.random.default_rng(seed)
+    params = U.init_params(seed, cin)
+    sl, _ = U.layer_slices(cin)
+    for name, ci, co, relu, wo, bo in sl:
+        params[bo:bo + co] = 0.05 * rng.normal(size=co)
+    x = rng.normal(size=(n, H, W, cin))
+    t = rng.normal(size=(n, H, W, 3))
+    m = (rng.uniform(size=(n, H, W)) > 0.2).astype(np.float64)
+    return params, x, t, m
+
+
+def _per_layer(g, ref, cin=3):
+    sl, _ = U.layer_slices(cin)
+    w = {name: np.linalg.norm(g[wo:bo] - ref[wo:bo]) / np.linalg.norm(ref[wo:bo]) for name, ci, co, r, wo, bo in sl}
+    b = {name: np.linalg.norm(g[bo:bo + co] - ref[bo:bo + co]) / np.linalg.norm(ref[bo:bo + co])
+         for name, ci, co, r, wo, bo in sl}
+    return w, b
+
+
+def test_bf16_gradient_rounds_only_what_is_stored():
+    """With BF16 storage emulated, the stored gradients are rounded: the
+    result differs from the unrounded gradient by about BF16's resolution,
+    not more (no term dropped on the way)."""
+    params, x, t, m = _small_problem()
+    y, cache = U.forward(params, x, storage="bf16")
+    g_r = U.backward(params, cache, y, t, m, storage="bf16")
+    P = U.unpack(params)
+    exact = {k: (U.bf16(Wt), b) for k, (Wt, b) in P.items()}
+    g_u = U.backward(U.pack(exact), cache, y, t, m)   # same rounded weights, unrounded gradients
+    w, b = _per_layer(g_r, g_u)
+    assert max(w.values()) < 2e-2 and max(b.values()) < 2e-2, (w, b)
+    assert max(w.values()) > 1e-4
+
+
+@pytest.mark.parametrize("layer", ["dec2b", "enc1b", "head"])
+def test_gradient_bar_catches_a_dropped_tap(layer, monkeypatch):
+    """The GPU gradient test's bar (per-layer relative L2 below 2e-2, weights
+    and biases apart) against a planted mistake in the oracle: one of the
+    nine taps dropped from one layer's input gradient (the adjoint
+    convolution) moves the gradients of that layer's inputs by far more."""
+    params, x, t, m = _small_problem()
+    y, cache = U.forward(params, x, storage="bf16")
+    ref = U.backward(params, cache, y, t, m, storage="bf16")
+    real = U.conv_backward
+    target = U.unpack(params)[layer][0].shape
+
+    def dropped(xin, Wt, dz, periodic_x=False):
+        dx, dW, db = real(xin, Wt, dz, periodic_x)
+        if Wt.shape == target:
+            W2 = Wt.copy()
+            W2[:, 1, 2] = 0.0          # tap (ky, kx) = (1, 2) missing from the adjoint
+            dx = real(xin, W2, dz, periodic_x)[0]
+        return dx, dW, db
+
+    monkeypatch.setattr(U, "conv_backward", dropped)
+    bad = U.backward(params, cache, y, t, m, storage="bf16")
+    w, b = _per_layer(bad, ref)
+    worst = max(max(w.values()), max(b.values()))
+    assert worst > 5e-2, (layer, w, b)
