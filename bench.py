@@ -396,7 +396,7 @@ def run_gpu(args, ws, rank, local):
     region_ms = [reduce_max(e0[r].elapsed_time(e1[r]), dist, f"cuda:{local}") for r in range(repeats)]
     total_ms = sum(region_ms)
     kern_ms = sum(es.elapsed_time(ee) for es, ee, _ in chunk_ev) / sum(n for _, _, n in chunk_ev)
-    bx, npt, layout = lat.launch()
+    bx, npt, layout, rows = lat.launch()
     u_stall = lat.force_resolution()
     ck = checks[:max(1, k)].cpu().numpy()
     finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
@@ -450,7 +450,8 @@ def run_gpu(args, ws, rank, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": (f"k_step_vec<{L},{kname},{st},{npt}>" if layout
                                     else f"k_step<{L},{kname},{st},{npt}>"),
-                         "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided"},
+                         "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided",
+                                    "rows_per_block": rows},
                          "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,
@@ -541,9 +542,16 @@ def run_batch(args, ws, rank, local):
                                                                      "block": block, "tile_nodes": tile}}))
         return
     torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    sampler.mark(0)
     t0 = time.perf_counter()
     status, steps, st, r = b.run_to_steady(args.tol, args.K, max_steps=50_000_000)
     t_batch = time.perf_counter() - t0
+    sampler.mark(1)
+    sampler.stop()
+    clocks = sampler.summary()
     nodes = np.array([c.nx * c.ny for c in chans], np.float64)
     updates = float((steps * nodes).sum())
     idx = list(range(0, len(chans), max(1, args.plain_stride)))
@@ -595,7 +603,7 @@ def run_batch(args, ws, rank, local):
             "plain": {"seconds_measured": t_plain, "channels_measured": len(idx), "seconds_extrapolated": t_plain_est,
                       "how": f"every {args.plain_stride}th channel run alone (lbm_create, lbm_residual every K), "
                              f"time x {scale:g}"},
-            "speedup_vs_plain": t_plain_est / t_batch,
+            "speedup_vs_plain": t_plain_est / t_batch, "clocks": clocks,
             "equal_error": {"max_rel_l2_batch_vs_plain": max(errs), "plain_vs_batch_steps_diff_max":
                             int(max(abs(int(steps[i]) - 1 - p) for i, p in zip(idx, plain_steps))),
                             "rel_l2_vs_noslip_parabola_median": float(np.median(para)),
@@ -644,6 +652,10 @@ def run_surrogate(args, ws, rank, local):
     losses, t_train, nsteps = sur.train(X, Y, M, epochs=1000, lr=1e-3, seconds=args.train_seconds)
     flops = S.train_flops_per_sample(H, Wd) * 8 * nsteps
     # held-out: cold (batched), warm (batched, inference included)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    sampler.mark(0)
     secs_c, steps_c, st_c, r_c, bc = S.solve(held, tol, K, max_steps)
     cold = S.final_fields(bc, len(held))
     bc.close()
@@ -662,6 +674,9 @@ def run_surrogate(args, ws, rank, local):
         train_err.append(float(np.linalg.norm(S.fields(Yt[j], *train[k], alpha=alpha)[1] - ut) / np.linalg.norm(ut)))
     secs_l, steps_l, st_l, _, _, fallbacks_l = S.warm_start(None, held, tol, K, max_steps)
     secs_w, steps_w, st_w, warm, t_inf, fallbacks = S.warm_start(sur, held, tol, K, max_steps)
+    sampler.mark(1)
+    sampler.stop()
+    clocks = sampler.summary()
     diff = [float(np.linalg.norm(warm[k][1] - cold[k][1]) / np.linalg.norm(cold[k][1])) for k in range(len(held))]
     # plain sequential cold start on a subset
     t_plain, n_plain = 0.0, 0
@@ -703,7 +718,7 @@ def run_surrogate(args, ws, rank, local):
             "lubrication_only": {"seconds": secs_l, "steps_mean": float(np.mean(steps_l)),
                                  "converged": int((st_l == 0).sum()), "fallbacks_to_cold": int(fallbacks_l),
                                  "what": "warm start from the lubrication estimate the network corrects"},
-            "speedup_vs_cold_batched": secs_c / secs_w,
+            "speedup_vs_cold_batched": secs_c / secs_w, "clocks": clocks,
             "plain_cold": {"seconds_extrapolated": t_plain_est, "cases_measured": n_plain,
                            "how": "every 10th held-out case alone (lbm_create, lbm_residual every K), time scaled"},
             "speedup_vs_plain_cold": t_plain_est / secs_w,
@@ -796,6 +811,10 @@ def run_precision(args, ws, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream(device=local)
     peak, _ = measured_peaks()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    sampler.mark(0)
 
     def run(label, make, steps):
         out, ref = {}, None
@@ -812,8 +831,12 @@ def run_precision(args, ws, rank, local):
             D, Q, _, bpn = lat.info()
             rho, u, tot = lat.moments()
             N = rho.size
-            rec = {"mlups": N / ms / 1e3, "gbs": N * bpn / ms / 1e6, "hbm_frac": N * bpn / ms / 1e6 / peak,
-                   "ms_per_step": ms, "launch": [bx, npt], "finite": bool(np.all(np.isfinite(u)))}
+            ach = N * bpn / ms / 1e6
+            rec = {"mlups": N / ms / 1e3, "gbs": ach, "hbm_frac": ach / peak,
+                   "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                "traffic": None},
+                   "ms_per_step": ms, "launch": list(lat.launch()), "finite": bool(np.all(np.isfinite(u))),
+                   "u_stall": lat.force_resolution(), "u_max": float(np.abs(u).max())}
             if ref is None:
                 ref = u
             else:
@@ -831,6 +854,9 @@ def run_precision(args, ws, rank, local):
                                           rho0=tg.rho0, u0=tg.u0, torch_stream=stream), tg.steps)
     tgv19 = run("tgv19", lambda st: P.Lattice("D3Q19", "SMRT", tg.shape, tg.tau, st, tg.periodic, g=tg.g,
                                               rho0=tg.rho0, u0=tg.u0, torch_stream=stream), tg.steps)
+    sampler.mark(1)
+    sampler.stop()
+    clocks = sampler.summary()
     # the FP64 oracle on the host cores, as a baseline per 3-D lattice: 3 steps on
     # a 256 x 256 x 4 periodic slab of the same vortex
     import oracle as O
@@ -853,6 +879,7 @@ def run_precision(args, ws, rank, local):
                        "tgv3d": {"n": args.tgv_n, "steps": args.tgv_steps, "Re": 1600, "U0": 0.05,
                                  "tau2": tg.tau[2], "lattice": "D3Q27"}},
             "kolmogorov_d2q9_smrt": kol, "tgv_d3q27_smrt": tgv, "tgv_d3q19_smrt": tgv19, "peak_gbs": peak,
+            "clocks": clocks,
             "cpu_baseline_3d": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
             // pass, i.e. by (dy, dx) rows and columns with one carry, so no
             // node needs a division
             const int stride = 2 * (int)blockDim.x;
-            const int dy = stride / C.nx, dx = stride - dy * C.nx;
+            const int step_dy = stride / C.nx, step_dx = stride - step_dy * C.nx;
             int xs[2], ys[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -314,9 +314,34 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                         snap[n] = ux;
                         snap[N + n] = uy;
                     }
-                    // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it, so
-                    // that a channel evolves with the same arithmetic here and alone
-                    if (COLL == SMRT && trim) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
+                }
+                if constexpr (ST == ST_F32) {
+                    if (on[0] && on[1]) {
+                        // both nodes: one collision in packed FP32, as k_step
+                        // pairs its nodes, so that a channel evolves with the
+                        // same arithmetic here and alone
+                        F2 G2[9];
+#pragma unroll
+                        for (int g = 0; g < 9; ++g) G2[g] = F2::pair(G[0][g], G[1][g]);
+                        const F2 gx2 = F2(gx), gy2 = F2(gy), z2 = F2(0.0f);
+                        if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+                        else if (COLL == SMRT) collide_smrt<D2Q9>(G2, gx2, gy2, z2, F2(om2), F2(om3), F2(om4), F2(om2));
+                        else collide_bgk<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+                        T *d0 = fout + (ys[0] * C.nxp + xs[0]), *d1 = fout + (ys[1] * C.nxp + xs[1]);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            Store<ST>::st(d0 + i * (int)C.plane, G2[gpos<D2Q9>(i)].lo());
+                            Store<ST>::st(d1 + i * (int)C.plane, G2[gpos<D2Q9>(i)].hi());
+                        }
+                        on[0] = on[1] = false;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (!on[k]) continue;
+                    const int x = xs[k], y = ys[k];
+                    // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it
+                    if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
                     else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
                     else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
                     T *dst = fout + (y * C.nxp + x);
@@ -325,8 +350,8 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                 }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    xs[k] += dx;
-                    ys[k] += dy;
+                    xs[k] += step_dx;
+                    ys[k] += step_dy;
                     if (xs[k] >= C.nx) {
                         xs[k] -= C.nx;
                         ++ys[k];
@@ -515,14 +540,23 @@ lbm_status build_tiles(lbm_batch *b) {
 
 typedef void (*BatchKernel)(const BatchRun);
 
-BatchKernel batch_kernel(int coll, int st) {
+// SMRT with every channel at tau_3 = tau_4 = 1 takes the kernel built for the
+// trimmed collision alone
+BatchKernel batch_kernel(int coll, int st, bool all_trim) {
+    if (coll == LBM_SMRT && all_trim) return st == LBM_F64 ? k_batch<SMRT_TRIM, ST_F64> : k_batch<SMRT_TRIM, ST_F32>;
     if (coll == LBM_SMRT) return st == LBM_F64 ? k_batch<SMRT, ST_F64> : k_batch<SMRT, ST_F32>;
     return st == LBM_F64 ? k_batch<BGK, ST_F64> : k_batch<BGK, ST_F32>;
 }
 
+bool all_trim(const lbm_batch *b) {
+    for (const BatchChan &C : b->ch)
+        if (!(C.om3 == 1.0 && C.om4 == 1.0)) return false;
+    return true;
+}
+
 // one run: reset + persistent kernel, captured in a graph and launched once
 lbm_status batch_run(lbm_batch *b, double tol, int K, int64_t max_steps) {
-    BatchKernel kern = batch_kernel(b->collision, b->storage);
+    BatchKernel kern = batch_kernel(b->collision, b->storage, all_trim(b));
     int dev = 0, sms = 0, per_sm = 0;
     B_CUDA(b, cudaGetDevice(&dev));
     B_CUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

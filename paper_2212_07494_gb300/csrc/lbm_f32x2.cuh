@@ -32,6 +32,9 @@ struct F2 {
         return r;
     }
     __device__ __forceinline__ void set(float a, float b) { asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(a), "f"(b)); }
+    __device__ __forceinline__ void split(float &a, float &b) const {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    }
     __device__ __forceinline__ float lo() const { return __uint_as_float((unsigned)v); }
     __device__ __forceinline__ float hi() const { return __uint_as_float((unsigned)(v >> 32)); }
 };

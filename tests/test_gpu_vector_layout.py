@@ -65,8 +65,9 @@ def test_vector_layout_f64_matches_oracle(lat, coll, case):
     for V in _widths(lat, "F64"):
         for bx in (32, 128):
             gl, o = make_pair(lat, _model(coll), shape, TAU[coll], "F64", periodic, g=_g(lat))
-            gl.set_launch(bx, V, "vector")
-            assert gl.launch() == (bx, V, 1)
+            rows = 1 if bx == 32 else 5
+            gl.set_launch(bx, V, "vector", rows)
+            assert gl.launch() == (bx, V, 1, rows)
             gl.set_populations(f0)
             if orc is None:
                 orc = o
@@ -104,7 +105,7 @@ def test_vector_layout_reduced_storage(lat, storage, coll):
         gl.step(1)
         strided = gl.populations()
         for V in _widths(lat, storage):
-            gl.set_launch(64, V, "vector")
+            gl.set_launch(64, V, "vector", 3)
             gl.set_populations(fr)
             gl.step(1)
             fv = gl.populations()
