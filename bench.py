@@ -396,7 +396,7 @@ def run_gpu(args, ws, rank, local):
     region_ms = [reduce_max(e0[r].elapsed_time(e1[r]), dist, f"cuda:{local}") for r in range(repeats)]
     total_ms = sum(region_ms)
     kern_ms = sum(es.elapsed_time(ee) for es, ee, _ in chunk_ev) / sum(n for _, _, n in chunk_ev)
-    bx, npt, layout, rows = lat.launch()
+    bx, npt, layout = lat.launch()
     u_stall = lat.force_resolution()
     ck = checks[:max(1, k)].cpu().numpy()
     finite = bool(np.all(ck[:, 6] == 0)) and bool(np.all(np.isfinite(ck)))
@@ -450,8 +450,7 @@ def run_gpu(args, ws, rank, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": (f"k_step_vec<{L},{kname},{st},{npt}>" if layout
                                     else f"k_step<{L},{kname},{st},{npt}>"),
-                         "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided",
-                                    "rows_per_block": rows},
+                         "launch": {"block_x": bx, "nodes_per_thread": npt, "layout": "vector" if layout else "strided"},
                          "bytes_per_launch": algo_bytes,
                          "avg_launch_ms": kern_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": launches, "clocks": clocks,

@@ -212,23 +212,21 @@ lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t 
 typedef enum { LBM_LAYOUT_STRIDED = 0, LBM_LAYOUT_VECTOR = 1 } lbm_layout;
 
 /* Launch shape of the fused stream-collide kernel: threads per block along x
- * (block_x: 32, 64, 128 or 256), nodes per thread along x and their layout,
- * and for LBM_LAYOUT_VECTOR the row bands a block runs through (rows, 1 to
- * 64; each thread loads the next band while it collides the current one;
- * rows = 1 for the strided layout).  Drops the captured step graphs;
+ * (block_x: 32, 64, 128 or 256), nodes per thread along x and their layout.
+ * Drops the captured step graphs;
  * synchronises the handle's stream.  The physics does not depend on the
  * shape; in FP32 arithmetic the results can differ in the last bits between
  * shapes (the FP32 storage modes collide nodes two at a time in packed FP32
  * where a thread has two, which may pair fused multiply-adds differently
  * from one node at a time).  A new handle starts with the vector layout at
- * its wider width, 32 threads and 8 row bands for D2Q9 in FP16 or BF16
+ * its wider width and 32 threads per block for D2Q9 in FP16 or BF16
  * storage when the layout applies, else with the strided layout (the faster
  * ones on GB300).  LBM_ERR_ARG for a shape not listed. */
-lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout, int rows);
+lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout);
 /* lbm_set_launch_layout with LBM_LAYOUT_STRIDED (nodes_per_thread 1 or 2). */
 lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread);
 /* The current launch shape (outputs nullable). */
-lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout, int *rows);
+lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout);
 /* The two vector widths (nodes per thread; equal when only one is built) of
  * LBM_LAYOUT_VECTOR for a lattice and storage (outputs nullable). */
 lbm_status lbm_launch_widths(int lattice, int storage, int *lo, int *hi);
@@ -236,10 +234,10 @@ lbm_status lbm_launch_widths(int lattice, int storage, int *lo, int *hi);
 /* Time every supported launch shape over `trials` launches each (CUDA events
  * on the handle's stream; the kernel reads the current state and writes the
  * spare buffer, so the state does not advance): the strided shapes, and the
- * vector shapes (blocks of 32, 64, 128; both widths; 1 or 8 row bands) where
+ * vector shapes (blocks of 32, 64, 128; both widths) where
  * that layout applies.  Keep the fastest and return its block_x and
- * nodes_per_thread (outputs nullable; lbm_get_launch gives its layout and
- * rows) with its mean launch time in milliseconds.  Synchronises. */
+ * nodes_per_thread (outputs nullable; lbm_get_launch gives its layout) with
+ * its mean launch time in milliseconds.  Synchronises. */
 lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_thread, double *ms);
 
 /* Information (outputs nullable): D, Q, the step counter, and the
@@ -445,7 +443,7 @@ size_t lbm_split_state_bytes(const lbm_split *s);
 lbm_status lbm_split_get_state(lbm_split *s, void *host, size_t bytes, int64_t *step);
 lbm_status lbm_split_get_populations(lbm_split *s, double *f);
 /* lbm_set_launch_layout on every slab. */
-lbm_status lbm_split_set_launch_layout(lbm_split *s, int block_x, int nodes_per_thread, int layout, int rows);
+lbm_status lbm_split_set_launch_layout(lbm_split *s, int block_x, int nodes_per_thread, int layout);
 /* Last error message of s (of the calling thread when s is NULL). */
 const char *lbm_split_last_error(const lbm_split *s);
 void lbm_split_destroy(lbm_split *s);

@@ -81,8 +81,8 @@ def library():
     L.lbm_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                            C.POINTER(C.c_size_t)]
     L.lbm_set_launch.argtypes = [H, C.c_int, C.c_int]
-    L.lbm_set_launch_layout.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int]
-    L.lbm_get_launch.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_set_launch_layout.argtypes = [H, C.c_int, C.c_int, C.c_int]
+    L.lbm_get_launch.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_launch_widths.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_force_resolution.argtypes = [H, dp]
     L.lbm_alu_peak.argtypes = [C.c_int, C.c_int64, dp, dp]
@@ -99,7 +99,7 @@ def library():
     L.lbm_split_state_bytes.restype = C.c_size_t
     L.lbm_split_get_state.argtypes = [S, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64)]
     L.lbm_split_get_populations.argtypes = [S, dp]
-    L.lbm_split_set_launch_layout.argtypes = [S, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.lbm_split_set_launch_layout.argtypes = [S, C.c_int, C.c_int, C.c_int]
     L.lbm_split_last_error.argtypes = [S]
     L.lbm_split_last_error.restype = C.c_char_p
     L.lbm_split_destroy.argtypes = [S]
@@ -291,16 +291,15 @@ def lbm_set_launch(h, block_x, nodes_per_thread):
     _check(library().lbm_set_launch(h, int(block_x), int(nodes_per_thread)), h)
 
 
-def lbm_set_launch_layout(h, block_x, nodes_per_thread, layout, rows=1):
-    _check(library().lbm_set_launch_layout(h, int(block_x), int(nodes_per_thread), _enum("layout", layout),
-                                           int(rows)), h)
+def lbm_set_launch_layout(h, block_x, nodes_per_thread, layout):
+    _check(library().lbm_set_launch_layout(h, int(block_x), int(nodes_per_thread), _enum("layout", layout)), h)
 
 
 def lbm_get_launch(h):
-    """(block_x, nodes_per_thread, layout, rows)"""
-    bx, npt, lay, rows = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-    _check(library().lbm_get_launch(h, C.byref(bx), C.byref(npt), C.byref(lay), C.byref(rows)), h)
-    return bx.value, npt.value, lay.value, rows.value
+    """(block_x, nodes_per_thread, layout)"""
+    bx, npt, lay = C.c_int(), C.c_int(), C.c_int()
+    _check(library().lbm_get_launch(h, C.byref(bx), C.byref(npt), C.byref(lay)), h)
+    return bx.value, npt.value, lay.value
 
 
 def lbm_launch_widths(lattice, storage):
@@ -441,13 +440,12 @@ class Lattice:
     def info(self):
         return lbm_info(self.h)
 
-    def set_launch(self, block_x, nodes_per_thread, layout=0, rows=1):
-        """layout 0 / "strided" or 1 / "vector"; rows: row bands per block of
-        the vector layout (see lbm_set_launch_layout)."""
-        lbm_set_launch_layout(self.h, block_x, nodes_per_thread, layout, rows)
+    def set_launch(self, block_x, nodes_per_thread, layout=0):
+        """layout 0 / "strided" or 1 / "vector" (see lbm_set_launch_layout)."""
+        lbm_set_launch_layout(self.h, block_x, nodes_per_thread, layout)
 
     def launch(self):
-        """(block_x, nodes_per_thread, layout, rows) of the step kernel."""
+        """(block_x, nodes_per_thread, layout) of the step kernel."""
         return lbm_get_launch(self.h)
 
     def force_resolution(self):
@@ -550,9 +548,9 @@ def lbm_split_get_populations(s, f):
     _scheck(library().lbm_split_get_populations(s, _dptr(f)), s)
 
 
-def lbm_split_set_launch_layout(s, block_x, nodes_per_thread, layout, rows=1):
+def lbm_split_set_launch_layout(s, block_x, nodes_per_thread, layout):
     _scheck(library().lbm_split_set_launch_layout(s, int(block_x), int(nodes_per_thread),
-                                                  _enum("layout", layout), int(rows)), s)
+                                                  _enum("layout", layout)), s)
 
 
 def lbm_split_last_error(s):
@@ -604,8 +602,8 @@ class Split:
         lbm_split_get_populations(self.s, f)
         return f.reshape((self.Q,) + self.shape)
 
-    def set_launch(self, block_x, nodes_per_thread, layout=0, rows=1):
-        lbm_split_set_launch_layout(self.s, block_x, nodes_per_thread, layout, rows)
+    def set_launch(self, block_x, nodes_per_thread, layout=0):
+        lbm_split_set_launch_layout(self.s, block_x, nodes_per_thread, layout)
 
     def close(self):
         if getattr(self, "s", None) is not None:

@@ -22,7 +22,6 @@ struct StepCfg {
     int bdx;  // threads per block along x
     int npt;  // nodes per thread: strided by bdx (vec = 0), or consecutive (vec = 1)
     int vec;  // 1: k_step_vec, each population of a thread's npt nodes moved as one vector
-    int rows; // k_step_vec: row bands a block runs through (loading the next while colliding one)
 };
 
 // vector widths (nodes per thread) k_step_vec is built for, per lattice and

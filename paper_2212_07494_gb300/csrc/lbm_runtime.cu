@@ -107,7 +107,7 @@ struct lbm_handle {
     int force_kind = 0;
     bool mask = false;
     KParams kp{};
-    StepCfg cfg{128, 1, 0, 1};
+    StepCfg cfg{128, 1, 0};
     size_t state_bytes = 0;   // one population buffer
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;              // buffer holding the state
@@ -558,12 +558,10 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     h->cfg.npt = (D == 2 && d->nx >= 512) ? 2 : 1;
     h->cfg.vec = 0;
     if (d->nx <= 64) h->cfg.bdx = 64;
-    h->cfg.rows = 1;
     if (D == 2 && storage_bytes(d->storage) == 2 && !h->mask && (long long)Q * plane < (1LL << 32)) {
         h->cfg.vec = 1;
         h->cfg.npt = vec_width_hi(d->lattice, d->storage);
         h->cfg.bdx = 32;
-        h->cfg.rows = 8;
     }
     h->graph_steps = 64;
 
@@ -873,12 +871,10 @@ lbm_status lbm_set_state(lbm_handle *h, const void *host, size_t bytes, int64_t 
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout, int rows) {
+lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (layout != LBM_LAYOUT_STRIDED && layout != LBM_LAYOUT_VECTOR) return fail(h, LBM_ERR_ARG, "bad layout");
-    if (rows < 1 || rows > 64 || (layout == LBM_LAYOUT_STRIDED && rows != 1))
-        return fail(h, LBM_ERR_ARG, "rows must be in [1, 64], and 1 for the strided layout");
-    const StepCfg c{block_x, nodes_per_thread, layout == LBM_LAYOUT_VECTOR ? 1 : 0, rows};
+    const StepCfg c{block_x, nodes_per_thread, layout == LBM_LAYOUT_VECTOR ? 1 : 0};
     if (!shape_ok(h, c)) {
         if (layout == LBM_LAYOUT_VECTOR && !vec_ok(h))
             return fail(h, LBM_ERR_ARG, "the vector layout takes no obstacle mask and Q * plane < 2^32");
@@ -895,15 +891,14 @@ lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_threa
 }
 
 lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread) {
-    return lbm_set_launch_layout(h, block_x, nodes_per_thread, LBM_LAYOUT_STRIDED, 1);
+    return lbm_set_launch_layout(h, block_x, nodes_per_thread, LBM_LAYOUT_STRIDED);
 }
 
-lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout, int *rows) {
+lbm_status lbm_get_launch(const lbm_handle *h, int *block_x, int *nodes_per_thread, int *layout) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (block_x) *block_x = h->cfg.bdx;
     if (nodes_per_thread) *nodes_per_thread = h->cfg.npt;
     if (layout) *layout = h->cfg.vec ? LBM_LAYOUT_VECTOR : LBM_LAYOUT_STRIDED;
-    if (rows) *rows = h->cfg.rows;
     return LBM_OK;
 }
 
@@ -919,15 +914,13 @@ lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (trials < 1) return fail(h, LBM_ERR_ARG, "trials must be >= 1");
     // strided shapes, then (without a mask) the vector widths
-    std::vector<StepCfg> shapes = {{32, 1, 0, 1},  {64, 1, 0, 1},  {64, 2, 0, 1}, {128, 1, 0, 1},
-                                   {128, 2, 0, 1}, {256, 1, 0, 1}, {256, 2, 0, 1}};
+    std::vector<StepCfg> shapes = {{32, 1, 0}, {64, 1, 0}, {64, 2, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {256, 2, 0}};
     if (vec_ok(h)) {
         const int wl = vec_width_lo(h->lattice, h->storage), wh = vec_width_hi(h->lattice, h->storage);
-        for (int bx : {32, 64, 128})
-            for (int rows : {1, 8}) {
-                shapes.push_back({bx, wl, 1, rows});
-                if (wh != wl) shapes.push_back({bx, wh, 1, rows});
-            }
+        for (int bx : {32, 64, 128}) {
+            shapes.push_back({bx, wl, 1});
+            if (wh != wl) shapes.push_back({bx, wh, 1});
+        }
     }
     cudaEvent_t e0, e1;
     LBM_CUDA(h, cudaEventCreate(&e0));
@@ -959,7 +952,7 @@ lbm_status lbm_autotune(lbm_handle *h, int trials, int *block_x, int *nodes_per_
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     lbm_status st = lbm_set_launch_layout(h, best_cfg.bdx, best_cfg.npt,
-                                          best_cfg.vec ? LBM_LAYOUT_VECTOR : LBM_LAYOUT_STRIDED, best_cfg.rows);
+                                          best_cfg.vec ? LBM_LAYOUT_VECTOR : LBM_LAYOUT_STRIDED);
     if (st != LBM_OK) return st;
     if (block_x) *block_x = best_cfg.bdx;
     if (nodes_per_thread) *nodes_per_thread = best_cfg.npt;

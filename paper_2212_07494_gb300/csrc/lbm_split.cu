@@ -454,10 +454,10 @@ lbm_status lbm_split_get_populations(lbm_split *s, double *f) {
     return LBM_OK;
 }
 
-lbm_status lbm_split_set_launch_layout(lbm_split *s, int block_x, int nodes_per_thread, int layout, int rows) {
+lbm_status lbm_split_set_launch_layout(lbm_split *s, int block_x, int nodes_per_thread, int layout) {
     if (!s) return sfail(nullptr, LBM_ERR_ARG, "split is NULL");
     for (int p = 0; p < s->parts; ++p) {
-        lbm_status st = lbm_set_launch_layout(s->h[p], block_x, nodes_per_thread, layout, rows);
+        lbm_status st = lbm_set_launch_layout(s->h[p], block_x, nodes_per_thread, layout);
         if (st != LBM_OK) return sfail(s, st, lbm_last_error(s->h[p]));
     }
     return LBM_OK;

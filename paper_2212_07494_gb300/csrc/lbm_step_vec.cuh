@@ -13,13 +13,11 @@
 // element out of its 32-bit word (the 2-byte types hold two per word), so
 // the shift costs no extra instruction per node.
 //
-// Rows are resolved once per row band: a source row across a periodic face
+// Rows are resolved once per block: a source row across a periodic face
 // wraps; a row next to a wall takes the per-node path (gather of
 // lbm_device.cuh with halfway bounce-back), as do the threads whose nodes
 // touch the row's ends (x = 0 or x = nx - 1, where the pull wraps or
-// bounces back).  Obstacle masks use the strided kernel k_step.  A block
-// runs through several row bands and loads the next while it collides the
-// current one.
+// bounces back).  Obstacle masks use the strided kernel k_step.
 //
 // Element offsets are 32-bit: the host launches this kernel only when
 // Q * plane < 2^32.
@@ -167,132 +165,112 @@ __device__ __forceinline__ bool row_src_halo(const KParams &p, int ax, int v, in
     return !(w[0] || w[1] || w[2]);
 }
 
-// the registers of one row band of a thread: its V nodes' vector of every
-// population and the edge element of the shifted ones
-template <int L, int ST, int V> struct VRow {
-    unsigned w[Lat<L>::Q][Vec<ST, V>::NW];
-    typename Bits<ST>::E edge[Lat<L>::Q];
-};
-
-// source rows of row band (y, z) for c = -1, 0, +1; false if a source lies
-// beyond a wall (the band then takes the per-node path)
-template <int D>
-__device__ __forceinline__ bool band_sources(const KParams &p, int y, int z, int (&ys)[3], int (&zs)[3]) {
-    bool ok = p.halo_ax == 1 ? row_src_halo(p, 1, y, ys) : row_src(y, p.ny, p.per[1], ys);
-    if (D == 3) ok = (p.halo_ax == 2 ? row_src_halo(p, 2, z, zs) : row_src(z, p.nz, p.per[2], zs)) && ok;
-    else zs[0] = zs[1] = zs[2] = 0;
-    return ok;
-}
-
-// the loads of one row band: every lane of the warp takes part (the edge
-// elements move by shuffle); threads past the row's end load nothing
-template <int L, int ST, int V>
-__device__ __forceinline__ void vrow_load(const KParams &p, const typename Store<ST>::T *__restrict__ fin,
-                                          const int (&ys)[3], const int (&zs)[3], int x0, bool on, bool fast,
-                                          int lane, VRow<L, ST, V> &r) {
-    typedef Vec<ST, V> VT;
-    constexpr int D = Lat<L>::D, Q = Lat<L>::Q, NW = VT::NW;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = Lat<L>::cx(i), cy = Lat<L>::cy(i), cz = Lat<L>::cz(i);
-        const unsigned src = (unsigned)i * (unsigned)p.plane +
-                             ((unsigned)(D == 3 ? zs[cz + 1] : 0) * (unsigned)p.ny + (unsigned)ys[cy + 1]) *
-                                 (unsigned)p.nxp + (unsigned)x0;
-        if (on) VT::load(fin + src, r.w[i]);
-        else
-#pragma unroll
-            for (int k = 0; k < NW; ++k) r.w[i][k] = 0u;
-        if (cx == 1) {
-            r.edge[i] = VT::from_prev_lane(r.w[i]);
-            if (lane == 0 && fast) r.edge[i] = VT::load1(fin + (src - 1u));
-        } else if (cx == -1) {
-            r.edge[i] = VT::from_next_lane(r.w[i]);
-            if (lane == 31 && fast) r.edge[i] = VT::load1(fin + (src + (unsigned)V));
-        } else {
-            r.edge[i] = 0;
-        }
-    }
-}
-
-// collide and store the V nodes of a thread whose sources are all in its
-// loaded row band
 template <int L, int COLL, int ST, int V>
-__device__ __forceinline__ void vrow_collide(const KParams &p, typename Store<ST>::T *__restrict__ fout, int y, int z,
-                                             int x0, const VRow<L, ST, V> &r) {
+__global__ void __launch_bounds__(256) k_step_vec(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+                                                  typename Store<ST>::T *__restrict__ fout) {
     typedef Vec<ST, V> VT;
     typedef typename Store<ST>::R R;
+    typedef typename Bits<ST>::E E;
     constexpr int D = Lat<L>::D, Q = Lat<L>::Q, NG = Grid<D>::N, NW = VT::NW;
+    const int y = blockIdx.y + (p.halo_ax == 1), z = blockIdx.z + (p.halo_ax == 2);
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4), omb = omega_bulk<R>(p);
     const bool per_node_force = p.force_kind == G_FIELD;
     R gx, gy, gz;
     if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
-    const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.nxp + (unsigned)x0;
-    unsigned o[Q][NW];
-    R held[Q];
-    if constexpr (sizeof(R) == 4 && V % 2 == 0) {
-        // nodes k and k + 1 collide together in packed FP32
+
+    int ys[3], zs[3] = {0, 0, 0};
+    bool row_ok = p.halo_ax == 1 ? row_src_halo(p, 1, y, ys) : row_src(y, p.ny, p.per[1], ys);
+    if (D == 3) row_ok = (p.halo_ax == 2 ? row_src_halo(p, 2, z, zs) : row_src(z, p.nz, p.per[2], zs)) && row_ok;
+    // fast: every source of the thread's V nodes is in this row band's
+    // interior or wraps across a periodic face of y or z
+    const bool fast = row_ok && x0 >= 1 && x0 + V <= p.nx - 1;
+
+    if (row_ok) {
+        // the whole block is one row band: every lane takes part in the loads
+        // and shuffles; threads past the row's end load nothing
+        const bool on = x0 < p.nx;
+        const int lane = threadIdx.x & 31;
+        unsigned w[Q][NW];
+        E edge[Q];
 #pragma unroll
-        for (int k = 0; k < V; k += 2) {
-            F2 G2[NG];
+        for (int i = 0; i < Q; ++i) {
+            const int cx = Lat<L>::cx(i), cy = Lat<L>::cy(i), cz = Lat<L>::cz(i);
+            const unsigned src = (unsigned)i * (unsigned)p.plane +
+                                 ((unsigned)(D == 3 ? zs[cz + 1] : 0) * (unsigned)p.ny + (unsigned)ys[cy + 1]) *
+                                     (unsigned)p.nxp + (unsigned)x0;
+            if (on) VT::load(fin + src, w[i]);
+            else
 #pragma unroll
-            for (int g = 0; g < NG; ++g) G2[g] = F2(0.0f);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int e0 = k - Lat<L>::cx(i), e1 = e0 + 1;   // elements of the source vector
-                const R v0 = (e0 < 0 || e0 >= V) ? dec<ST>(r.edge[i]) : VT::delem(r.w[i], e0);
-                const R v1 = (e1 < 0 || e1 >= V) ? dec<ST>(r.edge[i]) : VT::delem(r.w[i], e1);
-                G2[gpos<L>(i)] = F2::pair(v0, v1);
-            }
-            F2 gx2 = F2(gx), gy2 = F2(gy), gz2 = F2(gz);
-            if (per_node_force) {
-                R ax, ay, az, bx, by, bz;
-                load_force<L>(p, y, (long long)own + k, ax, ay, az);
-                load_force<L>(p, y, (long long)own + k + 1, bx, by, bz);
-                gx2 = F2::pair(ax, bx);
-                gy2 = F2::pair(ay, by);
-                gz2 = F2::pair(az, bz);
-            }
-            collide_any<L, COLL>(G2, gx2, gy2, gz2, F2(om2), F2(om3), F2(om4), F2(omb));
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                float lo, hi;
-                G2[gpos<L>(i)].split(lo, hi);
-                VT::put(o[i], k, lo, held[i]);
-                VT::put(o[i], k + 1, hi, held[i]);
+                for (int k = 0; k < NW; ++k) w[i][k] = 0u;
+            if (cx == 1) {
+                edge[i] = VT::from_prev_lane(w[i]);
+                if (lane == 0 && fast) edge[i] = VT::load1(fin + (src - 1u));
+            } else if (cx == -1) {
+                edge[i] = VT::from_next_lane(w[i]);
+                if (lane == 31 && fast) edge[i] = VT::load1(fin + (src + (unsigned)V));
+            } else {
+                edge[i] = 0;
             }
         }
-    } else {
+        if (fast) {
+            const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.nxp + (unsigned)x0;
+            unsigned o[Q][NW];
+            R held[Q];
+            if constexpr (sizeof(R) == 4 && V % 2 == 0) {
+                // nodes k and k + 1 collide together in packed FP32
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            R G[NG];
+                for (int k = 0; k < V; k += 2) {
+                    F2 G2[NG];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) G[g] = R(0);
+                    for (int g = 0; g < NG; ++g) G2[g] = F2(0.0f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int e = k - Lat<L>::cx(i);   // element of the source vector
-                G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(r.edge[i]) : VT::delem(r.w[i], e);
+                    for (int i = 0; i < Q; ++i) {
+                        const int e0 = k - Lat<L>::cx(i), e1 = e0 + 1;
+                        const R v0 = (e0 < 0 || e0 >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e0);
+                        const R v1 = (e1 < 0 || e1 >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e1);
+                        G2[gpos<L>(i)] = F2::pair(v0, v1);
+                    }
+                    F2 gx2 = F2(gx), gy2 = F2(gy), gz2 = F2(gz);
+                    if (per_node_force) {
+                        R ax, ay, az, bx, by, bz;
+                        load_force<L>(p, y, (long long)own + k, ax, ay, az);
+                        load_force<L>(p, y, (long long)own + k + 1, bx, by, bz);
+                        gx2 = F2::pair(ax, bx);
+                        gy2 = F2::pair(ay, by);
+                        gz2 = F2::pair(az, bz);
+                    }
+                    collide_any<L, COLL>(G2, gx2, gy2, gz2, F2(om2), F2(om3), F2(om4), F2(omb));
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        VT::put(o[i], k, G2[gpos<L>(i)].lo(), held[i]);
+                        VT::put(o[i], k + 1, G2[gpos<L>(i)].hi(), held[i]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    R G[NG];
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) G[g] = R(0);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int e = k - Lat<L>::cx(i);   // element of the source vector
+                        G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e);
+                    }
+                    if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
+                    collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
+                }
             }
-            if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
-            collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
+            for (int i = 0; i < Q; ++i) VT::store(fout + ((unsigned)i * (unsigned)p.plane + own), o[i]);
+            return;
         }
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) VT::store(fout + ((unsigned)i * (unsigned)p.plane + own), o[i]);
-}
-
-// the per-node path for a thread's V nodes of row band (y, z): rows next to a
-// wall, and the row ends (kept out of line: it runs rarely)
-template <int L, int COLL, int ST, int V>
-__device__ __noinline__ void vrow_slow(const KParams &p, const typename Store<ST>::T *__restrict__ fin,
-                                       typename Store<ST>::T *__restrict__ fout, int y, int z, int x0) {
-    typedef typename Store<ST>::R R;
-    constexpr int D = Lat<L>::D, Q = Lat<L>::Q, NG = Grid<D>::N;
-    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4), omb = omega_bulk<R>(p);
-    const bool per_node_force = p.force_kind == G_FIELD;
-    R gx, gy, gz;
-    if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
+    // the per-node path: rows next to a wall, and the row ends
+    if (x0 >= p.nx) return;
 #pragma unroll 1
     for (int k = 0; k < V; ++k) {
         const int x = x0 + k;
@@ -308,55 +286,13 @@ __device__ __noinline__ void vrow_slow(const KParams &p, const typename Store<ST
     }
 }
 
-// A block runs through `rows` consecutive row bands (y) of one z: each thread
-// loads the next band into a second set of registers while it collides the
-// current one, so its loads of a band are in flight during the arithmetic
-// of the previous band.
-template <int L, int COLL, int ST, int V>
-__global__ void __launch_bounds__(256) k_step_vec(const __grid_constant__ KParams p,
-                                                  const typename Store<ST>::T *__restrict__ fin,
-                                                  typename Store<ST>::T *__restrict__ fout, int rows) {
-    constexpr int D = Lat<L>::D;
-    const int z = blockIdx.z + (p.halo_ax == 2);
-    const int ylo = p.halo_ax == 1 ? 1 : 0;
-    const int yb = ylo + (int)blockIdx.y * rows;
-    const int ye = min(yb + rows, p.ny - ylo);
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int lane = threadIdx.x & 31;
-    const bool on = x0 < p.nx;
-    // every source of the thread's V nodes lies inside the row, so the band
-    // decides alone whether the thread takes the vector path
-    const bool xfast = x0 >= 1 && x0 + V <= p.nx - 1;
-    VRow<L, ST, V> A, B;
-    int ys[3], zs[3];
-    bool okA = band_sources<D>(p, yb, z, ys, zs), okB = false;
-    if (okA) vrow_load<L, ST, V>(p, fin, ys, zs, x0, on, xfast, lane, A);
-#pragma unroll 1
-    for (int y = yb; y < ye; y += 2) {
-        const bool hasB = y + 1 < ye;
-        okB = hasB && band_sources<D>(p, y + 1, z, ys, zs);
-        if (okB) vrow_load<L, ST, V>(p, fin, ys, zs, x0, on, xfast, lane, B);
-        if (okA && xfast) vrow_collide<L, COLL, ST, V>(p, fout, y, z, x0, A);
-        else if (on) vrow_slow<L, COLL, ST, V>(p, fin, fout, y, z, x0);
-        okA = y + 2 < ye && band_sources<D>(p, y + 2, z, ys, zs);
-        if (okA) vrow_load<L, ST, V>(p, fin, ys, zs, x0, on, xfast, lane, A);
-        if (hasB) {
-            if (okB && xfast) vrow_collide<L, COLL, ST, V>(p, fout, y + 1, z, x0, B);
-            else if (on) vrow_slow<L, COLL, ST, V>(p, fin, fout, y + 1, z, x0);
-        }
-    }
-}
-
 // host launcher of one (lattice, storage) pair: the collision and vector
 // width are template arguments, the supported widths listed by vec_widths
 template <int L, int ST> struct VecDispatch {
     template <int COLL, int V>
     static cudaError_t go(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
         typedef typename Store<ST>::T T;
-        dim3 grid = step_grid(p, cfg.bdx, V);
-        const int rows = cfg.rows > 1 ? cfg.rows : 1;
-        grid.y = (grid.y + rows - 1) / rows;
-        k_step_vec<L, COLL, ST, V><<<grid, cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout, rows);
+        k_step_vec<L, COLL, ST, V><<<step_grid(p, cfg.bdx, V), cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout);
         return cudaGetLastError();
     }
     template <int COLL>

@@ -4,9 +4,17 @@ FP32 accumulation) against the FP64 reference oracle/unet.py.
 Against the reference with BF16 storage emulated (weights, input and stored
 activations rounded where the kernels store them, FP64 arithmetic) the
 forward pass must agree to accumulation order: relative L2 < 1e-2.  The
-gradient also stores BF16 intermediates (dz per layer), which the reference
-does not round: cosine > 0.99 and relative L2 < 1e-1.  Against plain FP64 the
-BF16 network differs by the rounding of 18 layers (reported, bounded at 0.15)."""
+backward pass stores BF16 gradients too (each layer's dz, the input
+gradients of pooled and upsampled layers, the gated skip parts), which the
+reference rounds where the kernels store them: every layer's weight gradient
+and bias gradient, apart, to relative L2 < 2e-2.  A tap dropped from one
+layer's adjoint convolution moves some layer's gradient by 0.08 to 0.5
+(tests/test_oracle_unet.py), so the bar catches it.  What remains is FP32
+accumulation order and ReLU gates that flip where a pre-activation is within
+rounding of zero; the flips average out over many pixels, so the gradient
+shapes have at least a few hundred pixels at the coarsest level.  Against
+plain FP64 the BF16 network differs by the rounding of 18 layers (reported,
+bounded at 0.15)."""
 import numpy as np
 import pytest
 
@@ -64,7 +72,10 @@ def test_forward_matches_oracle(H, W, n, cin, periodic_x):
     net.close()
 
 
-@pytest.mark.parametrize("H,W,n,cin,periodic_x", [(24, 40, 2, 3, False), (24, 40, 2, 5, True),
+# 72 x 80 and 72 x 96 take the cp.async-fed convolutions at every level
+# (72 is neither a divisor nor a multiple of 128), 128 x 16 and 128 x 160 the
+# TMA-fed ones
+@pytest.mark.parametrize("H,W,n,cin,periodic_x", [(72, 80, 4, 5, True), (72, 96, 4, 3, False),
                                                   (128, 16, 8, 8, True), (128, 160, 8, 8, True)])
 def test_gradient_matches_oracle(H, W, n, cin, periodic_x):
     import torch
@@ -91,12 +102,13 @@ def test_gradient_matches_oracle(H, W, n, cin, periodic_x):
     print(f"loss {loss:.6g} vs {lr_:.6g}; grad cos {cos:.5f} rel {rel:.2e}; worst layer "
           f"{max(per, key=per.get)} {max(per.values()):.2e}; worst bias {max(bias, key=bias.get)} "
           f"{max(bias.values()):.2e}")
-    for name, r in bias.items():
-        assert r < 0.2, ("bias", name, r)
+    weights = {name: np.linalg.norm(g[wo:bo] - gr[wo:bo]) / np.linalg.norm(gr[wo:bo])
+               for name, ci, co, relu, wo, bo in sl}
+    for name in weights:
+        assert weights[name] < 2e-2, ("weights", name, weights[name])
+        assert bias[name] < 2e-2, ("bias", name, bias[name])
     assert abs(loss - lr_) / lr_ < 1e-2, (loss, lr_)
-    assert cos > 0.99 and rel < 1e-1, (cos, rel)
-    for name, r in per.items():
-        assert r < 0.2, (name, r)
+    assert cos > 0.9999 and rel < 2e-2, (cos, rel)
     net.close()
 
 
