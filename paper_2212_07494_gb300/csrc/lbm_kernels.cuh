@@ -19,8 +19,15 @@ __device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3
 // Fused pull-stream + collide + store for NPT nodes per thread along x
 // (strided by blockDim.x so every load instruction of a warp is a contiguous
 // row segment).  Loads for all NPT nodes are issued before any arithmetic.
+// In 2-byte storage the kernel is bound by instruction issue and latency:
+// at most 64 registers (launch bounds of 4 blocks of 256 threads) buys
+// occupancy (measured on GB300, 256^3 Taylor-Green in FP16: D3Q27 31.5
+// against 29.9 GLUPS, D3Q19 46.5 against 44.1); FP32 and FP64 keep the
+// compiler's choice.
+template <int ST> constexpr int step_min_blocks() { return ST == ST_F16 || ST == ST_BF16 ? 4 : 1; }
+
 template <int L, int COLL, int ST, bool MASK, int NPT>
-__global__ void __launch_bounds__(256) k_step(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+__global__ void __launch_bounds__(256, step_min_blocks<ST>()) k_step(const KParams p, const typename Store<ST>::T *__restrict__ fin,
                                               typename Store<ST>::T *__restrict__ fout) {
     typedef typename Store<ST>::R R;
     constexpr int NG = Grid<Lat<L>::D>::N;
