@@ -550,20 +550,17 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
     else fill_offsets<D3Q27>(kp);
 
-    // launch shape, from the measured rates on GB300: D2Q9 in 2-byte storage
-    // without an obstacle mask takes the vector kernel at its 16-byte width
-    // (where the strided kernel is bound by instruction issue); everything
-    // else the strided kernel, wide 2-D rows with two nodes per thread
+    // launch shape, from the measured rates on GB300: 2-byte storage without
+    // an obstacle mask takes the vector kernel (where the strided kernel is
+    // bound by instruction issue); everything else the strided kernel, wide
+    // 2-D rows with two nodes per thread
     h->cfg.bdx = D == 2 ? 128 : 64;
     h->cfg.npt = (D == 2 && d->nx >= 512) ? 2 : 1;
     h->cfg.vec = 0;
-    if (D == 3 && storage_bytes(d->storage) == 2) {
-        // 256^3, measured: D3Q27 best at 256 x 1, D3Q19 at 128 x 2 (nodes in pairs)
-        h->cfg.bdx = d->lattice == LBM_D3Q27 ? 256 : 128;
-        h->cfg.npt = d->lattice == LBM_D3Q27 ? 1 : 2;
-    }
     if (d->nx <= 64) h->cfg.bdx = 64;
-    if (D == 2 && storage_bytes(d->storage) == 2 && !h->mask && (long long)Q * plane < (1LL << 32)) {
+    if (storage_bytes(d->storage) == 2 && !h->mask && (long long)Q * plane < (1LL << 32)) {
+        // 2-byte storage without a mask: the vector layout at its wider width
+        // (D2Q9 8 nodes, 16 bytes; the 3-D lattices 4 nodes, 8 bytes)
         h->cfg.vec = 1;
         h->cfg.npt = vec_width_hi(d->lattice, d->storage);
         h->cfg.bdx = 32;

@@ -15,9 +15,11 @@
 //
 // Rows are resolved once per block: a source row across a periodic face
 // wraps; a row next to a wall takes the per-node path (gather of
-// lbm_device.cuh with halfway bounce-back), as do the threads whose nodes
-// touch the row's ends (x = 0 or x = nx - 1, where the pull wraps or
-// bounces back).  Obstacle masks use the strided kernel k_step.
+// lbm_device.cuh with halfway bounce-back).  At the row's ends the element
+// before or after a thread's vector wraps across a periodic x face (the
+// thread loads it from the other end of the row); with walls in x, and for
+// a last thread whose vector the row does not fill, the thread takes the
+// per-node path.  Obstacle masks use the strided kernel k_step.
 //
 // Element offsets are 32-bit: the host launches this kernel only when
 // Q * plane < 2^32.
@@ -190,7 +192,11 @@ __global__ void __launch_bounds__(256, vec_min_blocks<L>()) k_step_vec(const KPa
     if (D == 3) row_ok = (p.halo_ax == 2 ? row_src_halo(p, 2, z, zs) : row_src(z, p.nz, p.per[2], zs)) && row_ok;
     // fast: every source of the thread's V nodes is in this row band's
     // interior or wraps across a periodic face of y or z
-    const bool fast = row_ok && x0 >= 1 && x0 + V <= p.nx - 1;
+    // x: the thread's V nodes all lie in the row, and the elements just
+    // before and after them exist (inside the row, or across a periodic x
+    // face, where they wrap to the other end of the row)
+    const bool first = x0 == 0, last = x0 + V == p.nx;
+    const bool fast = row_ok && x0 + V <= p.nx && (p.per[0] || (!first && !last));
 
     if (row_ok) {
         // the whole block is one row band: every lane takes part in the loads
@@ -210,11 +216,13 @@ __global__ void __launch_bounds__(256, vec_min_blocks<L>()) k_step_vec(const KPa
 #pragma unroll
                 for (int k = 0; k < NW; ++k) w[i][k] = 0u;
             if (cx == 1) {
+                // element x0 - 1 (x = nx - 1 across the periodic face)
                 edge[i] = VT::from_prev_lane(w[i]);
-                if (lane == 0 && fast) edge[i] = VT::load1(fin + (src - 1u));
+                if ((lane == 0 || first) && fast) edge[i] = VT::load1(fin + (first ? src + (unsigned)(p.nx - 1) : src - 1u));
             } else if (cx == -1) {
+                // element x0 + V (x = 0 across the periodic face)
                 edge[i] = VT::from_next_lane(w[i]);
-                if (lane == 31 && fast) edge[i] = VT::load1(fin + (src + (unsigned)V));
+                if ((lane == 31 || last) && fast) edge[i] = VT::load1(fin + (last ? src - (unsigned)x0 : src + (unsigned)V));
             } else {
                 edge[i] = 0;
             }

@@ -25,11 +25,16 @@ TAU = {"BGK": (1.0, 1.0, 0.71, 1.0, 1.0), "SMRT": (1.0, 1.3, 0.63, 0.87, 1.1),
 COLLS = ["BGK", "SMRT", "SMRT_TRIM", "SMRT_FNEQ", "MRT_RAW"]
 # (shape, periodic): walls in y (and z) with a ragged row; walls at the row
 # ends with periodic y (z); a row of three warps plus a ragged tail with
-# everything periodic; a domain too short for any vector thread
+# everything periodic; a domain too short for any vector thread; rows that
+# every width fills, periodic in x, so the first and last threads of a row
+# take their edge elements across the periodic face
 CASES = {
-    "D2Q9": [((150, 37, 1), (1, 0, 1)), ((136, 20, 1), (0, 1, 1)), ((803, 6, 1), (1, 1, 1)), ((9, 5, 1), (1, 1, 1))],
-    "D3Q19": [((70, 9, 7), (1, 0, 0)), ((64, 6, 5), (0, 1, 1)), ((203, 4, 3), (1, 1, 1)), ((5, 4, 3), (1, 1, 1))],
-    "D3Q27": [((70, 9, 7), (1, 0, 0)), ((64, 6, 5), (0, 1, 1)), ((203, 4, 3), (1, 1, 1)), ((5, 4, 3), (1, 1, 1))],
+    "D2Q9": [((150, 37, 1), (1, 0, 1)), ((136, 20, 1), (0, 1, 1)), ((803, 6, 1), (1, 1, 1)), ((9, 5, 1), (1, 1, 1)),
+             ((256, 6, 1), (1, 1, 1))],
+    "D3Q19": [((70, 9, 7), (1, 0, 0)), ((64, 6, 5), (0, 1, 1)), ((203, 4, 3), (1, 1, 1)), ((5, 4, 3), (1, 1, 1)),
+              ((64, 4, 3), (1, 1, 1))],
+    "D3Q27": [((70, 9, 7), (1, 0, 0)), ((64, 6, 5), (0, 1, 1)), ((203, 4, 3), (1, 1, 1)), ((5, 4, 3), (1, 1, 1)),
+              ((64, 4, 3), (1, 1, 1))],
 }
 
 
@@ -54,7 +59,7 @@ def _state(lat, shape, seed, amp):
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D3Q19", "D3Q27"])
 @pytest.mark.parametrize("coll", COLLS)
-@pytest.mark.parametrize("case", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", [0, 1, 2, 3, 4])
 def test_vector_layout_f64_matches_oracle(lat, coll, case):
     """Three steps from an arbitrary state in FP64 at every vector width and
     two block widths: the oracle's populations to 1e-14."""
@@ -90,7 +95,7 @@ def test_vector_layout_reduced_storage(lat, storage, coll):
     against the strided kernel itself, which runs the same per-node
     arithmetic (nodes in pairs or alone, so fused multiply-adds may pair up
     differently): within a few FP32 roundings."""
-    for shape, periodic in CASES[lat][:3]:
+    for shape, periodic in CASES[lat][:3] + CASES[lat][4:]:
         f0, w = _state(lat, shape, 200, 0.05)
         gl, orc = make_pair(lat, _model(coll), shape, TAU[coll], storage, periodic, g=_g(lat), emulate_storage=True)
         orc.set_populations(f0)
@@ -151,9 +156,10 @@ def test_vector_layout_field_force_and_autotune(lat):
 
 def test_default_layouts():
     """A new handle starts with the layout measured faster on GB300: the
-    vector one for D2Q9 in 2-byte storage without a mask, else strided."""
+    vector one for 2-byte storage without a mask, else strided."""
     import paper_2212_07494_gb300 as P
-    for lat, st, vec in (("D2Q9", "F16", 1), ("D2Q9", "BF16", 1), ("D2Q9", "F32", 0), ("D3Q27", "F16", 0)):
+    for lat, st, vec in (("D2Q9", "F16", 1), ("D2Q9", "BF16", 1), ("D2Q9", "F32", 0), ("D3Q27", "F16", 1),
+                         ("D3Q19", "BF16", 1), ("D3Q27", "F32", 0)):
         shape = (256, 8, 1) if lat == "D2Q9" else (64, 4, 4)
         gl = P.Lattice(lat, "SMRT", shape, TAU["SMRT_TRIM"], st, (1, 1, 1))
         assert gl.launch()[2] == vec, (lat, st, gl.launch())
