@@ -218,10 +218,10 @@ typedef enum { LBM_LAYOUT_STRIDED = 0, LBM_LAYOUT_VECTOR = 1 } lbm_layout;
  * shape; in FP32 arithmetic the results can differ in the last bits between
  * shapes (the FP32 storage modes collide nodes two at a time in packed FP32
  * where a thread has two, which may pair fused multiply-adds differently
- * from one node at a time).  A new handle starts with the vector layout at
- * its wider width and 32 threads per block for FP16 or BF16 storage when the
- * layout applies, else with the strided layout (the faster ones on GB300).
- * LBM_ERR_ARG for a shape not listed. */
+ * from one node at a time).  A new handle starts with the shape measured
+ * fastest on GB300 for its lattice and storage: the vector layout at its
+ * wider width for FP16 and BF16 storage and for D3Q27 in FP32 when the layout
+ * applies, else the strided layout.  LBM_ERR_ARG for a shape not listed. */
 lbm_status lbm_set_launch_layout(lbm_handle *h, int block_x, int nodes_per_thread, int layout);
 /* lbm_set_launch_layout with LBM_LAYOUT_STRIDED (nodes_per_thread 1 or 2). */
 lbm_status lbm_set_launch(lbm_handle *h, int block_x, int nodes_per_thread);

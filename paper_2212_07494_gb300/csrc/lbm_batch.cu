@@ -109,14 +109,17 @@ __device__ __forceinline__ void gather_chan(const BatchChan &C, const typename S
     typedef typename Store<ST>::T T;
     const int plane = (int)C.plane;
     const int own = y * C.nxp + x;
-    const bool interior = x > 0 && x < C.nx - 1 && y > 0 && y < C.ny - 1;
+    // no wall or wrap along y, and x inside the row or periodic (the row's
+    // first and last nodes then take their x - c_x across the periodic face)
+    const bool interior = ((x > 0 && x < C.nx - 1) || C.per_x) && y > 0 && y < C.ny - 1;
+    const int xl = x == 0 ? C.nx - 1 : -1, xr = x == C.nx - 1 ? 1 - C.nx : 1;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = Lat<D2Q9>::cx(i), cy = Lat<D2Q9>::cy(i);
         int src;
         bool wall = false;
         if (interior) {
-            src = own - (cx + cy * C.nxp);
+            src = own + (cx == 1 ? xl : (cx == -1 ? xr : 0)) - cy * C.nxp;
         } else {
             int sx = x - cx, sy = y - cy;
             if (sx < 0) { if (C.per_x) sx += C.nx; else wall = true; }

@@ -180,17 +180,18 @@ struct KParams {
     // walls on that axis.
     int halo_ax, hg0, hgn;
     // per population i, relative to a node's element index:
-    long long doff[27];            // i*plane - (cx + cy*nxp + cz*nxp*ny): pull source
-    long long poff[27];            // i*plane: the node's own entry
-    int noff[27];                  // -(cx + cy*nxp + cz*nxp*ny): neighbour x - c_i
+    // per population i, relative to the element index of a node's x - c_x
+    // (the node itself, or its neighbour along x, wrapped on a periodic x):
+    long long doff[27];            // i*plane - (cy*nxp + cz*nxp*ny): pull source
+    long long poff[27];            // i*plane: the node's own entry (relative to the node)
+    int noff[27];                  // -(cy*nxp + cz*nxp*ny): neighbour x - c_i
 };
 
 // fill the per-population offsets of KParams for lattice L (host side)
 template <int L> inline void fill_offsets(KParams &p) {
     for (int i = 0; i < 27; ++i) p.doff[i] = p.poff[i] = p.noff[i] = 0;
     for (int i = 0; i < Lat<L>::Q; ++i) {
-        const long long nb = (long long)Lat<L>::cx(i) + (long long)Lat<L>::cy(i) * p.nxp +
-                             (long long)Lat<L>::cz(i) * p.nxp * p.ny;
+        const long long nb = (long long)Lat<L>::cy(i) * p.nxp + (long long)Lat<L>::cz(i) * p.nxp * p.ny;
         p.poff[i] = (long long)i * p.plane;
         p.doff[i] = p.poff[i] - nb;
         p.noff[i] = (int)(-nb);
@@ -774,15 +775,25 @@ __device__ __forceinline__ void gather(const KParams &p, const typename Store<ST
     const long long own = node_index(p, x, y, z);
 #pragma unroll
     for (int g = 0; g < Grid<D>::N; ++g) G[g] = R(0);
-    const bool interior = x > 0 && x < p.nx - 1 && inner(p, 1, y, p.ny) && (D == 2 || inner(p, 2, z, p.nz));
+    // no wall and no wrap along y and z, and x inside the row or periodic: the
+    // sources are fixed offsets from the node, from its left neighbour
+    // (c_x = +1) or its right one (c_x = -1), those wrapped across a periodic
+    // x face, so the first and last nodes of a row take this path too
+    const bool interior = ((x > 0 && x < p.nx - 1) || p.per[0]) && inner(p, 1, y, p.ny) &&
+                          (D == 2 || inner(p, 2, z, p.nz));
     if (interior) {
-        const typename Store<ST>::T *base = f + own;
+        const long long xl = x == 0 ? p.nx - 1 : -1;          // to x - 1
+        const long long xr = x == p.nx - 1 ? 1 - p.nx : 1;    // to x + 1
+        const typename Store<ST>::T *base = f + own, *basel = base + xl, *baser = base + xr;
 #pragma unroll
         for (int i = 0; i < Lat<L>::Q; ++i) {
-            if (MASK && i != 0 && p.solid[own + p.noff[i]] != 0)
+            const int cx = Lat<L>::cx(i);
+            const long long sx = cx == 1 ? xl : (cx == -1 ? xr : 0);
+            const typename Store<ST>::T *src = cx == 1 ? basel : (cx == -1 ? baser : base);
+            if (MASK && i != 0 && p.solid[own + sx + p.noff[i]] != 0)
                 G[gpos<L>(i)] = Store<ST>::ld(base + p.poff[opp<L>(i)]);
             else
-                G[gpos<L>(i)] = Store<ST>::ld(base + p.doff[i]);
+                G[gpos<L>(i)] = Store<ST>::ld(src + p.doff[i]);
         }
         return;
     }

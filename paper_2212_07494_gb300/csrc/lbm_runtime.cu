@@ -550,20 +550,26 @@ lbm_status lbm_create(const lbm_desc *d, lbm_handle **out) {
     else if (d->lattice == LBM_D3Q19) fill_offsets<D3Q19>(kp);
     else fill_offsets<D3Q27>(kp);
 
-    // launch shape, from the measured rates on GB300: 2-byte storage without
-    // an obstacle mask takes the vector kernel (where the strided kernel is
-    // bound by instruction issue); everything else the strided kernel, wide
-    // 2-D rows with two nodes per thread
+    // launch shape, from the measured rates on GB300 (D2Q9 4096^2, 256^3):
+    // without an obstacle mask, 2-byte storage and D3Q27 in FP32 take the
+    // vector kernel; everything else the strided kernel, wide 2-D rows and
+    // D3Q19 in FP32 with two nodes per thread
     h->cfg.bdx = D == 2 ? 128 : 64;
     h->cfg.npt = (D == 2 && d->nx >= 512) ? 2 : 1;
     h->cfg.vec = 0;
     if (d->nx <= 64) h->cfg.bdx = 64;
-    if (storage_bytes(d->storage) == 2 && !h->mask && (long long)Q * plane < (1LL << 32)) {
+    if (D == 3 && d->storage == LBM_F32 && d->lattice == LBM_D3Q19) h->cfg.npt = 2;
+    const bool vec_fits = !h->mask && (long long)Q * plane < (1LL << 32);
+    if (vec_fits && storage_bytes(d->storage) == 2) {
         // 2-byte storage without a mask: the vector layout at its wider width
         // (D2Q9 8 nodes, 16 bytes; the 3-D lattices 4 nodes, 8 bytes)
         h->cfg.vec = 1;
         h->cfg.npt = vec_width_hi(d->lattice, d->storage);
-        h->cfg.bdx = 32;
+        h->cfg.bdx = d->lattice == LBM_D3Q27 ? 64 : 32;
+    } else if (vec_fits && d->lattice == LBM_D3Q27 && d->storage == LBM_F32) {
+        h->cfg.vec = 1;
+        h->cfg.npt = vec_width_hi(d->lattice, d->storage);
+        h->cfg.bdx = 128;
     }
     h->graph_steps = 64;
 

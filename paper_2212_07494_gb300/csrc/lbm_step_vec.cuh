@@ -167,14 +167,19 @@ __device__ __forceinline__ bool row_src_halo(const KParams &p, int ax, int v, in
     return !(w[0] || w[1] || w[2]);
 }
 
-// D2Q9: at most 64 registers (launch bounds of 4 blocks of 256 threads), so
-// more warps keep loads in flight; measured on GB300 at 4096^2 in FP16
-// storage: 147 GLUPS against 141 with the compiler's own choice of about 94
-// registers.  The 3-D lattices keep the compiler's choice.
-template <int L> constexpr int vec_min_blocks() { return L == D2Q9 ? 4 : 1; }
+// Register caps (launch bounds of n blocks of 256 threads: at most
+// 65536 / (256 n) registers, 64 for n = 4, 85 for n = 3, 128 for n = 2), so
+// that more warps keep loads in flight.  Measured on GB300 (D2Q9 4096^2 Kolmogorov, 256^3
+// Taylor-Green): D2Q9 2-byte at 64 registers 147 against 141 GLUPS; D3Q27
+// and D3Q19 2-byte at 128 registers 49.8 and 70.0 against 36.1 and 49.6;
+// D3Q27 FP32 at 85 registers 32.2 against 28.1.  FP64 keeps the compiler's
+// choice.
+template <int L, int ST> constexpr int vec_min_blocks() {
+    return L == D2Q9 ? (ST == ST_F64 ? 1 : 4) : (ST == ST_F64 ? 1 : (ST == ST_F32 ? 3 : 2));
+}
 
 template <int L, int COLL, int ST, int V>
-__global__ void __launch_bounds__(256, vec_min_blocks<L>()) k_step_vec(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+__global__ void __launch_bounds__(256, vec_min_blocks<L, ST>()) k_step_vec(const KParams p, const typename Store<ST>::T *__restrict__ fin,
                                                   typename Store<ST>::T *__restrict__ fout) {
     typedef Vec<ST, V> VT;
     typedef typename Store<ST>::R R;

@@ -156,10 +156,11 @@ def test_vector_layout_field_force_and_autotune(lat):
 
 def test_default_layouts():
     """A new handle starts with the layout measured faster on GB300: the
-    vector one for 2-byte storage without a mask, else strided."""
+    vector one for 2-byte storage and D3Q27 in FP32 without a mask, else
+    strided."""
     import paper_2212_07494_gb300 as P
     for lat, st, vec in (("D2Q9", "F16", 1), ("D2Q9", "BF16", 1), ("D2Q9", "F32", 0), ("D3Q27", "F16", 1),
-                         ("D3Q19", "BF16", 1), ("D3Q27", "F32", 0)):
+                         ("D3Q19", "BF16", 1), ("D3Q27", "F32", 1), ("D3Q19", "F32", 0), ("D2Q9", "F64", 0)):
         shape = (256, 8, 1) if lat == "D2Q9" else (64, 4, 4)
         gl = P.Lattice(lat, "SMRT", shape, TAU["SMRT_TRIM"], st, (1, 1, 1))
         assert gl.launch()[2] == vec, (lat, st, gl.launch())
