@@ -85,6 +85,7 @@ def parse():
     ap.add_argument("--tol-train", type=float, default=1e-8)
     ap.add_argument("--plain-stride", type=int, default=16, help="batch: every n-th channel runs the plain solver")
     ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--max-steps", type=int, default=50_000_000, help="batch: step budget per channel")
     ap.add_argument("--K", type=int, default=1000)
     return ap.parse_args()
 
@@ -546,8 +547,9 @@ def run_batch(args, ws, rank, local):
     time.sleep(0.4)
     sampler.mark(0)
     t0 = time.perf_counter()
-    status, steps, st, r = b.run_to_steady(args.tol, args.K, max_steps=50_000_000)
+    status, steps, st, r = b.run_to_steady(args.tol, args.K, max_steps=args.max_steps)
     t_batch = time.perf_counter() - t0
+    print(f"batch: {t_batch:.1f} s, status {status}, steps max {int(steps.max())}", file=sys.stderr, flush=True)
     sampler.mark(1)
     sampler.stop()
     clocks = sampler.summary()
@@ -565,10 +567,11 @@ def run_batch(args, ws, rank, local):
         while True:
             rr = lat.residual(args.K)
             n += args.K
-            if rr <= args.tol or n >= 50_000_000:
+            if rr <= args.tol or n >= args.max_steps:
                 break
         _, u_plain, _ = lat.moments()
         t_plain += time.perf_counter() - t1
+        print(f"plain channel {i}: {n} steps, r {rr:.3g}, {time.perf_counter() - t1:.1f} s", file=sys.stderr, flush=True)
         lat.close()
         plain_steps.append(n)
         _, u_b = b.moments(i)

@@ -122,9 +122,11 @@ def test_tail_handoff_matches_the_kernel_alone(storage):
     final fields in FP64 (only the residual's summation order differs); in
     FP32 the plain and batched kernels round differently (see
     test_batch_channels_with_obstacles; the batch collides its nodes in
-    packed pairs, a plain lattice of this size one at a time), so a residual
-    near tol may stop a check interval or two apart, with fields equal to
-    FP32 noise.  Handoff 1000
+    packed pairs, a plain lattice of this size one at a time), so the
+    residual of a channel that creeps down to tol over tens of thousands of
+    steps crosses it at a slightly different check: a few per cent of its
+    steps apart (two intervals at least), with fields equal to FP32 noise.
+    Handoff 1000
     hands every channel over after its first step, 8 only the last eight, 0
     never."""
     import paper_2212_07494_gb300 as P
@@ -146,7 +148,8 @@ def test_tail_handoff_matches_the_kernel_alone(storage):
             assert np.array_equal(res[ho][0], res[0][0]), (ho, res[ho][0] - res[0][0])
             assert np.allclose(res[ho][2], res[0][2], rtol=1e-6), ho
         else:
-            assert np.abs(res[ho][0] - res[0][0]).max() <= 2 * K, (ho, res[ho][0] - res[0][0])
+            gap = np.abs(res[ho][0] - res[0][0])
+            assert np.all(gap <= np.maximum(2 * K, 0.05 * res[0][0])), (ho, res[ho][0] - res[0][0])
         for i in range(len(chans)):
             # a channel that stopped an interval or two apart is at another
             # point of its slow approach to the steady state
