@@ -114,8 +114,8 @@ def job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
 
 
 # the sources that define the D2Q9 stream-collide kernel and its launch
-STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h", "lbm_inst_d2q9.cu", "lbm_step_vec.cuh",
-                "lbm_vec_d2q9_f32.cu")
+STEP_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_internal.h", "lbm_f32x2.cuh", "lbm_inst_d2q9.cu",
+                "lbm_step_vec.cuh", "lbm_vec_d2q9_f32.cu")
 
 
 def kernel_sources_sha():

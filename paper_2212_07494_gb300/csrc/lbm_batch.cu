@@ -158,6 +158,27 @@ __device__ __forceinline__ void block_sum_batch(double (&v)[2]) {
     }
 }
 
+// One FP32 node of a channel on the pair instructions (both lanes), out of
+// line: the node of a pass whose partner lies past the tile, so that the
+// kernel keeps one inlined pair collision per collision kind
+template <int COLL>
+__device__ __noinline__ void batch_node_alone(const BatchChan C, const float *fin, float *fout,
+                                              const unsigned char *solid, int x, int y, float gx, float gy,
+                                              float om2, float om3, float om4, bool trim) {
+    float G[9];
+    gather_chan<ST_F32>(C, fin, solid, x, y, G);
+    F2 G2[9];
+#pragma unroll
+    for (int g = 0; g < 9; ++g) G2[g] = F2(G[g]);
+    const F2 gx2 = F2(gx), gy2 = F2(gy), z2 = F2(0.0f);
+    if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+    else if (COLL == SMRT) collide_smrt<D2Q9>(G2, gx2, gy2, z2, F2(om2), F2(om3), F2(om4), F2(om2));
+    else collide_bgk<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+    float *dst = fout + (y * C.nxp + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<ST_F32>::st(dst + i * (int)C.plane, G2[gpos<D2Q9>(i)].lo());
+}
+
 // tiles per step for a channel of nx x ny with `active` nodes still running
 __host__ __device__ inline int tiles_for(int nx, int ny, long long active, int grid, int tile_min, int tile_max) {
     long long target = active / (2LL * grid);
@@ -321,8 +342,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                 if constexpr (ST == ST_F32) {
                     if (on[0] && on[1]) {
                         // both nodes: one collision in packed FP32, as k_step
-                        // pairs its nodes, so that a channel evolves with the
-                        // same arithmetic here and alone
+                        // pairs its nodes
                         F2 G2[9];
 #pragma unroll
                         for (int g = 0; g < 9; ++g) G2[g] = F2::pair(G[0][g], G[1][g]);
@@ -336,20 +356,24 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                             Store<ST>::st(d0 + i * (int)C.plane, G2[gpos<D2Q9>(i)].lo());
                             Store<ST>::st(d1 + i * (int)C.plane, G2[gpos<D2Q9>(i)].hi());
                         }
-                        on[0] = on[1] = false;
+                    } else {
+                        // a node alone (the tile's last pass): out of line
+                        if (on[0]) batch_node_alone<COLL>(C, fin, fout, solid, xs[0], ys[0], gx, gy, om2, om3, om4, trim);
+                        if (on[1]) batch_node_alone<COLL>(C, fin, fout, solid, xs[1], ys[1], gx, gy, om2, om3, om4, trim);
                     }
-                }
+                } else {
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (!on[k]) continue;
-                    const int x = xs[k], y = ys[k];
-                    // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it
-                    if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
-                    else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
-                    else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
-                    T *dst = fout + (y * C.nxp + x);
+                    for (int k = 0; k < 2; ++k) {
+                        if (!on[k]) continue;
+                        const int x = xs[k], y = ys[k];
+                        // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it
+                        if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
+                        else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
+                        else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
+                        T *dst = fout + (y * C.nxp + x);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[k][gpos<D2Q9>(i)]);
+                        for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[k][gpos<D2Q9>(i)]);
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {

@@ -4,13 +4,20 @@
 // for two nodes' worth of FP32 arithmetic.  The collision templates of
 // lbm_device.cuh take it as their arithmetic type R, so one call collides
 // two nodes; each lane of the pair gets exactly the IEEE round-to-nearest
-// result a scalar float would.
+// result of the corresponding scalar instruction.
 //
 // A product is kept unevaluated until it is used (F2Mul), so that a product
-// added to or subtracted from a value becomes one fused multiply-add, the
-// contraction the compiler makes for scalar floats.  Which products fuse
-// can differ from the scalar code's choice, so the two paths agree to FP32
-// rounding, not bit for bit.
+// added to or subtracted from a value becomes one fused multiply-add.  Which
+// products fuse can differ from the compiler's choice for plain floats, so
+// a node collided alone also runs through F2, with its values in both lanes
+// (collide_one): every FP32 node then gets the same bits alone or paired,
+// whatever the launch shape pairs it with.  That matters beyond
+// reproducibility: a periodic row whose nodes all run one arithmetic keeps
+// its translation symmetry exactly, whereas nodes rounding two ways break it
+// at the last bit and the slow shear modes along the row keep FP32 noise
+// alive, so a run to a tight steady-state residual stalls (measured: a
+// 502 x 126 channel that settles in 50,000 steps stalled at r_K = 2e-8 with
+// half its nodes paired and half alone).
 #pragma once
 
 namespace lbm {
@@ -91,7 +98,14 @@ __device__ __forceinline__ F2 &operator+=(F2 &a, F2Mul m) { return a = f2_fma(m.
 __device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { return a = f2_sub(a, b); }
 __device__ __forceinline__ F2 &operator*=(F2 &a, F2 b) { return a = f2_mul(a, b); }
 
-// a / b per lane, each correctly rounded (the IEEE quotient)
-__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2::pair(a.lo() / b.lo(), a.hi() / b.hi()); }
+// the IEEE quotient of one lane (div.rn.f32; inline PTX like the pair
+// instructions, so that the compiler neither folds nor rewrites it)
+__device__ __forceinline__ float f1_div(float a, float b) {
+    float r;
+    asm("div.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+// a / b per lane, each correctly rounded
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2::pair(f1_div(a.lo(), b.lo()), f1_div(a.hi(), b.hi())); }
 
 }  // namespace lbm

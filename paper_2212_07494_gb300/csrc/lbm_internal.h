@@ -1,5 +1,6 @@
-// lbm_internal.h -- host-side interface between the C ABI runtime and the
-// per-lattice kernel launchers.  Plain CUDA runtime types only.
+// lbm_internal.h -- interface between the C ABI runtime and the
+// per-lattice kernel launchers, and the collision dispatch that every step
+// kernel shares (collide_any, collide_one).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -9,6 +10,36 @@
 #include "lbm_f32x2.cuh"
 
 namespace lbm {
+
+// the collision selected by COLL on one node's grid G (or two nodes' with F2)
+template <int L, int COLL, typename R>
+__device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
+    if constexpr (COLL == SMRT) collide_smrt<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<L>(G, gx, gy, gz, om2);
+    else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G, gx, gy, gz, om2, om3, om4, omb);
+    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<L>(G, gx, gy, gz, om2, om3, om4);
+    else collide_bgk<L>(G, gx, gy, gz, om2);
+}
+
+// One node's collision.  In FP32 the node runs through the pair type with
+// its values in both lanes (lbm_f32x2.cuh) and keeps the first: the same
+// template instantiation and the same instructions as two paired nodes, so
+// a node's result does not depend on whether the launch shape collides it
+// alone or paired.  FP64 as written.
+template <int L, int COLL, typename R>
+__device__ __forceinline__ void collide_one(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
+    if constexpr (sizeof(R) == 4) {
+        constexpr int NG = Grid<Lat<L>::D>::N;
+        F2 H[NG];
+#pragma unroll
+        for (int g = 0; g < NG; ++g) H[g] = F2(G[g]);
+        collide_any<L, COLL>(H, F2(gx), F2(gy), F2(gz), F2(om2), F2(om3), F2(om4), F2(omb));
+#pragma unroll
+        for (int g = 0; g < NG; ++g) G[g] = H[g].lo();
+    } else {
+        collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+    }
+}
 
 // number of doubles each moments block writes to the partial-sum scratch:
 // {sum (rho - 1), Px, Py, Pz, residual numerator, residual denominator,

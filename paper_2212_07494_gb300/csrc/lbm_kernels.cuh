@@ -7,15 +7,6 @@
 
 namespace lbm {
 
-template <int L, int COLL, typename R>
-__device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3, R om4, R omb) {
-    if constexpr (COLL == SMRT) collide_smrt<L>(G, gx, gy, gz, om2, om3, om4, omb);
-    else if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<L>(G, gx, gy, gz, om2);
-    else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G, gx, gy, gz, om2, om3, om4, omb);
-    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<L>(G, gx, gy, gz, om2, om3, om4);
-    else collide_bgk<L>(G, gx, gy, gz, om2);
-}
-
 // Fused pull-stream + collide + store for NPT nodes per thread along x
 // (strided by blockDim.x so every load instruction of a warp is a contiguous
 // row segment).  Loads for all NPT nodes are issued before any arithmetic.
@@ -26,8 +17,28 @@ __device__ __forceinline__ void collide_any(R *G, R gx, R gy, R gz, R om2, R om3
 // compiler's choice.
 template <int ST> constexpr int step_min_blocks() { return ST == ST_F16 || ST == ST_BF16 ? 4 : 1; }
 
+// One node on the pair instructions (collide_one), out of line: the node of
+// a two-node thread whose partner is past the row's end or solid, so that
+// the kernel keeps one inlined collision (the pair's).  The kernel's
+// parameters are __grid_constant__: the reference copies nothing.
+template <int L, int COLL, int ST, bool MASK>
+__device__ __noinline__ void step_node_alone(const KParams &p, const typename Store<ST>::T *__restrict__ fin,
+                                             typename Store<ST>::T *__restrict__ fout, int x, int y, int z) {
+    typedef typename Store<ST>::R R;
+    constexpr int NG = Grid<Lat<L>::D>::N;
+    R G[NG];
+    gather<L, ST, MASK>(p, fin, x, y, z, G);
+    const long long own = node_index(p, x, y, z);
+    R gx, gy, gz;
+    load_force<L>(p, y, own, gx, gy, gz);
+    collide_one<L, COLL>(G, gx, gy, gz, omega<R>(p, 2), omega<R>(p, 3), omega<R>(p, 4), omega_bulk<R>(p));
+    typename Store<ST>::T *dst = fout + own;
+#pragma unroll
+    for (int i = 0; i < Lat<L>::Q; ++i) Store<ST>::st(dst + p.poff[i], G[gpos<L>(i)]);
+}
+
 template <int L, int COLL, int ST, bool MASK, int NPT>
-__global__ void __launch_bounds__(256, step_min_blocks<ST>()) k_step(const KParams p, const typename Store<ST>::T *__restrict__ fin,
+__global__ void __launch_bounds__(256, step_min_blocks<ST>()) k_step(const __grid_constant__ KParams p, const typename Store<ST>::T *__restrict__ fin,
                                               typename Store<ST>::T *__restrict__ fout) {
     typedef typename Store<ST>::R R;
     constexpr int NG = Grid<Lat<L>::D>::N;
@@ -47,8 +58,8 @@ __global__ void __launch_bounds__(256, step_min_blocks<ST>()) k_step(const KPara
     const bool per_node_force = p.force_kind == G_FIELD;
     if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
     if constexpr (NPT == 2 && sizeof(R) == 4) {
-        // both nodes present: one collision for the pair in packed FP32
         if (act[0] && act[1]) {
+            // both nodes: one collision for the pair in packed FP32
             const long long own0 = node_index(p, x0, y, z), own1 = own0 + blockDim.x;
             F2 G2[NG];
 #pragma unroll
@@ -71,21 +82,21 @@ __global__ void __launch_bounds__(256, step_min_blocks<ST>()) k_step(const KPara
             }
             return;
         }
-    }
+        // a node whose partner is past the row's end or solid: out of line
+        if (act[0]) step_node_alone<L, COLL, ST, MASK>(p, fin, fout, x0, y, z);
+        if (act[1]) step_node_alone<L, COLL, ST, MASK>(p, fin, fout, x0 + (int)blockDim.x, y, z);
+    } else {
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        if (!act[k]) continue;
-        const int x = x0 + k * blockDim.x;
-        const long long own = node_index(p, x, y, z);
-        if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
-        if (COLL == SMRT) collide_smrt<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
-        else if (COLL == SMRT_TRIM) collide_smrt_trim<L>(G[k], gx, gy, gz, om2);
-        else if (COLL == SMRT_FNEQ) collide_smrt_fneq<L>(G[k], gx, gy, gz, om2, om3, om4, omb);
-        else if (COLL == MRT_RAW) collide_mrt_raw<L>(G[k], gx, gy, gz, om2, om3, om4);
-        else collide_bgk<L>(G[k], gx, gy, gz, om2);
-        typename Store<ST>::T *dst = fout + own;
+        for (int k = 0; k < NPT; ++k) {
+            if (!act[k]) continue;
+            const int x = x0 + k * blockDim.x;
+            const long long own = node_index(p, x, y, z);
+            if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
+            collide_one<L, COLL>(G[k], gx, gy, gz, om2, om3, om4, omb);
+            typename Store<ST>::T *dst = fout + own;
 #pragma unroll
-        for (int i = 0; i < Lat<L>::Q; ++i) Store<ST>::st(dst + p.poff[i], G[k][gpos<L>(i)]);
+            for (int i = 0; i < Lat<L>::Q; ++i) Store<ST>::st(dst + p.poff[i], G[k][gpos<L>(i)]);
+        }
     }
 }
 

@@ -178,7 +178,73 @@ template <int L, int ST> constexpr int vec_min_blocks() {
     return L == D2Q9 ? (ST == ST_F64 ? 1 : 4) : (ST == ST_F64 ? 1 : (ST == ST_F32 ? 3 : 2));
 }
 
+// The per-node path of k_step_vec: rows next to a wall, and the row ends
+// (the SLOW launch).
 template <int L, int COLL, int ST, int V>
+__device__ __forceinline__ void step_vec_nodes(const KParams &p, const typename Store<ST>::T *__restrict__ fin,
+                                            typename Store<ST>::T *__restrict__ fout, int x0, int y, int z) {
+    typedef typename Store<ST>::R R;
+    constexpr int D = Lat<L>::D, Q = Lat<L>::Q, NG = Grid<D>::N;
+    const R om2 = omega<R>(p, 2), om3 = omega<R>(p, 3), om4 = omega<R>(p, 4), omb = omega_bulk<R>(p);
+    const bool per_node_force = p.force_kind == G_FIELD;
+    R gx = R(0), gy = R(0), gz = R(0);
+    if (!per_node_force) load_force<L>(p, y, 0, gx, gy, gz);
+    if constexpr (sizeof(R) == 4) {
+        // two of the thread's nodes per collision in packed FP32, gathered
+        // node by node; a lone last node fills both lanes and only its lane
+        // is stored (every node on the pair instructions)
+#pragma unroll 1
+        for (int k = 0; k < V; k += 2) {
+            const int xa = x0 + k;
+            if (xa >= p.nx) break;
+            const bool two = k + 1 < V && xa + 1 < p.nx;
+            R Ga[NG], Gb[NG];
+            gather<L, ST, false>(p, fin, xa, y, z, Ga);
+            if (two) gather<L, ST, false>(p, fin, xa + 1, y, z, Gb);
+            F2 G2[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) G2[g] = F2::pair(Ga[g], two ? Gb[g] : Ga[g]);
+            const long long own = node_index(p, xa, y, z);
+            F2 gx2 = F2(gx), gy2 = F2(gy), gz2 = F2(gz);
+            if (per_node_force) {
+                R ax, ay, az, bx, by, bz;
+                load_force<L>(p, y, own, ax, ay, az);
+                load_force<L>(p, y, two ? own + 1 : own, bx, by, bz);
+                gx2 = F2::pair(ax, bx);
+                gy2 = F2::pair(ay, by);
+                gz2 = F2::pair(az, bz);
+            }
+            collide_any<L, COLL>(G2, gx2, gy2, gz2, F2(om2), F2(om3), F2(om4), F2(omb));
+            typename Store<ST>::T *dst = fout + own;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                Store<ST>::st(dst + p.poff[i], G2[gpos<L>(i)].lo());
+                if (two) Store<ST>::st(dst + 1 + p.poff[i], G2[gpos<L>(i)].hi());
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int k = 0; k < V; ++k) {
+            const int x = x0 + k;
+            if (x >= p.nx) break;
+            R G[NG];
+            gather<L, ST, false>(p, fin, x, y, z, G);
+            const long long own = node_index(p, x, y, z);
+            if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
+            collide_one<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+            typename Store<ST>::T *dst = fout + own;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Store<ST>::st(dst + p.poff[i], G[gpos<L>(i)]);
+        }
+    }
+}
+
+// SLOW = false: the threads whose nodes take the vector path ("fast"); the
+// others return.  SLOW = true: the other nodes (rows next to a wall, the
+// row ends), node by node, in a launch of their own that the host adds only
+// when the domain has such nodes.  Two kernels, so that the per-node path's
+// collision and register needs stay out of the vector path's allocation.
+template <int L, int COLL, int ST, int V, bool SLOW>
 __global__ void __launch_bounds__(256, vec_min_blocks<L, ST>()) k_step_vec(const KParams p, const typename Store<ST>::T *__restrict__ fin,
                                                   typename Store<ST>::T *__restrict__ fout) {
     typedef Vec<ST, V> VT;
@@ -202,6 +268,10 @@ __global__ void __launch_bounds__(256, vec_min_blocks<L, ST>()) k_step_vec(const
     // face, where they wrap to the other end of the row)
     const bool first = x0 == 0, last = x0 + V == p.nx;
     const bool fast = row_ok && x0 + V <= p.nx && (p.per[0] || (!first && !last));
+    if constexpr (SLOW) {
+        if (!fast && x0 < p.nx) step_vec_nodes<L, COLL, ST, V>(p, fin, fout, x0, y, z);
+        return;
+    }
 
     if (row_ok) {
         // the whole block is one row band: every lane takes part in the loads
@@ -278,7 +348,7 @@ __global__ void __launch_bounds__(256, vec_min_blocks<L, ST>()) k_step_vec(const
                         G[gpos<L>(i)] = (e < 0 || e >= V) ? dec<ST>(edge[i]) : VT::delem(w[i], e);
                     }
                     if (per_node_force) load_force<L>(p, y, (long long)own + k, gx, gy, gz);
-                    collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
+                    collide_one<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
 #pragma unroll
                     for (int i = 0; i < Q; ++i) VT::put(o[i], k, G[gpos<L>(i)], held[i]);
                 }
@@ -288,31 +358,29 @@ __global__ void __launch_bounds__(256, vec_min_blocks<L, ST>()) k_step_vec(const
             return;
         }
     }
-    // the per-node path: rows next to a wall, and the row ends
-    if (x0 >= p.nx) return;
-#pragma unroll 1
-    for (int k = 0; k < V; ++k) {
-        const int x = x0 + k;
-        if (x >= p.nx) break;
-        R G[NG];
-        gather<L, ST, false>(p, fin, x, y, z, G);
-        const long long own = node_index(p, x, y, z);
-        if (per_node_force) load_force<L>(p, y, own, gx, gy, gz);
-        collide_any<L, COLL>(G, gx, gy, gz, om2, om3, om4, omb);
-        typename Store<ST>::T *dst = fout + own;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Store<ST>::st(dst + p.poff[i], G[gpos<L>(i)]);
-    }
+    // the other nodes are the SLOW launch's
 }
 
 // host launcher of one (lattice, storage) pair: the collision and vector
 // width are template arguments, the supported widths listed by vec_widths
 template <int L, int ST> struct VecDispatch {
+    // a node can leave the vector path only across a wall (some axis not
+    // periodic) or at a ragged row end (nx not a multiple of V); otherwise
+    // the per-node launch would find nothing to do and is left out
+    template <int V> static bool has_slow_nodes(const KParams &p) {
+        return !(p.per[0] && p.per[1] && (Lat<L>::D == 2 || p.per[2]) && p.nx % V == 0);
+    }
     template <int COLL, int V>
     static cudaError_t go(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {
         typedef typename Store<ST>::T T;
-        k_step_vec<L, COLL, ST, V><<<step_grid(p, cfg.bdx, V), cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout);
-        return cudaGetLastError();
+        const dim3 grid = step_grid(p, cfg.bdx, V);
+        k_step_vec<L, COLL, ST, V, false><<<grid, cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && has_slow_nodes<V>(p)) {
+            k_step_vec<L, COLL, ST, V, true><<<grid, cfg.bdx, 0, s>>>(p, (const T *)fin, (T *)fout);
+            e = cudaGetLastError();
+        }
+        return e;
     }
     template <int COLL>
     static cudaError_t by_width(StepCfg cfg, const KParams &p, const void *fin, void *fout, cudaStream_t s) {

@@ -96,13 +96,13 @@ def test_split_force_kinds_and_layouts(kind, layout):
     whole, split = _pair(3, "D2Q9", "MRT_RAW", shape, TAU_G, "F32", (1, 1, 1), g=g, force_kind=kind,
                          rho0=rho0, u0=u0)
     lo, hi = P.lbm_launch_widths("D2Q9", "F32")
-    # the same shape on both (in FP32 nodes pair up by the shape)
+    # other shapes on the two sides: a node rounds alike alone or paired
     if layout == "vector":
         whole.set_launch(32, hi, "vector")
-        split.set_launch(32, hi, "vector")
+        split.set_launch(64, lo, "vector")
     else:
         whole.set_launch(64, 2, "strided")
-        split.set_launch(64, 2, "strided")
+        split.set_launch(128, 1, "strided")
     whole.step(100)
     split.step(100)
     assert np.array_equal(whole.state()[0], split.state()[0])
