@@ -76,7 +76,7 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
  * moments relax order by order, a_p^(n) = a_0^(n) + (1 - 1/tau_n) a_1^(n)
  * + (1 - 1/(2 tau_n)) a_F^(n), with a_F^(n) = n F u^(n-1) and the fourth
  * order from the appendix's recursion.  All moment models start from the
- * same state; batches (lbm_batch_create) take BGK and SMRT. */
+ * same state; batches (lbm_batch_create) take all four. */
 typedef enum { LBM_BGK = 0, LBM_SMRT = 1, LBM_SMRT_FNEQ = 2, LBM_MRT_RAW = 3 } lbm_collision;
 
 /* Storage of the populations.  All modes store the deviation
@@ -274,7 +274,8 @@ const char *lbm_last_error(const lbm_handle *h);
  * tiles of rows that any CTA may claim; a channel's next step starts when
  * all tiles of its current step are done.  Every K steps a channel computes
  * its residual r_K (as lbm_residual) and retires once r_K <= tol.
- * Channels share lattice (D2Q9), collision and storage (LBM_F32 or LBM_F64);
+ * Channels share lattice (D2Q9), collision (any lbm_collision; one tau per
+ * order, no split bulk time) and storage (LBM_F32 or LBM_F64);
  * each takes its own nx, ny, periodic flags, tau, uniform (or no) force and
  * optional solid mask (halfway bounce-back at solid nodes).  The descriptions' rho0/u0 are copied.  The stream of
  * descs[0] is used (NULL => the library makes one). */

@@ -158,6 +158,21 @@ __device__ __forceinline__ void block_sum_batch(double (&v)[2]) {
     }
 }
 
+// the channel's collision on one node's grid (R = double) or two nodes'
+// (R = F2); SMRT with tau_3 = tau_4 = 1 takes the trimmed collision, as
+// k_step does, and the bulk relaxes with tau_2
+template <int COLL, typename R>
+__device__ __forceinline__ void batch_collide(R *G, R gx, R gy, R om2, R om3, R om4, bool trim) {
+    const R z = R(0);
+    if constexpr (COLL == SMRT_TRIM) collide_smrt_trim<D2Q9>(G, gx, gy, z, om2);
+    else if constexpr (COLL == SMRT) {
+        if (trim) collide_smrt_trim<D2Q9>(G, gx, gy, z, om2);
+        else collide_smrt<D2Q9>(G, gx, gy, z, om2, om3, om4, om2);
+    } else if constexpr (COLL == SMRT_FNEQ) collide_smrt_fneq<D2Q9>(G, gx, gy, z, om2, om3, om4, om2);
+    else if constexpr (COLL == MRT_RAW) collide_mrt_raw<D2Q9>(G, gx, gy, z, om2, om3, om4);
+    else collide_bgk<D2Q9>(G, gx, gy, z, om2);
+}
+
 // One FP32 node of a channel on the pair instructions (both lanes), out of
 // line: the node of a pass whose partner lies past the tile, so that the
 // kernel keeps one inlined pair collision per collision kind
@@ -170,10 +185,7 @@ __device__ __noinline__ void batch_node_alone(const BatchChan C, const float *fi
     F2 G2[9];
 #pragma unroll
     for (int g = 0; g < 9; ++g) G2[g] = F2(G[g]);
-    const F2 gx2 = F2(gx), gy2 = F2(gy), z2 = F2(0.0f);
-    if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G2, gx2, gy2, z2, F2(om2));
-    else if (COLL == SMRT) collide_smrt<D2Q9>(G2, gx2, gy2, z2, F2(om2), F2(om3), F2(om4), F2(om2));
-    else collide_bgk<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+    batch_collide<COLL>(G2, F2(gx), F2(gy), F2(om2), F2(om3), F2(om4), trim);
     float *dst = fout + (y * C.nxp + x);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store<ST_F32>::st(dst + i * (int)C.plane, G2[gpos<D2Q9>(i)].lo());
@@ -346,10 +358,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                         F2 G2[9];
 #pragma unroll
                         for (int g = 0; g < 9; ++g) G2[g] = F2::pair(G[0][g], G[1][g]);
-                        const F2 gx2 = F2(gx), gy2 = F2(gy), z2 = F2(0.0f);
-                        if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G2, gx2, gy2, z2, F2(om2));
-                        else if (COLL == SMRT) collide_smrt<D2Q9>(G2, gx2, gy2, z2, F2(om2), F2(om3), F2(om4), F2(om2));
-                        else collide_bgk<D2Q9>(G2, gx2, gy2, z2, F2(om2));
+                        batch_collide<COLL>(G2, F2(gx), F2(gy), F2(om2), F2(om3), F2(om4), trim);
                         T *d0 = fout + (ys[0] * C.nxp + xs[0]), *d1 = fout + (ys[1] * C.nxp + xs[1]);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
@@ -366,10 +375,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchRun r) {
                     for (int k = 0; k < 2; ++k) {
                         if (!on[k]) continue;
                         const int x = xs[k], y = ys[k];
-                        // tau_3 = tau_4 = 1: the trimmed collision, as k_step takes it
-                        if (COLL == SMRT_TRIM || (COLL == SMRT && trim)) collide_smrt_trim<D2Q9>(G[k], gx, gy, R(0), om2);
-                        else if (COLL == SMRT) collide_smrt<D2Q9>(G[k], gx, gy, R(0), om2, om3, om4, om2);
-                        else collide_bgk<D2Q9>(G[k], gx, gy, R(0), om2);
+                        batch_collide<COLL>(G[k], gx, gy, om2, om3, om4, trim);
                         T *dst = fout + (y * C.nxp + x);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) Store<ST>::st(dst + i * (int)C.plane, G[k][gpos<D2Q9>(i)]);
@@ -572,6 +578,8 @@ typedef void (*BatchKernel)(const BatchRun);
 BatchKernel batch_kernel(int coll, int st, bool all_trim) {
     if (coll == LBM_SMRT && all_trim) return st == LBM_F64 ? k_batch<SMRT_TRIM, ST_F64> : k_batch<SMRT_TRIM, ST_F32>;
     if (coll == LBM_SMRT) return st == LBM_F64 ? k_batch<SMRT, ST_F64> : k_batch<SMRT, ST_F32>;
+    if (coll == LBM_SMRT_FNEQ) return st == LBM_F64 ? k_batch<SMRT_FNEQ, ST_F64> : k_batch<SMRT_FNEQ, ST_F32>;
+    if (coll == LBM_MRT_RAW) return st == LBM_F64 ? k_batch<MRT_RAW, ST_F64> : k_batch<MRT_RAW, ST_F32>;
     return st == LBM_F64 ? k_batch<BGK, ST_F64> : k_batch<BGK, ST_F32>;
 }
 
@@ -848,8 +856,7 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
     const lbm_desc &d0 = descs[0];
     if (d0.lattice != LBM_D2Q9) return bfail(nullptr, LBM_ERR_ARG, "batches are D2Q9");
     if (d0.storage != LBM_F32 && d0.storage != LBM_F64) return bfail(nullptr, LBM_ERR_ARG, "batch storage is F32 or F64");
-    if (d0.collision != LBM_BGK && d0.collision != LBM_SMRT)
-        return bfail(nullptr, LBM_ERR_ARG, "batches take BGK or SMRT collisions");
+    if (d0.collision < LBM_BGK || d0.collision > LBM_MRT_RAW) return bfail(nullptr, LBM_ERR_ARG, "bad collision");
     for (int c = 0; c < n; ++c) {
         const lbm_desc &d = descs[c];
         if (d.lattice != d0.lattice || d.collision != d0.collision || d.storage != d0.storage)
@@ -861,7 +868,7 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         if (d.collision == LBM_BGK && !(d.tau[2] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2] must be > 1/2");
         if (d.tau_bulk != 0.0 && d.tau_bulk != d.tau[2])
             return bfail(nullptr, LBM_ERR_ARG, "batches relax the second order with one tau (tau_bulk 0 or tau[2])");
-        if (d.collision == LBM_SMRT)
+        if (d.collision != LBM_BGK)
             for (int k = 2; k <= 4; ++k)
                 if (!(d.tau[k] > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "tau[2..4] must be > 1/2");
     }
@@ -921,8 +928,8 @@ lbm_status lbm_batch_create(const lbm_desc *descs, int n, lbm_batch **out) {
         C.per_x = d.periodic[0] ? 1 : 0;
         C.per_y = d.periodic[1] ? 1 : 0;
         C.om2 = 1.0 / d.tau[2];
-        C.om3 = d.collision == LBM_SMRT ? 1.0 / d.tau[3] : 0.0;
-        C.om4 = d.collision == LBM_SMRT ? 1.0 / d.tau[4] : 0.0;
+        C.om3 = d.collision != LBM_BGK ? 1.0 / d.tau[3] : 0.0;
+        C.om4 = d.collision != LBM_BGK ? 1.0 / d.tau[4] : 0.0;
         C.gx = d.force_kind == LBM_G_UNIFORM ? d.g[0] : 0.0;
         C.gy = d.force_kind == LBM_G_UNIFORM ? d.g[1] : 0.0;
         b->field_off[c] = fields;

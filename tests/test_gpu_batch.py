@@ -23,7 +23,8 @@ def _channels(n, seed, nx=(5, 90), ny=(3, 40)):
     return out
 
 
-@pytest.mark.parametrize("coll,storage", [("SMRT", "F32"), ("BGK", "F32"), ("SMRT", "F64")])
+@pytest.mark.parametrize("coll,storage", [("SMRT", "F32"), ("BGK", "F32"), ("SMRT", "F64"), ("SMRT_FNEQ", "F32"),
+                                          ("SMRT_FNEQ", "F64"), ("MRT_RAW", "F32"), ("MRT_RAW", "F64")])
 def test_batch_matches_single_lattices(coll, storage):
     import paper_2212_07494_gb300 as P
     chans = _channels(12, 7)
